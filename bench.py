@@ -1,0 +1,511 @@
+#!/usr/bin/env python
+"""Throughput benchmark: Tersoff MD on one GB300 (mixed and FP64 paths).
+
+Workload: Si diamond 40x40x40 cubic cells (512,000 atoms, a = 5.432 A),
+Gaussian displacements sigma = 0.05 A, Maxwell velocities at 1000 K,
+velocity-Verlet NVE with dt = 1 fs, neighbour list radius 4.0 A (cutoff 3.0 A
++ skin 1.0 A) rebuilt every 10 steps. One benchmark step = one rebuild period
+= 10 MD steps (kick, drift, [rebuild], forces, kick), so every step includes
+one neighbour build. Metric: atom-steps/s = atoms x MD steps / device time.
+
+The L2 cache is flushed (a 512 MiB write) before every timed step, outside the
+timed events. With N GPUs (torchrun) each rank runs its own replica of the
+workload (the metric's workload is one periodic cell; there is no data-path
+collective); value = all ranks' atom-steps / slowest rank's time.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Tersoff atom-steps/s on 1 GB300, mixed vs FP64 path, at stated force error"
+UNIT = "atom-steps/s"
+MD_PER_STEP = 10
+DT = 0.001
+R_LIST = 4.0
+PEAK_FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+PEAK_FP64_TFLOPS_NOMINAL = 1.25
+
+# Algorithmic FP32 operations of the mixed force kernel per unit of work
+# (additions, multiplications, one per FMA half; special-function ops counted
+# separately): per skin-list entry scanned by the filter, per short-list
+# neighbour (bond vector, length, unit vector, force/virial epilogue), per pair
+# term and per three-body term.
+FLOP_SKIN, FLOP_SHORT, FLOP_PAIR, FLOP_TRIPLET = 15, 36, 63, 61
+MUFU_SHORT, MUFU_PAIR, MUFU_TRIPLET = 1, 7, 1
+
+
+def workload_name():
+    return ("si-diamond-40x40x40-512000-atoms-1000K-dt1fs-rlist4.0-rebuild10-"
+            "10-md-steps-per-step")
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_ms: float, local_units: float, world: int):
+    """Max of the per-rank times and the sum of units over ranks."""
+    if world == 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([local_units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for _, _, r in rows for q in range(4) if r[q] == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def smi_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids) and ids[local_rank].strip().isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+def work_counts(x, types, box, cnt, nbr, table, ns):
+    """Skin entries, short-list entries, pairs and three-body terms inside their
+    cutoffs (FLOP model bookkeeping, from the library's exported list)."""
+    import numpy as np
+    t = np.asarray(table).reshape(ns, ns, ns, 14)
+    rout = t[..., 10] + t[..., 11]  # R + D per record
+    n = x.shape[0]
+    mask = nbr >= 0
+    j = np.where(mask, nbr, 0)
+    d = x[j] - x[:, None, :]
+    d -= box * np.rint(d / box)
+    r = np.sqrt((d * d).sum(-1))
+    ti = types[:, None]
+    tj = types[j]
+    pair_cut = rout[ti, tj, tj]
+    filt = np.zeros((ns, ns))
+    for a in range(ns):
+        for b in range(ns):
+            filt[a, b] = max(rout[a, b, b], rout[a, :, b].max())
+    short = mask & (r <= filt[ti, tj])
+    pairs = short & (r < pair_cut)
+    skin = int(mask.sum())
+    nshort = int(short.sum())
+    npair = int(pairs.sum())
+    # three-body terms: ordered (j, k), j in pairs, k short and inside its cutoff
+    trip = 0
+    zmax = int(short.sum(1).max()) if n else 0
+    order = np.argsort(~short, axis=1, kind="stable")[:, :zmax]
+    rs = np.take_along_axis(r, order, 1)
+    ok = np.take_along_axis(short, order, 1)
+    okp = np.take_along_axis(pairs, order, 1)
+    tjs = np.take_along_axis(tj, order, 1)
+    for qj in range(zmax):
+        for qk in range(zmax):
+            if qj == qk:
+                continue
+            cut = rout[types, tjs[:, qj], tjs[:, qk]]
+            trip += int((okp[:, qj] & ok[:, qk] & (rs[:, qk] < cut)).sum())
+    return skin, nshort, npair, trip
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_1607_02904_gb300 as T
+
+    world, rank, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    x, v, t, box, names = W.config_si_md()
+    n = x.shape[0]
+    table = T.mix_tersoff89(*W.element_records(names))
+    mass = [W.MASS_AMU[s] for s in names]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def setup(prec):
+        ctx = T.Context(prec)
+        ctx.params(table)
+        xd = torch.tensor(x, dtype=torch.float64, device=dev)
+        vd = torch.tensor(v, dtype=torch.float64, device=dev)
+        td = torch.tensor(t, dtype=torch.int32, device=dev)
+        ctx.neighbor_build(xd, td, box, R_LIST)
+        fd = torch.zeros_like(xd)
+        e = torch.zeros(1, dtype=torch.float64, device=dev)
+        w = torch.zeros(6, dtype=torch.float64, device=dev)
+        ctx.compute(xd, e, fd, w)
+        return ctx, xd, vd, td, fd, e, w
+
+    def timed(ctx, xd, vd, fd, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        l0 = ctx.launch_count()
+        stream = torch.cuda.current_stream()
+        ms = []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = ctx.launch_count() - l0
+        kern = ctx.timing(0)
+        build = ctx.timing(1)
+        integ = ctx.timing(2)
+        ctx.set_timing(False)
+        return sum(ms), launches, kern, build, integ, clocks
+
+    out = {}
+    # ---------------- accuracy of the mixed path against the FP64 path (same start)
+    ctx64, xd64, vd64, td, f64, e64, w64 = setup(T.FP64)
+    ctxm, xdm, vdm, _, fm, em, wm = setup(T.MIXED)
+    torch.cuda.synchronize()
+    fr = f64.cpu().numpy()
+    fmm = fm.cpu().numpy()
+    force_rms_rel = float(np.sqrt(((fmm - fr) ** 2).mean()) / np.sqrt((fr ** 2).mean()))
+    energy_rel = float(abs(em.item() - e64.item()) / abs(e64.item()))
+    virial_rel = float((wm - w64).abs().max().item() / w64.abs().max().item())
+
+    # FLOP model inputs from the exported skin list
+    cap, mx = ctxm.neighbor_capacity()
+    cnt, nbr, _ = ctxm.neighbor_export(mx)
+    skin, nshort, npair, ntrip = work_counts(x, t, box, cnt.cpu().numpy(), nbr.cpu().numpy(),
+                                             table, len(names))
+    del cnt, nbr
+    flop_launch = (FLOP_SKIN * skin + FLOP_SHORT * nshort + FLOP_PAIR * npair +
+                   FLOP_TRIPLET * ntrip)
+    mufu_launch = MUFU_SHORT * nshort + MUFU_PAIR * npair + MUFU_TRIPLET * ntrip
+
+    # ---------------- timed: mixed (headline), then FP64
+    sampler = ClockSampler(smi_index(local))
+    ms_m, launches_m, kern_m, build_m, integ_m, clocks = timed(ctxm, xdm, vdm, fm, args.steps,
+                                                               args.warmup, sampler)
+    ms_d, launches_d, kern_d, build_d, integ_d, _ = timed(ctx64, xd64, vd64, f64, args.steps,
+                                                          args.warmup)
+    units = float(n) * MD_PER_STEP * args.steps
+    tmax_m, units_all = aggregate(ms_m, units, world)
+    tmax_d, _ = aggregate(ms_d, units, world)
+    value = units_all / (tmax_m * 1e-3)
+    value_d = units_all / (tmax_d * 1e-3)
+
+    # ---------------- end to end through the host-buffer entry point (mixed)
+    xh = xdm.cpu().pin_memory()
+    vh = vdm.cpu().pin_memory()
+    fh = fm.cpu().pin_memory()
+    for _ in range(max(1, args.warmup)):
+        ctxm.md_step_host(xh, vh, fh, mass, DT, MD_PER_STEP, MD_PER_STEP)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    ms_e = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a.record(stream)
+        ctxm.md_step_host(xh, vh, fh, mass, DT, MD_PER_STEP, MD_PER_STEP)
+        b.record(stream)
+        b.synchronize()
+        ms_e += a.elapsed_time(b)
+    wall_e = time.perf_counter() - t0
+    tmax_e, _ = aggregate(ms_e, units, world)
+    value_e = units_all / (tmax_e * 1e-3)
+
+    kern_ms = kern_m[0] / max(kern_m[1], 1)
+    achieved = flop_launch / (kern_ms * 1e-3) / 1e12
+    kern_ms_d = kern_d[0] / max(kern_d[1], 1)
+
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else {}
+
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tmax_m / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "accumulate_dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": workload_name(),
+            "atoms_per_gpu": n,
+            "md_steps_per_step": MD_PER_STEP,
+            "dt_ps": DT,
+            "neighbor_rebuild_every": MD_PER_STEP,
+            "r_list_A": R_LIST,
+            "l2": "flushed before each timed step (512 MiB write, outside the timed events)",
+            "parallelism": f"replicas x{world}",
+        },
+        "force_error": {
+            "reference": "FP64 GPU path (itself within 1e-10 of the FP64 CPU oracle in tests)",
+            "force_rms_rel": force_rms_rel,
+            "energy_rel": energy_rel,
+            "virial_max_rel": virial_rel,
+        },
+        "fp64": {
+            "value": value_d,
+            "unit": UNIT,
+            "ms_per_step": tmax_d / args.steps,
+            "dtype": "f64",
+            "force_kernel_ms": kern_ms_d,
+            "force_kernel_tflops": flop_launch / (kern_ms_d * 1e-3) / 1e12,
+            "force_kernel_frac_of_fp64_nominal": flop_launch / (kern_ms_d * 1e-3) / 1e12 /
+            PEAK_FP64_TFLOPS_NOMINAL,
+            "gpu_launches": launches_d,
+        },
+        "mixed_over_fp64": value / value_d,
+        "roofline": {
+            "bound": "alu",
+            "kernel": "k_tersoff<float> (fused zeta/bond-order/force)",
+            "achieved": achieved,
+            "peak": PEAK_FP32_TFLOPS_NOMINAL,
+            "unit": "TFLOP/s",
+            "frac": achieved / PEAK_FP32_TFLOPS_NOMINAL,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max clock",
+            "traffic": None,
+            "flop_per_launch": flop_launch,
+            "mufu_per_launch": mufu_launch,
+            "work_per_launch": {"skin_entries": skin, "short_entries": nshort, "pairs": npair,
+                                "triplets": ntrip},
+            "kernel_ms": kern_ms,
+            "kernel_launches_timed": kern_m[1],
+        },
+        "breakdown_ms_per_step": {
+            "force": kern_m[0] / args.steps,
+            "neighbor_build": build_m[0] / args.steps,
+            "integrate": integ_m[0] / args.steps,
+        },
+        "e2e": {
+            "value": value_e,
+            "unit": UNIT,
+            "h2d_bytes_per_step": 3 * n * 3 * 8,
+            "d2h_bytes_per_step": 3 * n * 3 * 8,
+            "wall_s": wall_e,
+        },
+        "gpu_launches": launches_m,
+        "clocks": clocks,
+        "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(x, v, t, box, names, table)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(x, v, t, box, names, table, nsteps=20):
+    """The FP64 oracle on the host cores: full 512,000-atom system, velocity
+    Verlet for nsteps steps (rebuild every 10) minus its own setup (one list
+    build and one force evaluation), scaled to atom-steps/s."""
+    import oracle
+    import workloads as W
+    mass = [W.MASS_AMU[s] for s in names]
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.md_run(x, v, t, box, table, mass, DT, 0, R_LIST, MD_PER_STEP, cap=48,
+                  nthreads=cores)
+    t1 = time.perf_counter()
+    oracle.md_run(x, v, t, box, table, mass, DT, nsteps, R_LIST, MD_PER_STEP, cap=48,
+                  nthreads=cores)
+    t2 = time.perf_counter()
+    per = (t2 - t1) - (t1 - t0)
+    return {"value": x.shape[0] * nsteps / per, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"oracle MD on the full {x.shape[0]}-atom system: {nsteps} VV steps "
+                      f"(rebuild every {MD_PER_STEP}), setup subtracted, {cores} OpenMP threads",
+            "seconds": t2 - t0}
+
+
+def run_reference(args):
+    world, rank, local = dist_info()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    import oracle
+    import workloads as W
+    x, v, t, box, names = W.config_si_md()
+    table = oracle.mix_tersoff89(*W.element_records(names))
+    mass = [W.MASS_AMU[s] for s in names]
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.md_run(x, v, t, box, table, mass, DT, 1, R_LIST, MD_PER_STEP, cap=48,
+                      nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.md_run(x, v, t, box, table, mass, DT, MD_PER_STEP, R_LIST, MD_PER_STEP, cap=48,
+                      nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    units = x.shape[0] * MD_PER_STEP * args.steps
+    value = units / total
+    out = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(), "atoms_per_gpu": x.shape[0],
+                   "md_steps_per_step": MD_PER_STEP, "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: oracle md_run of {MD_PER_STEP} VV steps on the "
+                                   f"full system including its list build and first force "
+                                   f"evaluation, {cores} OpenMP threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_profile_case(args):
+    """The benchmark workload without timing, for profiler captures."""
+    import torch
+    import workloads as W
+    import paper_1607_02904_gb300 as T
+    x, v, t, box, names = W.config_si_md()
+    table = T.mix_tersoff89(*W.element_records(names))
+    mass = [W.MASS_AMU[s] for s in names]
+    ctx = T.Context(T.MIXED if args.precision == "mixed" else T.FP64)
+    ctx.params(table)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+    td = torch.tensor(t, dtype=torch.int32, device="cuda")
+    ctx.neighbor_build(xd, td, box, R_LIST)
+    fd = torch.zeros_like(xd)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(args.steps):
+        if args.only == "force":
+            ctx.compute(xd, e, fd)
+        else:
+            ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["force", "md"], default=None,
+                    help="profiling case: K force evaluations (or K MD rebuild periods) of "
+                         "the benchmark workload, nothing printed")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    args = ap.parse_args()
+    if args.only:
+        run_profile_case(args)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * tersoff.h -- C ABI of the GB300 Tersoff library (libtersoff_gb300.so).
+ *
+ * The library evaluates the Tersoff multi-body potential (Hoehnerbach, Ismail,
+ * Bientinesi, "The Vectorization of the Tersoff Multi-Body Potential", SC'16;
+ * Sec. III, Eq. 5-7) -- energy, forces and virial over a neighbour list --
+ * and runs velocity-Verlet molecular dynamics with it, on one GPU.
+ *
+ * Conventions for every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller unless a comment
+ *    says "host". Positions, velocities and forces are row-major N x 3 double
+ *    (atom-major, x y z). Species are int32 in [0, n_species).
+ *  - Units are "metal": Angstrom, eV, ps, amu.
+ *  - The box is orthorhombic and periodic in all three directions, with edges
+ *    box[0..2] (host array). Distances use the minimum image convention.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Work is enqueued on it; an entry point returns after enqueueing
+ *    unless its comment says it synchronises the stream.
+ *  - Every entry point returns a status code (TERSOFF_OK or TERSOFF_E_*);
+ *    tersoff_last_error() gives a one-line description of the last failure on
+ *    that context. A failed call leaves caller-owned outputs undefined.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef TERSOFF_GB300_H
+#define TERSOFF_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tersoff_ctx tersoff_ctx;
+
+/* status codes */
+#define TERSOFF_OK 0
+#define TERSOFF_E_INVALID_ARG 1    /* bad pointer, size or value */
+#define TERSOFF_E_BOX_TOO_SMALL 2  /* a box edge is shorter than 2 x list radius */
+#define TERSOFF_E_NEIGH_OVERFLOW 3 /* neighbour capacity exceeded (see tersoff_neighbor_capacity) */
+#define TERSOFF_E_NONFINITE 4      /* non-finite position found while building lists */
+#define TERSOFF_E_TIMEOUT 5        /* a bounded device-side wait gave up */
+#define TERSOFF_E_CUDA 6           /* a CUDA runtime call failed */
+#define TERSOFF_E_STATE 7          /* call out of order (e.g. compute before params) */
+
+/* arithmetic paths */
+#define TERSOFF_FP64 0  /* all arithmetic in double (the paper's Opt-D mode, Sec. V-E) */
+#define TERSOFF_MIXED 1 /* per-term arithmetic in float, sums across atoms in double
+                           (the paper's Opt-M mode, Sec. V-E) */
+
+/* Number of doubles per parameter record and their order. */
+#define TERSOFF_NPARAM 14
+/* field order inside a record */
+#define TERSOFF_P_M 0
+#define TERSOFF_P_GAMMA 1
+#define TERSOFF_P_LAMBDA3 2
+#define TERSOFF_P_C 3
+#define TERSOFF_P_D 4
+#define TERSOFF_P_H 5
+#define TERSOFF_P_N 6
+#define TERSOFF_P_BETA 7
+#define TERSOFF_P_LAMBDA2 8
+#define TERSOFF_P_B 9
+#define TERSOFF_P_R 10
+#define TERSOFF_P_D_CUT 11
+#define TERSOFF_P_LAMBDA1 12
+#define TERSOFF_P_A 13
+
+/* Maximum number of species per context. */
+#define TERSOFF_MAX_SPECIES 4
+
+/* Create a context computing in `precision` (TERSOFF_FP64 or TERSOFF_MIXED)
+ * on the current CUDA device. *ctx receives the new context. */
+int tersoff_create(tersoff_ctx** ctx, int precision);
+
+/* Free a context and all device memory it owns. NULL is accepted. Waits for
+ * the context's outstanding work. */
+int tersoff_destroy(tersoff_ctx* ctx);
+
+/* One-line description of the last failure on `ctx` (static storage owned by
+ * the context; valid until the next call on it). */
+const char* tersoff_last_error(const tersoff_ctx* ctx);
+
+/* Switch the arithmetic path of an existing context. */
+int tersoff_set_precision(tersoff_ctx* ctx, int precision);
+
+/* Load the per-triplet parameter table (Eq. 5-7's parameters; Sec. III).
+ * table: HOST array of n_species^3 records of TERSOFF_NPARAM doubles, record
+ * ((ti*n_species + tj)*n_species + tk) for centre species ti, bond partner tj
+ * and third atom tk. Record (ti,tj,tj) gives the pair terms of bond i-j
+ * (n, beta, lambda2, B, lambda1, A and the R, D of f_C(r_ij)); record
+ * (ti,tj,tk) gives the three-body terms (m, gamma, lambda3, c, d, h and the
+ * R, D of f_C(r_ik)). m must be a positive integer; D > 0; n > 0.
+ * The table is copied; the caller keeps ownership. */
+int tersoff_params(tersoff_ctx* ctx, int n_species, const double* table);
+
+/* Build the full ("skin") neighbour list S_i = { j != i : r_ij <= r_list }
+ * (Sec. II Eq. 4, with the skin of Sec. III) for n atoms at positions x
+ * (device, N x 3) with species types (device, N), in the periodic box `box`
+ * (host, 3 doubles). r_list is the cutoff plus skin. The membership test is
+ * exact: d = x_j - x_i; d -= L * rint(d * (1/L)) per axis in double, and
+ * r^2 = (dx*dx + dy*dy) + dz*dz compared with r_list^2, all without fused
+ * multiply-add. The list is kept inside the context and used by the compute
+ * and MD calls until the next build. If an atom has more neighbours than the
+ * current capacity, the capacity is grown and the build redone. Synchronises
+ * `stream` (to read the overflow check). Returns TERSOFF_E_BOX_TOO_SMALL if
+ * some box edge < 2 r_list and TERSOFF_E_NONFINITE for non-finite input.
+ * Does not modify x. At most 2^26 atoms. */
+int tersoff_neighbor_build(tersoff_ctx* ctx, const double* x, const int* types, int n,
+                           const double* box, double r_list, void* stream);
+
+/* Current per-atom capacity of the neighbour list and the largest count seen
+ * in the last build (host outputs, either may be NULL). */
+int tersoff_neighbor_capacity(const tersoff_ctx* ctx, int* capacity, int* max_count);
+
+/* Set the per-atom capacity used by the next build (>= 1). */
+int tersoff_set_neighbor_capacity(tersoff_ctx* ctx, int capacity);
+
+/* Copy the last-built list out: cnt (device, N int32) receives each atom's
+ * neighbour count, nbr (device, N x cap int32, row-major) the neighbour indices
+ * in ascending order, padded with -1. Returns TERSOFF_E_NEIGH_OVERFLOW if some
+ * count exceeds cap (cnt is still written). */
+int tersoff_neighbor_export(tersoff_ctx* ctx, int* cnt, int* nbr, int cap, void* stream);
+
+/* Energy, forces and virial (Eq. 1, Eq. 5-7) of the atoms of the last
+ * neighbour build, at positions x (device, N x 3; the same atoms, moved by
+ * less than half the skin since the build). Outputs (device): energy[1],
+ * forces[N x 3], virial[6] = (xx, yy, zz, xy, xz, yz) with
+ * W_ab = sum over terms of (x_a - x_i)_a F_b relative to each term's centre
+ * atom i (positive = repulsive); any output may be NULL. Outputs are
+ * overwritten, not accumulated. */
+int tersoff_compute(tersoff_ctx* ctx, const double* x, int n, double* energy,
+                    double* forces, double* virial, void* stream);
+
+/* Per-atom energy of the last tersoff_compute (device, N doubles): the pair
+ * terms V(i, j, zeta_ij) summed over j, assigned to the centre atom i. */
+int tersoff_compute_peratom(tersoff_ctx* ctx, const double* x, int n, double* eatom,
+                            void* stream);
+
+/* Velocity-Verlet NVE steps in metal units (x in A, v in A/ps, dt in ps,
+ * forces in eV/A). Requires a prior tersoff_neighbor_build on these atoms and
+ * forces f holding F(x) (for example from tersoff_compute). Each step:
+ *   v += dt/2 f/m;  x += dt v;  rebuild the list when the number of steps
+ *   since the last build reaches rebuild_every (0 = never);  f = F(x);
+ *   v += dt/2 f/m.
+ * mass: HOST array of n_species masses (amu). x, v, f (device, N x 3) are
+ * updated in place; positions are not wrapped into the box. thermo (device,
+ * nsteps x 3, may be NULL) receives potential, kinetic and total energy (eV)
+ * after each step. Synchronises `stream` at the end to report neighbour
+ * overflow during the run. */
+int tersoff_md_step(tersoff_ctx* ctx, double* x, double* v, double* f, int n,
+                    const double* mass, double dt, int nsteps, int rebuild_every,
+                    double* thermo, void* stream);
+
+/* The same MD steps with HOST arrays x, v, f (N x 3 doubles each, ideally
+ * pinned) and host thermo (nsteps x 3, may be NULL): copies the state to the
+ * device, runs tersoff_md_step, and copies x, v, f and thermo back. Device
+ * staging buffers are owned by the context. Synchronises `stream`. */
+int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int n,
+                         const double* mass, double dt, int nsteps, int rebuild_every,
+                         double* thermo, void* stream);
+
+/* Number of kernel launches this context has enqueued since creation (host
+ * output); used to report launch counts. */
+int tersoff_launch_count(const tersoff_ctx* ctx, long long* count);
+
+/* Kernel timing. With enable != 0 the context records a CUDA event pair on the
+ * launching stream around every force-kernel launch (kind 0), every neighbour
+ * build (kind 1, all of its kernels) and every integration kernel (kind 2).
+ * Enabling resets the totals. */
+int tersoff_set_timing(tersoff_ctx* ctx, int enable);
+
+/* Accumulated device time in milliseconds and number of timed launches of
+ * `kind` since timing was enabled (host outputs). Waits for the recorded
+ * events. */
+int tersoff_timing(tersoff_ctx* ctx, int kind, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TERSOFF_GB300_H */

@@ -1,0 +1,18 @@
+"""GB300 (sm_103a) Tersoff potential: energy, forces, virial and MD.
+
+The compute path is the CUDA library ``libtersoff_gb300.so`` (C ABI in
+``include/tersoff.h``); this package binds it (``Context``), builds the
+per-triplet parameter table from element parameters (``params``), and wraps
+the energy in a ``torch.autograd.Function``.
+"""
+from ._lib import (  # noqa: F401
+    Context,
+    TersoffError,
+    FP64,
+    MIXED,
+    NPARAM,
+    load,
+    library_path,
+    declared_symbols,
+)
+from .params import mix_tersoff89, FIELDS  # noqa: F401

@@ -1,0 +1,203 @@
+"""ctypes binding of the C ABI in include/tersoff.h (argument marshalling only).
+
+Every array handed to the library is a contiguous CUDA torch tensor (device
+memory and streams come from PyTorch); nothing is computed here. If the shared
+library cannot be built or loaded the import fails loudly: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+OK = 0
+E_INVALID_ARG = 1
+E_BOX_TOO_SMALL = 2
+E_NEIGH_OVERFLOW = 3
+E_NONFINITE = 4
+E_TIMEOUT = 5
+E_CUDA = 6
+E_STATE = 7
+FP64 = 0
+MIXED = 1
+NPARAM = 14
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIG = {
+    "tersoff_create": ([ctypes.POINTER(_P), _I], _I),
+    "tersoff_destroy": ([_P], _I),
+    "tersoff_last_error": ([_P], ctypes.c_char_p),
+    "tersoff_set_precision": ([_P, _I], _I),
+    "tersoff_params": ([_P, _I, _P], _I),
+    "tersoff_neighbor_build": ([_P, _P, _P, _I, _P, _D, _P], _I),
+    "tersoff_neighbor_capacity": ([_P, _P, _P], _I),
+    "tersoff_set_neighbor_capacity": ([_P, _I], _I),
+    "tersoff_neighbor_export": ([_P, _P, _P, _I, _P], _I),
+    "tersoff_compute": ([_P, _P, _I, _P, _P, _P, _P], _I),
+    "tersoff_compute_peratom": ([_P, _P, _I, _P, _P], _I),
+    "tersoff_md_step": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
+    "tersoff_md_step_host": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
+    "tersoff_launch_count": ([_P, _P], _I),
+    "tersoff_set_timing": ([_P, _I], _I),
+    "tersoff_timing": ([_P, _I, _P, _P], _I),
+}
+
+
+class TersoffError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tersoff status {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load (building first if needed) libtersoff_gb300.so and bind symbols."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIG.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Entry points declared in include/tersoff.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_build.HERE), "include", "tersoff.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(tersoff_\w+)\(", text, re.M)))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One tersoff_ctx. Methods mirror the C entry points of the same names."""
+
+    def __init__(self, precision=MIXED):
+        self.lib = load()
+        h = _P()
+        st = self.lib.tersoff_create(ctypes.byref(h), int(precision))
+        if st != OK:
+            raise TersoffError(st, "tersoff_create failed")
+        self.h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tersoff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            msg = self.lib.tersoff_last_error(self.h)
+            raise TersoffError(st, msg.decode() if msg else "")
+
+    def set_precision(self, precision):
+        self._check(self.lib.tersoff_set_precision(self.h, int(precision)))
+
+    def params(self, table):
+        """table: host float64 array-like of n_species^3 * 14 values."""
+        import numpy as np
+        t = np.ascontiguousarray(table, dtype=np.float64).ravel()
+        ns = round((t.size // NPARAM) ** (1.0 / 3.0))
+        assert ns ** 3 * NPARAM == t.size, "table size must be n_species^3 * 14"
+        self._check(self.lib.tersoff_params(self.h, ns, t.ctypes.data_as(_P)))
+        self.ns = ns
+
+    def neighbor_build(self, x, types, box, r_list, stream=None):
+        import numpy as np
+        b = np.ascontiguousarray(box, dtype=np.float64)
+        self.n = int(x.shape[0])
+        self._check(self.lib.tersoff_neighbor_build(self.h, _ptr(x), _ptr(types), self.n,
+                                                    b.ctypes.data_as(_P), float(r_list),
+                                                    _stream(stream)))
+
+    def neighbor_capacity(self):
+        cap = _I()
+        mx = _I()
+        self._check(self.lib.tersoff_neighbor_capacity(self.h, ctypes.byref(cap),
+                                                       ctypes.byref(mx)))
+        return cap.value, mx.value
+
+    def set_neighbor_capacity(self, cap):
+        self._check(self.lib.tersoff_set_neighbor_capacity(self.h, int(cap)))
+
+    def neighbor_export(self, cap, stream=None):
+        import torch
+        cnt = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        nbr = torch.empty((self.n, cap), dtype=torch.int32, device="cuda")
+        st = self.lib.tersoff_neighbor_export(self.h, _ptr(cnt), _ptr(nbr), int(cap),
+                                              _stream(stream))
+        if st not in (OK, E_NEIGH_OVERFLOW):
+            self._check(st)
+        return cnt, nbr, st
+
+    def compute(self, x, energy=None, forces=None, virial=None, stream=None):
+        self._check(self.lib.tersoff_compute(self.h, _ptr(x), int(x.shape[0]), _ptr(energy),
+                                             _ptr(forces), _ptr(virial), _stream(stream)))
+
+    def compute_peratom(self, x, eatom, stream=None):
+        self._check(self.lib.tersoff_compute_peratom(self.h, _ptr(x), int(x.shape[0]),
+                                                     _ptr(eatom), _stream(stream)))
+
+    def md_step(self, x, v, f, mass, dt, nsteps, rebuild_every, thermo=None, stream=None):
+        import numpy as np
+        m = np.ascontiguousarray(mass, dtype=np.float64)
+        self._check(self.lib.tersoff_md_step(self.h, _ptr(x), _ptr(v), _ptr(f), int(x.shape[0]),
+                                             m.ctypes.data_as(_P), float(dt), int(nsteps),
+                                             int(rebuild_every), _ptr(thermo), _stream(stream)))
+
+    def md_step_host(self, x, v, f, mass, dt, nsteps, rebuild_every, thermo=None, stream=None):
+        """x, v, f, thermo: host (ideally pinned) float64 torch tensors."""
+        import numpy as np
+        m = np.ascontiguousarray(mass, dtype=np.float64)
+        self._check(self.lib.tersoff_md_step_host(self.h, _ptr(x), _ptr(v), _ptr(f),
+                                                  int(x.shape[0]), m.ctypes.data_as(_P),
+                                                  float(dt), int(nsteps), int(rebuild_every),
+                                                  _ptr(thermo), _stream(stream)))
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.tersoff_set_timing(self.h, int(bool(enable))))
+
+    def timing(self, kind):
+        """(total_ms, launches) of kind 0 force kernel, 1 neighbour build, 2 integrate."""
+        ms = _D()
+        cnt = ctypes.c_longlong()
+        self._check(self.lib.tersoff_timing(self.h, int(kind), ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+    def launch_count(self):
+        c = ctypes.c_longlong()
+        self._check(self.lib.tersoff_launch_count(self.h, ctypes.byref(c)))
+        return c.value

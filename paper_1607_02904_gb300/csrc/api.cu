@@ -1,0 +1,556 @@
+// C ABI entry points (include/tersoff.h): argument checks, device buffers owned
+// by the context, and the launch sequences of the compute and MD calls.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace tgb {
+
+int fail(Ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" +
+                  cudaGetErrorString(e) + ") in " + where;
+  return fail(c, TERSOFF_E_CUDA, m);
+}
+
+static cudaEvent_t take_event(Ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+TimedRegion::TimedRegion(Ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
+  if (!c->timing) return;
+  a = take_event(c);
+  b = take_event(c);
+  if (a) cudaEventRecord(a, s);
+}
+
+TimedRegion::~TimedRegion() {
+  if (!c->timing || !a || !b) return;
+  cudaEventRecord(b, s);
+  c->pending.push_back({kind, a, b});
+}
+
+int fold_timing(Ctx* c) {
+  for (auto& p : c->pending) {
+    cudaEventSynchronize(p.b);
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->t_ms[p.kind] += ms;
+      c->t_count[p.kind] += 1;
+    }
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+  return TERSOFF_OK;
+}
+
+namespace {
+
+// Metal units: 1 amu A^2 / ps^2 in eV, and its inverse (force eV/A over mass
+// amu in A/ps^2).
+constexpr double MVV2E = 1.0364269e-4;
+constexpr double FTM2V = 1.0 / MVV2E;
+constexpr double PI = 3.14159265358979323846;
+
+template <class T>
+int dev_alloc(Ctx* c, T** p, size_t count) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (count == 0) count = 1;
+  TGB_CUDA(c, cudaMalloc((void**)p, sizeof(T) * count));
+  return TERSOFF_OK;
+}
+
+int ensure_atoms(Ctx* c, int n) {
+  if ((size_t)n <= c->atoms_alloc && c->d_types) return TERSOFF_OK;
+  size_t m = (size_t)n;
+  int st;
+  if ((st = dev_alloc(c, &c->d_types, m))) return st;
+  if ((st = dev_alloc(c, &c->d_cnt, m))) return st;
+  if ((st = dev_alloc(c, &c->d_origin, 3 * m))) return st;
+  if ((st = dev_alloc(c, &c->d_cell_of, m))) return st;
+  if ((st = dev_alloc(c, &c->d_cell_atoms, m))) return st;
+  if ((st = dev_alloc(c, &c->d_pos32, m))) return st;
+  if ((st = dev_alloc(c, &c->d_posq, m))) return st;
+  if ((st = dev_alloc(c, &c->d_pos64, m))) return st;
+  if ((st = dev_alloc(c, &c->d_fbuf, 3 * m))) return st;
+  c->atoms_alloc = m;
+  c->nbr_alloc = 0;  // list storage depends on n
+  return TERSOFF_OK;
+}
+
+int ensure_nbr(Ctx* c) {
+  size_t need = (size_t)c->cap * (size_t)c->n;
+  if (need <= c->nbr_alloc && c->d_nbr) return TERSOFF_OK;
+  int st = dev_alloc(c, &c->d_nbr, need);
+  if (st) return st;
+  c->nbr_alloc = need;
+  return TERSOFF_OK;
+}
+
+bool valid_precision(int p) { return p == TERSOFF_FP64 || p == TERSOFF_MIXED; }
+
+// Build grid geometry on the host.
+int setup_grid(Ctx* c, const double* box, double r_list) {
+  Grid& g = c->grid;
+  double hmax = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    if (!(box[a] > 0.0) || !std::isfinite(box[a]))
+      return fail(c, TERSOFF_E_INVALID_ARG, "box edges must be positive and finite");
+    if (box[a] < 2.0 * r_list)
+      return fail(c, TERSOFF_E_BOX_TOO_SMALL,
+                  "box edge shorter than twice the neighbour-list radius");
+    int nc = (int)std::floor(box[a] / r_list);
+    if (nc < 2) nc = 2;
+    if (nc > 1024) nc = 1024;
+    g.nc[a] = nc;
+    g.L[a] = box[a];
+    g.invL[a] = 1.0 / box[a];
+    g.h[a] = box[a] / nc;
+    g.invh[a] = nc / box[a];
+    hmax = std::fmax(hmax, g.h[a]);
+  }
+  // offsets u = x - o stay within [-8, h + 8) A between rebuilds; 2^S such
+  // that (h + 8) 2^S < 2^30 keeps differences inside int32
+  g.fix_shift = (int)std::floor(30.0 - std::log2(hmax + 8.0));
+  return TERSOFF_OK;
+}
+
+int read_flags(Ctx* c, cudaStream_t s) {
+  TGB_CUDA(c, cudaMemcpyAsync(c->h_flags, c->d_flags, sizeof(int) * FLAG_COUNT,
+                              cudaMemcpyDeviceToHost, s));
+  TGB_CUDA(c, cudaStreamSynchronize(s));
+  return TERSOFF_OK;
+}
+
+// neighbour build with overflow regrow; synchronises s
+int build_list(Ctx* c, const double* x, cudaStream_t s) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    int st = ensure_nbr(c);
+    if (st) return st;
+    TGB_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+    if ((st = launch_neighbor_build(c, x, s))) return st;
+    if ((st = read_flags(c, s))) return st;
+    if (c->h_flags[FLAG_NONFINITE])
+      return fail(c, TERSOFF_E_NONFINITE, "non-finite position in neighbour build");
+    c->max_cnt = c->h_flags[FLAG_OVERFLOW];
+    c->max_short = c->h_flags[FLAG_SHORT_MAX];
+    if (c->max_cnt <= c->cap) {
+      c->have_list = true;
+      c->steps_since_build = 0;
+      return TERSOFF_OK;
+    }
+    // grow with headroom for atoms entering the skin before the next build
+    c->cap = c->max_cnt + c->max_cnt / 4 + 4;
+  }
+  return fail(c, TERSOFF_E_NEIGH_OVERFLOW, "neighbour capacity could not be grown");
+}
+
+int check_ctx(Ctx* c) {
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  TGB_CUDA(c, cudaSetDevice(c->device));
+  return TERSOFF_OK;
+}
+
+}  // namespace
+}  // namespace tgb
+
+using tgb::Ctx;
+
+struct tersoff_ctx {
+  Ctx impl;
+};
+
+static Ctx* C(tersoff_ctx* p) { return p ? &p->impl : nullptr; }
+
+extern "C" {
+
+int tersoff_create(tersoff_ctx** out, int precision) {
+  if (!out) return TERSOFF_E_INVALID_ARG;
+  *out = nullptr;
+  if (!tgb::valid_precision(precision)) return TERSOFF_E_INVALID_ARG;
+  tersoff_ctx* p = new tersoff_ctx();
+  Ctx* c = &p->impl;
+  c->precision = precision;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete p;
+    return TERSOFF_E_CUDA;
+  }
+  if (cudaMalloc(&c->d_flags, sizeof(int) * tgb::FLAG_COUNT) != cudaSuccess ||
+      cudaMallocHost(&c->h_flags, sizeof(int) * tgb::FLAG_COUNT) != cudaSuccess ||
+      cudaMalloc(&c->d_acc, sizeof(double) * 8) != cudaSuccess ||
+      cudaMalloc(&c->d_coef, sizeof(double) * 2 * TERSOFF_MAX_SPECIES) != cudaSuccess) {
+    cudaFree(c->d_flags);
+    cudaFreeHost(c->h_flags);
+    delete p;
+    return TERSOFF_E_CUDA;
+  }
+  cudaMemset(c->d_flags, 0, sizeof(int) * tgb::FLAG_COUNT);
+  cudaMemset(c->d_acc, 0, sizeof(double) * 8);
+  *out = p;
+  return TERSOFF_OK;
+}
+
+int tersoff_destroy(tersoff_ctx* p) {
+  if (!p) return TERSOFF_OK;
+  Ctx* c = &p->impl;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  void* bufs[] = {c->d_rec64, c->d_rec32, c->d_filt64, c->d_filt32, c->d_types, c->d_cnt,
+                  c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
+                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posq,
+                  c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
+                  c->d_coef};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  tgb::fold_timing(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete p;
+  return TERSOFF_OK;
+}
+
+const char* tersoff_last_error(const tersoff_ctx* p) {
+  if (!p) return "null context";
+  return p->impl.err.c_str();
+}
+
+int tersoff_set_precision(tersoff_ctx* p, int precision) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (!tgb::valid_precision(precision))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "precision must be TERSOFF_FP64 or TERSOFF_MIXED");
+  c->precision = precision;
+  return TERSOFF_OK;
+}
+
+int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (ns < 1 || ns > TERSOFF_MAX_SPECIES || !table)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "n_species must be in [1, 4] and table non-null");
+  const int nrec = ns * ns * ns;
+  for (int r = 0; r < nrec; ++r) {
+    const double* t = table + (size_t)r * TERSOFF_NPARAM;
+    for (int f = 0; f < TERSOFF_NPARAM; ++f)
+      if (!std::isfinite(t[f])) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "non-finite parameter");
+    double m = t[TERSOFF_P_M];
+    if (m < 1.0 || m > 16.0 || m != std::floor(m))
+      return tgb::fail(c, TERSOFF_E_INVALID_ARG, "m must be an integer in [1, 16]");
+    if (!(t[TERSOFF_P_D_CUT] > 0.0) || !(t[TERSOFF_P_N] > 0.0) || !(t[TERSOFF_P_D] != 0.0) ||
+        !(t[TERSOFF_P_R] > t[TERSOFF_P_D_CUT]))
+      return tgb::fail(c, TERSOFF_E_INVALID_ARG, "need D > 0, R > D, n > 0, d != 0");
+  }
+  std::vector<double> r64((size_t)nrec * tgb::RSTRIDE, 0.0);
+  std::vector<float> r32((size_t)nrec * tgb::RSTRIDE, 0.0f);
+  bool lam3 = false;
+  for (int r = 0; r < nrec; ++r) {
+    const double* t = table + (size_t)r * TERSOFF_NPARAM;
+    double* o = &r64[(size_t)r * tgb::RSTRIDE];
+    const double gam = t[TERSOFF_P_GAMMA], cc = t[TERSOFF_P_C], dd = t[TERSOFF_P_D];
+    const double R = t[TERSOFF_P_R], D = t[TERSOFF_P_D_CUT];
+    o[tgb::K_GAMMA] = gam;
+    o[tgb::K_GC2D2] = gam * cc * cc / (dd * dd);
+    o[tgb::K_G2C2] = 2.0 * gam * cc * cc;
+    o[tgb::K_D2] = dd * dd;
+    o[tgb::K_H] = t[TERSOFF_P_H];
+    o[tgb::K_LAM3] = t[TERSOFF_P_LAMBDA3];
+    o[tgb::K_M] = t[TERSOFF_P_M];
+    o[tgb::K_R3] = R;
+    o[tgb::K_PID3] = tgb::PI / (2.0 * D);
+    o[tgb::K_DFC3] = -tgb::PI / (4.0 * D);
+    o[tgb::K_RIN3] = R - D;
+    o[tgb::K_ROUT3] = R + D;
+    o[tgb::K_A] = t[TERSOFF_P_A];
+    o[tgb::K_LAM1] = t[TERSOFF_P_LAMBDA1];
+    o[tgb::K_LAM1LO] = 0.0;
+    o[tgb::K_B] = t[TERSOFF_P_B];
+    o[tgb::K_LAM2] = t[TERSOFF_P_LAMBDA2];
+    o[tgb::K_LAM2LO] = 0.0;
+    o[tgb::K_BETA] = t[TERSOFF_P_BETA];
+    o[tgb::K_N] = t[TERSOFF_P_N];
+    o[tgb::K_NINV2] = -1.0 / (2.0 * t[TERSOFF_P_N]);
+    o[tgb::K_R2] = R;
+    o[tgb::K_PID2] = tgb::PI / (2.0 * D);
+    o[tgb::K_DFC2] = -tgb::PI / (4.0 * D);
+    o[tgb::K_RIN2] = R - D;
+    o[tgb::K_ROUT2] = R + D;
+    if (t[TERSOFF_P_LAMBDA3] != 0.0) lam3 = true;
+    float* of = &r32[(size_t)r * tgb::RSTRIDE];
+    for (int k = 0; k < tgb::RSTRIDE; ++k) of[k] = (float)o[k];
+    of[tgb::K_LAM1LO] = (float)(o[tgb::K_LAM1] - (double)of[tgb::K_LAM1]);
+    of[tgb::K_LAM2LO] = (float)(o[tgb::K_LAM2] - (double)of[tgb::K_LAM2]);
+  }
+  // filter radius for (ti, tx): largest outer cutoff of any term in which an
+  // atom of type tx is the bond partner j or the third atom k of a type-ti atom
+  std::vector<double> filt((size_t)ns * ns, 0.0);
+  double rmax = 0.0;
+  for (int ti = 0; ti < ns; ++ti)
+    for (int tx = 0; tx < ns; ++tx) {
+      double rf = r64[(size_t)((ti * ns + tx) * ns + tx) * tgb::RSTRIDE + tgb::K_ROUT2];
+      for (int tj = 0; tj < ns; ++tj)
+        rf = std::fmax(rf, r64[(size_t)((ti * ns + tj) * ns + tx) * tgb::RSTRIDE + tgb::K_ROUT3]);
+      filt[(size_t)ti * ns + tx] = rf;
+      rmax = std::fmax(rmax, rf);
+    }
+  std::vector<double> f64(filt.size());
+  std::vector<float> f32(filt.size());
+  for (size_t q = 0; q < filt.size(); ++q) {
+    // a little above the radius so that rounding never drops a contributing atom
+    double r = filt[q] * (1.0 + 1e-6);
+    f64[q] = r * r;
+    f32[q] = (float)(r * r);
+  }
+  if ((st = tgb::dev_alloc(c, &c->d_rec64, r64.size()))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_rec32, r32.size()))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_filt64, f64.size()))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_filt32, f32.size()))) return st;
+  TGB_CUDA(c, cudaMemcpy(c->d_rec64, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
+  TGB_CUDA(c, cudaMemcpy(c->d_rec32, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
+  TGB_CUDA(c, cudaMemcpy(c->d_filt64, f64.data(), sizeof(double) * f64.size(), cudaMemcpyHostToDevice));
+  TGB_CUDA(c, cudaMemcpy(c->d_filt32, f32.data(), sizeof(float) * f32.size(), cudaMemcpyHostToDevice));
+  c->ns = ns;
+  c->table.assign(table, table + (size_t)nrec * TERSOFF_NPARAM);
+  c->filt = filt;
+  c->has_lam3 = lam3;
+  c->rmax_cut = rmax;
+  c->have_list = false;
+  return TERSOFF_OK;
+}
+
+int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, int n,
+                           const double* box, double r_list, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (c->ns == 0) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_params must come first");
+  if (n < 0 || n > tgb::MAX_ATOMS || (n > 0 && (!x || !types)) || !box)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad atom arrays or count (max 2^26 atoms)");
+  if (!(r_list > 0.0) || !std::isfinite(r_list))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "r_list must be positive");
+  if (r_list < c->rmax_cut)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "r_list is below the potential's cutoff");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = tgb::setup_grid(c, box, r_list))) return st;
+  c->n = n;
+  c->r_list = r_list;
+  c->have_list = false;
+  if ((st = tgb::ensure_atoms(c, n))) return st;
+  if (n > 0)
+    TGB_CUDA(c, cudaMemcpyAsync(c->d_types, types, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+  // species range check on the device copy is folded into the build kernels'
+  // parameter lookups; validate here on a host copy for clear errors
+  if (n > 0) {
+    std::vector<int> ht(n);
+    TGB_CUDA(c, cudaMemcpyAsync(ht.data(), types, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+    TGB_CUDA(c, cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i)
+      if (ht[i] < 0 || ht[i] >= c->ns)
+        return tgb::fail(c, TERSOFF_E_INVALID_ARG, "species index out of range");
+  }
+  return tgb::build_list(c, x, s);
+}
+
+int tersoff_neighbor_capacity(const tersoff_ctx* p, int* capacity, int* max_count) {
+  if (!p) return TERSOFF_E_INVALID_ARG;
+  if (capacity) *capacity = p->impl.cap;
+  if (max_count) *max_count = p->impl.max_cnt;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_neighbor_capacity(tersoff_ctx* p, int capacity) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (capacity < 1 || capacity > 4096)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "capacity must be in [1, 4096]");
+  c->cap = capacity;
+  c->have_list = false;
+  return TERSOFF_OK;
+}
+
+int tersoff_neighbor_export(tersoff_ctx* p, int* cnt, int* nbr, int cap, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "no neighbour list");
+  if (cap < 1 || (c->n > 0 && (!cnt || !nbr)))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad export buffers");
+  if ((st = tgb::launch_neighbor_export(c, cnt, nbr, cap, (cudaStream_t)stream))) return st;
+  if (c->max_cnt > cap)
+    return tgb::fail(c, TERSOFF_E_NEIGH_OVERFLOW, "export capacity below the largest count");
+  return TERSOFF_OK;
+}
+
+static int compute_impl(Ctx* c, const double* x, int n, double* energy, double* forces,
+                        double* virial, double* eatom, cudaStream_t s) {
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (n != c->n || (n > 0 && !x))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
+  double* f = forces ? forces : c->d_fbuf;
+  if ((st = tgb::launch_pack_positions(c, x, s))) return st;
+  if (n > 0) TGB_CUDA(c, cudaMemsetAsync(f, 0, sizeof(double) * 3 * (size_t)n, s));
+  TGB_CUDA(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * 8, s));
+  {
+    tgb::TimedRegion tr(c, 0, s);
+    if ((st = tgb::launch_forward(c, f, c->d_acc, eatom, s))) return st;
+  }
+  if (energy)
+    TGB_CUDA(c, cudaMemcpyAsync(energy, c->d_acc, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (virial)
+    TGB_CUDA(c, cudaMemcpyAsync(virial, c->d_acc + 1, sizeof(double) * 6,
+                                cudaMemcpyDeviceToDevice, s));
+  return TERSOFF_OK;
+}
+
+int tersoff_compute(tersoff_ctx* p, const double* x, int n, double* energy, double* forces,
+                    double* virial, void* stream) {
+  return compute_impl(C(p), x, n, energy, forces, virial, nullptr, (cudaStream_t)stream);
+}
+
+int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eatom,
+                            void* stream) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (!eatom && n > 0) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "eatom is null");
+  return compute_impl(c, x, n, nullptr, nullptr, nullptr, eatom, (cudaStream_t)stream);
+}
+
+static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double* mass,
+                   double dt, int nsteps, int rebuild_every, double* thermo, cudaStream_t s) {
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (n != c->n || (n > 0 && (!x || !v || !f)) || !mass || nsteps < 0 || rebuild_every < 0 ||
+      !(dt > 0.0) || !std::isfinite(dt))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad MD arguments");
+  for (int t = 0; t < c->ns; ++t)
+    if (!(mass[t] > 0.0)) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "masses must be positive");
+  if (n == 0 || nsteps == 0) return TERSOFF_OK;
+  // per-species dt/2 * FTM2V / m and masses, kept in the accumulator tail
+  double hc[2 * TERSOFF_MAX_SPECIES];
+  for (int t = 0; t < c->ns; ++t) {
+    hc[t] = 0.5 * dt * tgb::FTM2V / mass[t];
+    hc[TERSOFF_MAX_SPECIES + t] = mass[t];
+  }
+  TGB_CUDA(c, cudaMemcpyAsync(c->d_coef, hc, sizeof(hc), cudaMemcpyHostToDevice, s));
+  const double* cdt = c->d_coef;
+  const double* dmass = c->d_coef + TERSOFF_MAX_SPECIES;
+  TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_FALLBACK, 0, sizeof(int), s));
+  for (int step = 0; step < nsteps; ++step) {
+    c->steps_since_build++;
+    const bool rebuild = rebuild_every > 0 && c->steps_since_build >= rebuild_every;
+    {
+      tgb::TimedRegion tr(c, 2, s);
+      if ((st = tgb::launch_kick_drift(c, x, v, f, cdt, dt, !rebuild, s))) break;
+    }
+    if (rebuild) {
+      {
+        tgb::TimedRegion tr(c, 1, s);
+        st = tgb::build_list(c, x, s);
+      }
+      if (st) break;
+      c->steps_since_build = 0;
+      if ((st = tgb::launch_pack_positions(c, x, s))) break;
+    }
+    {
+      tgb::TimedRegion tr(c, 0, s);
+      if ((st = tgb::launch_forward(c, f, c->d_acc, nullptr, s))) break;
+    }
+    {
+      tgb::TimedRegion tr(c, 2, s);
+      if ((st = tgb::launch_kick(c, v, f, cdt, dmass, thermo != nullptr, s))) break;
+    }
+    if (thermo && (st = tgb::launch_thermo(c, tgb::MVV2E, thermo + 3 * (size_t)step, s))) break;
+  }
+  if (st) return st;
+  TGB_CUDA(c, cudaStreamSynchronize(s));
+  return TERSOFF_OK;
+}
+
+int tersoff_md_step(tersoff_ctx* p, double* x, double* v, double* f, int n, const double* mass,
+                    double dt, int nsteps, int rebuild_every, double* thermo, void* stream) {
+  return md_impl(C(p), x, v, f, n, mass, dt, nsteps, rebuild_every, thermo,
+                 (cudaStream_t)stream);
+}
+
+int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
+                         const double* mass, double dt, int nsteps, int rebuild_every,
+                         double* thermo, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (n != c->n || (n > 0 && (!x || !v || !f)))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad MD arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t m = 3 * (size_t)n;
+  if (c->stage_alloc < 3 * m) {
+    if ((st = tgb::dev_alloc(c, &c->d_stage, 3 * m))) return st;
+    c->stage_alloc = 3 * m;
+  }
+  if (thermo && c->thermo_alloc < 3 * (size_t)nsteps) {
+    if ((st = tgb::dev_alloc(c, &c->d_thermo, 3 * (size_t)nsteps))) return st;
+    c->thermo_alloc = 3 * (size_t)nsteps;
+  }
+  double *dx = c->d_stage, *dv = c->d_stage + m, *df = c->d_stage + 2 * m;
+  TGB_CUDA(c, cudaMemcpyAsync(dx, x, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  TGB_CUDA(c, cudaMemcpyAsync(dv, v, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  TGB_CUDA(c, cudaMemcpyAsync(df, f, sizeof(double) * m, cudaMemcpyHostToDevice, s));
+  st = md_impl(c, dx, dv, df, n, mass, dt, nsteps, rebuild_every, thermo ? c->d_thermo : nullptr,
+               s);
+  if (st) return st;
+  TGB_CUDA(c, cudaMemcpyAsync(x, dx, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  TGB_CUDA(c, cudaMemcpyAsync(v, dv, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  TGB_CUDA(c, cudaMemcpyAsync(f, df, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  if (thermo)
+    TGB_CUDA(c, cudaMemcpyAsync(thermo, c->d_thermo, sizeof(double) * 3 * nsteps,
+                                cudaMemcpyDeviceToHost, s));
+  TGB_CUDA(c, cudaStreamSynchronize(s));
+  return TERSOFF_OK;
+}
+
+int tersoff_launch_count(const tersoff_ctx* p, long long* count) {
+  if (!p || !count) return TERSOFF_E_INVALID_ARG;
+  *count = p->impl.launches;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_timing(tersoff_ctx* p, int enable) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  tgb::fold_timing(c);
+  c->timing = enable != 0;
+  for (int k = 0; k < 3; ++k) {
+    c->t_ms[k] = 0.0;
+    c->t_count[k] = 0;
+  }
+  return TERSOFF_OK;
+}
+
+int tersoff_timing(tersoff_ctx* p, int kind, double* total_ms, long long* launches) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (kind < 0 || kind > 2) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "kind must be 0, 1 or 2");
+  tgb::fold_timing(c);
+  if (total_ms) *total_ms = c->t_ms[kind];
+  if (launches) *launches = c->t_count[kind];
+  return TERSOFF_OK;
+}
+
+}  // extern "C"

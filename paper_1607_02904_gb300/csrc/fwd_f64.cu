@@ -1,0 +1,14 @@
+// FP64 instances of the force kernel.
+#include "fwd_launch.cuh"
+
+namespace tgb {
+int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
+  return fwd::launch_prec<double>(c, f, acc, eatom, s);
+}
+
+int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
+  if (c->n == 0) return TERSOFF_OK;
+  if (c->precision == TERSOFF_MIXED) return launch_forward_f32(c, f, acc, eatom, s);
+  return launch_forward_f64(c, f, acc, eatom, s);
+}
+}  // namespace tgb

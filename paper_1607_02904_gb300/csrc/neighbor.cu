@@ -1,0 +1,348 @@
+// Cell-binned full neighbour lists (Sec. II Eq. 4; skin of Sec. III).
+//
+// Pipeline, all on the caller's stream:
+//   k_bin      atom -> cell (wrapped position), per-atom origin o_i, FP32 offset
+//   scan       exclusive prefix sum of cell counts (three kernels)
+//   k_scatter  atoms grouped by cell
+//   k_neigh    one thread per atom scans the 27 stencil cells; candidates far from
+//              the cutoff are classified in FP32 from cell-relative offsets, those
+//              within a safety band of it by the exact FP64 minimum-image test
+//              (same operation sequence as the definition); entries are then
+//              sorted by neighbour index.
+// An entry stores j and the stencil cell offset; with u_i = x_i - o_i the bond
+// vector is  x_j(image) - x_i = (u_j - u_i) + off * h.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace tgb {
+namespace {
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+struct GridDev {
+  int nc[3];
+  double L[3], invL[3], h[3], invh[3];
+  float hf[3];
+};
+
+GridDev to_dev(const Grid& g) {
+  GridDev d;
+  for (int a = 0; a < 3; ++a) {
+    d.nc[a] = g.nc[a];
+    d.L[a] = g.L[a];
+    d.invL[a] = g.invL[a];
+    d.h[a] = g.h[a];
+    d.invh[a] = g.invh[a];
+    d.hf[a] = (float)g.h[a];
+  }
+  return d;
+}
+
+__global__ void k_bin(int n, const double* __restrict__ x, const int* __restrict__ types,
+                      GridDev g, int* __restrict__ cell_of, int* __restrict__ cell_count,
+                      double* __restrict__ origin, float4* __restrict__ pos32,
+                      int* __restrict__ flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c3[3];
+  float uf[3];
+  bool finite = true;
+  for (int a = 0; a < 3; ++a) {
+    double xa = x[3 * (size_t)i + a];
+    if (!isfinite(xa)) {
+      finite = false;
+      xa = 0.0;
+    }
+    double w = xa - g.L[a] * floor(xa * g.invL[a]);
+    int c = (int)(w * g.invh[a]);
+    c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+    double u = w - c * g.h[a];
+    origin[3 * (size_t)i + a] = xa - u;
+    uf[a] = (float)u;
+    c3[a] = c;
+  }
+  if (!finite) atomicOr(&flags[FLAG_NONFINITE], 1);
+  int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+  cell_of[i] = cell;
+  atomicAdd(&cell_count[cell], 1);
+  pos32[i] = make_float4(uf[0], uf[1], uf[2], __int_as_float(types[i]));
+}
+
+// --- exclusive scan over m ints (three passes) ---
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) >= o) v += t;
+  }
+  return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns exclusive prefix, *total
+__device__ int block_excl_scan(int v, int* total) {
+  __shared__ int wsum[SCAN_BLOCK / 32];
+  __shared__ int wtotal;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    int s = lane < nw ? wsum[lane] : 0;
+    int si = warp_incl_scan(s);
+    if (lane < nw) wsum[lane] = si - s;
+    if (lane == nw - 1) wtotal = si;
+  }
+  __syncthreads();
+  int res = incl - v + wsum[wid];
+  if (total) *total = wtotal;
+  __syncthreads();
+  return res;
+}
+
+__global__ void k_scan_tiles(const int* __restrict__ in, int m, int* __restrict__ out,
+                             int* __restrict__ tile_sums) {
+  int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  int s = 0;
+  for (int q = 0; q < SCAN_ITEMS; ++q) {
+    v[q] = (base + q < m) ? in[base + q] : 0;
+    s += v[q];
+  }
+  int total;
+  int pre = block_excl_scan(s, &total);
+  for (int q = 0; q < SCAN_ITEMS; ++q) {
+    if (base + q < m) out[base + q] = pre;
+    pre += v[q];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of the tile sums in place
+__global__ void k_scan_sums(int* __restrict__ sums, int nt) {
+  int carry = 0;
+  for (int base = 0; base < nt; base += SCAN_BLOCK) {
+    int idx = base + threadIdx.x;
+    int v = idx < nt ? sums[idx] : 0;
+    int total;
+    int pre = block_excl_scan(v, &total);
+    if (idx < nt) sums[idx] = pre + carry;
+    carry += total;
+  }
+}
+
+__global__ void k_scan_add(int* __restrict__ out, int m, const int* __restrict__ tile_off,
+                           int* __restrict__ fill) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= m) return;
+  int v = out[idx] + tile_off[idx / SCAN_TILE];
+  out[idx] = v;
+  if (fill) fill[idx] = v;
+}
+
+__global__ void k_scatter(int n, const int* __restrict__ cell_of, int* __restrict__ fill,
+                          int* __restrict__ cell_atoms) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int slot = atomicAdd(&fill[cell_of[i]], 1);
+  cell_atoms[slot] = i;
+}
+
+// Exact membership test (the definition's operation sequence, no FMA).
+__device__ __forceinline__ bool exact_member(const double* __restrict__ x, int i, int j,
+                                             const GridDev& g, double rc2, float dx32,
+                                             float dy32, float dz32) {
+  double d[3];
+  float st[3] = {dx32, dy32, dz32};
+  for (int a = 0; a < 3; ++a) {
+    double dd = __dsub_rn(x[3 * (size_t)j + a], x[3 * (size_t)i + a]);
+    dd = __dsub_rn(dd, __dmul_rn(g.L[a], rint(__dmul_rn(dd, g.invL[a]))));
+    d[a] = dd;
+    // the stencil image must be the minimum image (relevant when a box edge
+    // holds only two cells and two images of j are visited)
+    if (fabs((double)st[a] - dd) > 0.5 * g.L[a]) return false;
+  }
+  double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
+                        __dmul_rn(d[2], d[2]));
+  return r2 <= rc2;
+}
+
+template <int NS>
+__global__ void __launch_bounds__(128) k_neigh(
+    int n, const double* __restrict__ x, const float4* __restrict__ pos32,
+    const int* __restrict__ cell_of, const int* __restrict__ cell_start,
+    const int* __restrict__ cell_atoms, GridDev g, double rc2, float lo2, float hi2,
+    const float* __restrict__ filt2, int cap, uint32_t* __restrict__ nbr,
+    int* __restrict__ cnt, int* __restrict__ flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float4 pi = pos32[i];
+  const int ti = __float_as_int(pi.w);
+  const int ci = cell_of[i];
+  const int cx = ci % g.nc[0];
+  const int cy = (ci / g.nc[0]) % g.nc[1];
+  const int cz = ci / (g.nc[0] * g.nc[1]);
+  int count = 0, nshort = 0;
+  for (int oz = -1; oz <= 1; ++oz) {
+    int az = cz + oz;
+    az += (az < 0) ? g.nc[2] : 0;
+    az -= (az >= g.nc[2]) ? g.nc[2] : 0;
+    for (int oy = -1; oy <= 1; ++oy) {
+      int ay = cy + oy;
+      ay += (ay < 0) ? g.nc[1] : 0;
+      ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
+      for (int ox = -1; ox <= 1; ++ox) {
+        int ax = cx + ox;
+        ax += (ax < 0) ? g.nc[0] : 0;
+        ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
+        const int c = (az * g.nc[1] + ay) * g.nc[0] + ax;
+        const float sx = ox * g.hf[0], sy = oy * g.hf[1], sz = oz * g.hf[2];
+        const uint32_t code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) |
+                              ((uint32_t)(oz + 1) << 30);
+        const int s1 = cell_start[c + 1];
+        for (int s = cell_start[c]; s < s1; ++s) {
+          const int j = cell_atoms[s];
+          if (j == i) continue;
+          const float4 pj = pos32[j];
+          const float dx = (pj.x - pi.x) + sx;
+          const float dy = (pj.y - pi.y) + sy;
+          const float dz = (pj.z - pi.z) + sz;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          bool in;
+          if (r2 < lo2)
+            in = true;
+          else if (r2 > hi2)
+            in = false;
+          else
+            in = exact_member(x, i, j, g, rc2, dx, dy, dz);
+          if (in) {
+            if (count < cap) nbr[(size_t)count * n + i] = (uint32_t)j | code;
+            ++count;
+            const int tj = __float_as_int(pj.w);
+            if (r2 <= filt2[ti * NS + tj]) ++nshort;
+          }
+        }
+      }
+    }
+  }
+  cnt[i] = count;
+  atomicMax(&flags[FLAG_OVERFLOW], count);
+  atomicMax(&flags[FLAG_SHORT_MAX], nshort);
+  // insertion sort of the stored entries by neighbour index
+  const int m = count < cap ? count : cap;
+  for (int a = 1; a < m; ++a) {
+    const uint32_t key = nbr[(size_t)a * n + i];
+    const uint32_t kj = key & ENTRY_JMASK;
+    int b = a - 1;
+    while (b >= 0) {
+      const uint32_t eb = nbr[(size_t)b * n + i];
+      if ((eb & ENTRY_JMASK) <= kj) break;
+      nbr[(size_t)(b + 1) * n + i] = eb;
+      --b;
+    }
+    nbr[(size_t)(b + 1) * n + i] = key;
+  }
+}
+
+__global__ void k_export(int n, const uint32_t* __restrict__ nbr, const int* __restrict__ cnt,
+                         int cap_in, int cap_out, int* __restrict__ out_cnt,
+                         int* __restrict__ out_nbr) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = cnt[i];
+  out_cnt[i] = c;
+  int m = c < cap_in ? c : cap_in;
+  for (int s = 0; s < cap_out; ++s)
+    out_nbr[(size_t)i * cap_out + s] = (s < m) ? (int)(nbr[(size_t)s * n + i] & ENTRY_JMASK) : -1;
+}
+
+template <class T>
+int grow(Ctx* c, T** p, size_t* have, size_t need) {
+  if (*have >= need && *p) return TERSOFF_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  TGB_CUDA(c, cudaMalloc((void**)p, sizeof(T) * need));
+  *have = need;
+  return TERSOFF_OK;
+}
+
+}  // namespace
+
+int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
+  const int n = c->n;
+  const Grid& G = c->grid;
+  const long ncell = (long)G.nc[0] * G.nc[1] * G.nc[2];
+  // cell arrays
+  if (c->cells_alloc < (size_t)ncell + 1) {
+    cudaFree(c->d_cell_count);
+    cudaFree(c->d_cell_start);
+    cudaFree(c->d_cell_fill);
+    cudaFree(c->d_scan_tmp);
+    c->d_cell_count = c->d_cell_start = c->d_cell_fill = c->d_scan_tmp = nullptr;
+    size_t m = (size_t)ncell + 1;
+    TGB_CUDA(c, cudaMalloc(&c->d_cell_count, sizeof(int) * m));
+    TGB_CUDA(c, cudaMalloc(&c->d_cell_start, sizeof(int) * m));
+    TGB_CUDA(c, cudaMalloc(&c->d_cell_fill, sizeof(int) * m));
+    TGB_CUDA(c, cudaMalloc(&c->d_scan_tmp, sizeof(int) * (m / SCAN_TILE + 2)));
+    c->cells_alloc = m;
+  }
+  GridDev g = to_dev(G);
+  const int B = 256;
+  const int nb = (n + B - 1) / B;
+  TGB_CUDA(c, cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (ncell + 1), s));
+  if (n > 0) {
+    k_bin<<<nb, B, 0, s>>>(n, x, c->d_types, g, c->d_cell_of, c->d_cell_count, c->d_origin,
+                           c->d_pos32, c->d_flags);
+    c->launches++;
+  }
+  const int m = (int)ncell + 1;
+  const int ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<ntiles, SCAN_BLOCK, 0, s>>>(c->d_cell_count, m, c->d_cell_start, c->d_scan_tmp);
+  k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(c->d_scan_tmp, ntiles);
+  k_scan_add<<<(m + 255) / 256, 256, 0, s>>>(c->d_cell_start, m, c->d_scan_tmp, c->d_cell_fill);
+  c->launches += 3;
+  if (n > 0) {
+    k_scatter<<<nb, B, 0, s>>>(n, c->d_cell_of, c->d_cell_fill, c->d_cell_atoms);
+    c->launches++;
+  }
+  const double rc2 = c->r_list * c->r_list;
+  // FP32 classification band: the FP32 r^2 of a stencil candidate differs from
+  // the exact value by far less than this (offsets below 2 cells, float eps).
+  const double hmax = fmax(G.h[0], fmax(G.h[1], G.h[2]));
+  const double band = 64.0 * (4.0 * hmax) * (4.0 * hmax) * 1.2e-7 + 1e-6;
+  const float lo2 = (float)(rc2 - band);
+  const float hi2 = (float)(rc2 + band);
+  if (n > 0) {
+    switch (c->ns) {
+#define TGB_NEIGH(NSV)                                                                     \
+  case NSV:                                                                                \
+    k_neigh<NSV><<<(n + 127) / 128, 128, 0, s>>>(n, x, c->d_pos32, c->d_cell_of,          \
+                                                 c->d_cell_start, c->d_cell_atoms, g, rc2, \
+                                                 lo2, hi2, c->d_filt32, c->cap, c->d_nbr,  \
+                                                 c->d_cnt, c->d_flags);                    \
+    break;
+      TGB_NEIGH(1)
+      TGB_NEIGH(2)
+      TGB_NEIGH(3)
+      TGB_NEIGH(4)
+#undef TGB_NEIGH
+      default:
+        return fail(c, TERSOFF_E_STATE, "unsupported species count");
+    }
+    c->launches++;
+  }
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+int launch_neighbor_export(Ctx* c, int* cnt, int* nbr, int cap, cudaStream_t s) {
+  if (c->n == 0) return TERSOFF_OK;
+  k_export<<<(c->n + 255) / 256, 256, 0, s>>>(c->n, c->d_nbr, c->d_cnt, c->cap, cap, cnt, nbr);
+  c->launches++;
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+}  // namespace tgb

@@ -1,0 +1,545 @@
+// Fused Tersoff energy / force / virial kernel (Sec. III Eq. 5-7, Sec. IV).
+//
+// One thread per centre atom i (the GPU mapping of Sec. IV-B, scheme (c)).
+//  1. Filter (Sec. IV-B "filter component", Sec. IV-D): the thread scans its
+//     skin list S_i and marks the entries within the largest cutoff that any
+//     term of (type i, type j) can use; the marks form a bit mask.
+//  2. Fast path, when the short list fits the compile-time capacity ZC: the
+//     short list is loaded into registers (bond vectors, lengths, unit
+//     vectors); for every j the first K loop accumulates zeta_ij together with
+//     its derivatives with respect to x_j and every x_k (the pre-computed
+//     derivatives of Sec. IV-A, kept in registers), then b_ij, V and
+//     dV/dzeta are formed and the forces are applied. Forces on the
+//     neighbours accumulate in registers; the force on i and the virial follow
+//     from them at the end (every term's forces sum to zero, and all of atom
+//     i's terms are centred on i).
+//  3. General path (short list longer than ZC, the fall-back of Sec. IV-A):
+//     Algorithm 2's loop order directly over S_i with the cutoff test inside
+//     the loops, forces scattered per term.
+// Forces are scattered with FP64 atomics (global sums in double); energy and
+// virial are reduced in the warp, and across warps and blocks in double.
+//
+// Arithmetic: T = double for the FP64 path. T = float for the mixed path;
+// there bond vectors come from exact integer differences of fixed-point
+// positions, reciprocal square roots and reciprocals get one Newton step,
+// and the exponent arguments of f_R, f_A carry the rounding residual of
+// lambda * r, so each term is accurate to a few float ulps.
+#pragma once
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace tgb {
+namespace fwd {
+
+constexpr int BLOCK = 128;
+
+// float -> double through the IEEE-754 bit layouts (exact; float subnormals
+// flush to signed zero). Integer operations only.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t mag = u & 0x7fffffffu;
+  uint32_t hi = (mag >> 3) + 0x38000000u;  // exponent rebias 127 -> 1023
+  uint32_t lo = mag << 29;
+  const bool tiny = mag < 0x00800000u;
+  hi = tiny ? 0u : hi;
+  lo = tiny ? 0u : lo;
+  hi = (mag >= 0x7f800000u) ? ((mag >> 3) | 0x7ff00000u) : hi;  // inf / nan
+  return __hiloint2double((int)(hi | sign), (int)lo);
+}
+__device__ __forceinline__ double to_f64(float v) { return f2d_bits(v); }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+
+// ---------------------------------------------------------------- math per precision
+template <class T> struct M;
+
+template <> struct M<float> {
+  // reciprocal square root with one Newton step on 1/y^2 = x
+  static __device__ __forceinline__ float rsqrt_nr(float x) {
+    float y = rsqrtf(x);
+    float e = fmaf(-x * y, y, 1.0f);
+    return fmaf(0.5f * y, e, y);
+  }
+  // reciprocal with one Newton step on 1/y = x
+  static __device__ __forceinline__ float rcp_nr(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    float e = fmaf(-x, y, 1.0f);
+    return fmaf(y, e, y);
+  }
+  // exp(-(lh + ll) r) with the rounding residual of lh*r folded in
+  static __device__ __forceinline__ float exp_neg_lr(float lh, float ll, float r) {
+    float a = lh * r;
+    float res = fmaf(lh, r, -a) + ll * r;
+    return expf(-a) * (1.0f - res);
+  }
+  static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+  static __device__ __forceinline__ void sincospi_(float x, float* s, float* c) {
+    sincospif(x, s, c);
+  }
+  // b = (1 + (beta zeta)^n)^(-1/(2n)),  db/dzeta
+  static __device__ __forceinline__ void bond(float zeta, float beta, float n, float ninv2,
+                                              float& b, float& db) {
+    if (zeta > 0.0f) {
+      float u = exp2f(n * log2f(beta * zeta));
+      float opu = 1.0f + u;
+      b = exp2f(ninv2 * log2f(opu));
+      db = -0.5f * b * u * rcp_nr(opu * zeta);
+    } else {
+      b = 1.0f;
+      db = 0.0f;
+    }
+  }
+};
+
+template <> struct M<double> {
+  static __device__ __forceinline__ double rsqrt_nr(double x) { return rsqrt(x); }
+  static __device__ __forceinline__ double rcp_nr(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double exp_neg_lr(double lh, double, double r) {
+    return exp(-lh * r);
+  }
+  static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+  static __device__ __forceinline__ void sincospi_(double x, double* s, double* c) {
+    sincospi(x, s, c);
+  }
+  static __device__ __forceinline__ void bond(double zeta, double beta, double n, double ninv2,
+                                              double& b, double& db) {
+    if (zeta > 0.0) {
+      double u = exp(n * log(beta * zeta));
+      double opu = 1.0 + u;
+      b = exp(ninv2 * log1p(u));
+      db = -0.5 * b * u / (opu * zeta);
+    } else {
+      b = 1.0;
+      db = 0.0;
+    }
+  }
+};
+
+// ---------------------------------------------------------------- arguments
+template <class T> struct FwdArgs {
+  int n, cap;
+  int ns;                // species count (used when the kernel's NS is 0)
+  const uint32_t* nbr;   // slot-major skin list
+  const int* cnt;
+  const float4* pos32;   // mixed: (u, type bits)
+  const int4* posq;      // mixed: fixed-point u, type
+  const dpos4* pos64;  // fp64: (u, type)
+  const T* rec;          // ns^3 derived records
+  const T* filt2;        // ns x ns squared filter radii
+  T h[3];                // cell edges
+  int hq[3];             // cell edges in fixed point
+  float qinv;            // 2^-fix_shift
+  double* f;             // forces, accumulated
+  double* acc;           // energy, virial (6)
+  double* eatom;         // optional per-atom energy
+  int* flags;
+};
+
+// position of atom j relative to its origin, in T, and its species
+template <class T> struct Pos;
+template <> struct Pos<float> {
+  // filter precision (cheap): float offsets
+  static __device__ __forceinline__ void coarse(const FwdArgs<float>& a, int j, float& x,
+                                                float& y, float& z, int& t) {
+    float4 p = __ldg(&a.pos32[j]);
+    x = p.x;
+    y = p.y;
+    z = p.z;
+    t = __float_as_int(p.w);
+  }
+};
+template <> struct Pos<double> {
+  static __device__ __forceinline__ void coarse(const FwdArgs<double>& a, int j, double& x,
+                                                double& y, double& z, int& t) {
+    dpos4 p = a.pos64[j];
+    x = p.x;
+    y = p.y;
+    z = p.z;
+    t = (int)p.w;
+  }
+};
+
+__device__ __forceinline__ void decode(uint32_t e, int& j, int& ox, int& oy, int& oz) {
+  j = (int)(e & ENTRY_JMASK);
+  ox = (int)((e >> 26) & 3u) - 1;
+  oy = (int)((e >> 28) & 3u) - 1;
+  oz = (int)(e >> 30) - 1;
+}
+
+// Accurate bond vector from i to entry e's image of j.
+template <class T> struct Bond;
+template <> struct Bond<float> {
+  static __device__ __forceinline__ void vec(const FwdArgs<float>& a, int4 qi, uint32_t e,
+                                             float& dx, float& dy, float& dz, int& j, int& tj) {
+    int ox, oy, oz;
+    decode(e, j, ox, oy, oz);
+    int4 qj = __ldg(&a.posq[j]);
+    int ix = qj.x - qi.x + ox * a.hq[0];
+    int iy = qj.y - qi.y + oy * a.hq[1];
+    int iz = qj.z - qi.z + oz * a.hq[2];
+    dx = (float)ix * a.qinv;
+    dy = (float)iy * a.qinv;
+    dz = (float)iz * a.qinv;
+    tj = qj.w;
+  }
+};
+template <> struct Bond<double> {
+  static __device__ __forceinline__ void vec(const FwdArgs<double>& a, dpos4 pi, uint32_t e,
+                                             double& dx, double& dy, double& dz, int& j,
+                                             int& tj) {
+    int ox, oy, oz;
+    decode(e, j, ox, oy, oz);
+    dpos4 pj = a.pos64[j];
+    dx = (pj.x - pi.x) + ox * a.h[0];
+    dy = (pj.y - pi.y) + oy * a.h[1];
+    dz = (pj.z - pi.z) + oz * a.h[2];
+    tj = (int)pj.w;
+  }
+};
+
+template <class T> struct SelfPos;
+template <> struct SelfPos<float> { using type = int4; };
+template <> struct SelfPos<double> { using type = dpos4; };
+
+template <class T>
+__device__ __forceinline__ typename SelfPos<T>::type self_pos(const FwdArgs<T>& a, int i);
+template <>
+__device__ __forceinline__ int4 self_pos<float>(const FwdArgs<float>& a, int i) {
+  return __ldg(&a.posq[i]);
+}
+template <>
+__device__ __forceinline__ dpos4 self_pos<double>(const FwdArgs<double>& a, int i) {
+  return a.pos64[i];
+}
+
+// ---------------------------------------------------------------- term pieces
+// f_C and its derivative (Tersoff's cutoff), fields at offsets R, PID, DFC, RIN
+template <class T>
+__device__ __forceinline__ void cutoff(const T* p, int kR, int kPID, int kDFC, int kRIN, T r,
+                                       T& fc, T& dfc) {
+  if (r <= p[kRIN]) {
+    fc = T(1);
+    dfc = T(0);
+  } else {
+    T s, c;
+    // sin(pi/2 (r-R)/D) = sinpi((r-R)/(2D)); p[kPID] = pi/(2D) so divide by pi
+    M<T>::sincospi_((r - p[kR]) * p[kPID] * T(0.31830988618379067), &s, &c);
+    fc = T(0.5) - T(0.5) * s;
+    dfc = p[kDFC] * c;
+  }
+}
+
+// one three-body term zeta(i,j,k) and the coefficients of its derivative:
+//   d zeta = A1 d(cos) + A2 d(r_ij) + (A3 - A2) d(r_ik)
+template <class T, bool LAM3>
+__device__ __forceinline__ void triplet(const T* p3, T rij, T rik, T cs, T& zt, T& A1, T& A2,
+                                        T& A3) {
+  T fc, dfc;
+  cutoff<T>(p3, K_R3, K_PID3, K_DFC3, K_RIN3, rik, fc, dfc);
+  const T t = p3[K_H] - cs;
+  const T t2 = t * t;
+  const T q = M<T>::rcp_nr(p3[K_D2] + t2);
+  const T g = p3[K_GC2D2] * (t2 * q) + p3[K_GAMMA];
+  const T dg = -p3[K_G2C2] * t * q * q;
+  T ex = T(1), dex = T(0);
+  if (LAM3) {
+    const T l3 = p3[K_LAM3];
+    const int m = (int)p3[K_M];
+    const T aa = l3 * (rij - rik);
+    T am1 = T(1);
+    for (int s = 1; s < m; ++s) am1 *= aa;
+    ex = M<T>::exp_(am1 * aa);
+    dex = ex * T(m) * l3 * am1;
+  }
+  const T fg = fc * g;
+  zt = fg * ex;
+  A1 = fc * dg * ex;
+  A2 = fg * dex;
+  A3 = dfc * g * ex;
+}
+
+// pair part: V = 1/2 fc (fR + b fA), dV/dr, dV/dzeta
+template <class T>
+__device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, T& dz) {
+  T b, db;
+  M<T>::bond(zeta, p2[K_BETA], p2[K_N], p2[K_NINV2], b, db);
+  T fc, dfc;
+  cutoff<T>(p2, K_R2, K_PID2, K_DFC2, K_RIN2, rij, fc, dfc);
+  const T er = M<T>::exp_neg_lr(p2[K_LAM1], p2[K_LAM1LO], rij);
+  const T ea = M<T>::exp_neg_lr(p2[K_LAM2], p2[K_LAM2LO], rij);
+  const T fr = p2[K_A] * er;
+  const T fa = -p2[K_B] * ea;
+  const T s = fr + b * fa;
+  V = T(0.5) * fc * s;
+  // d/dr [fc (fR + b fA)] at fixed b: fR' = -l1 fR, fA' = -l2 fA
+  dVdr = T(0.5) * (dfc * s - fc * (p2[K_LAM1] * fr + p2[K_LAM2] * b * fa));
+  dz = T(0.5) * fc * fa * db;
+}
+
+__device__ __forceinline__ void atomic_add3(double* f, int j, double a, double b, double c) {
+  atomicAdd(f + 3 * (size_t)j + 0, a);
+  atomicAdd(f + 3 * (size_t)j + 1, b);
+  atomicAdd(f + 3 * (size_t)j + 2, c);
+}
+
+// ---------------------------------------------------------------- general path
+// Algorithm 2 directly over S_i, cutoff tests inside the loops.
+template <class T, int NS, bool LAM3>
+__device__ __noinline__ void general_atom(const FwdArgs<T>& a, const T* srec, int i, int ti,
+                                          T& ei, T* w) {
+  using P = typename SelfPos<T>::type;
+  const int ns = NS > 0 ? NS : a.ns;
+  const P pi = self_pos<T>(a, i);
+  const int c = min(a.cnt[i], a.cap);
+  T fix = 0, fiy = 0, fiz = 0;
+  for (int sj = 0; sj < c; ++sj) {
+    T dxj, dyj, dzj;
+    int j, tj;
+    Bond<T>::vec(a, pi, a.nbr[(size_t)sj * a.n + i], dxj, dyj, dzj, j, tj);
+    const T* p2 = srec + ((ti * ns + tj) * ns + tj) * RSTRIDE;
+    const T r2j = dxj * dxj + dyj * dyj + dzj * dzj;
+    const T rij = r2j * M<T>::rsqrt_nr(r2j);
+    if (!(rij < p2[K_ROUT2])) continue;
+    const T rinj = T(1) / rij;
+    const T uxj = dxj * rinj, uyj = dyj * rinj, uzj = dzj * rinj;
+    T zeta = 0;
+    for (int sk = 0; sk < c; ++sk) {
+      if (sk == sj) continue;
+      T dxk, dyk, dzk;
+      int k, tk;
+      Bond<T>::vec(a, pi, a.nbr[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
+      const T* p3 = srec + ((ti * ns + tj) * ns + tk) * RSTRIDE;
+      const T r2k = dxk * dxk + dyk * dyk + dzk * dzk;
+      const T rik = r2k * M<T>::rsqrt_nr(r2k);
+      if (!(rik < p3[K_ROUT3])) continue;
+      const T cs = (dxj * dxk + dyj * dyk + dzj * dzk) * rinj / rik;
+      T zt, A1, A2, A3;
+      triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+      zeta += zt;
+    }
+    T V, dVdr, dz;
+    pair<T>(p2, rij, zeta, V, dVdr, dz);
+    ei += V;
+    T Fjx = -dVdr * uxj, Fjy = -dVdr * uyj, Fjz = -dVdr * uzj;
+    for (int sk = 0; sk < c; ++sk) {
+      if (sk == sj) continue;
+      T dxk, dyk, dzk;
+      int k, tk;
+      Bond<T>::vec(a, pi, a.nbr[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
+      const T* p3 = srec + ((ti * ns + tj) * ns + tk) * RSTRIDE;
+      const T r2k = dxk * dxk + dyk * dyk + dzk * dzk;
+      const T rik = r2k * M<T>::rsqrt_nr(r2k);
+      if (!(rik < p3[K_ROUT3])) continue;
+      const T rink = T(1) / rik;
+      const T uxk = dxk * rink, uyk = dyk * rink, uzk = dzk * rink;
+      const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
+      T zt, A1, A2, A3;
+      triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+      // d zeta / d x_j and d x_k
+      const T gjx = A1 * (uxk - cs * uxj) * rinj + A2 * uxj;
+      const T gjy = A1 * (uyk - cs * uyj) * rinj + A2 * uyj;
+      const T gjz = A1 * (uzk - cs * uzj) * rinj + A2 * uzj;
+      const T gkx = A1 * (uxj - cs * uxk) * rink + (A3 - A2) * uxk;
+      const T gky = A1 * (uyj - cs * uyk) * rink + (A3 - A2) * uyk;
+      const T gkz = A1 * (uzj - cs * uzk) * rink + (A3 - A2) * uzk;
+      Fjx -= dz * gjx;
+      Fjy -= dz * gjy;
+      Fjz -= dz * gjz;
+      const T Fkx = -dz * gkx, Fky = -dz * gky, Fkz = -dz * gkz;
+      atomic_add3(a.f, k, to_f64(Fkx), to_f64(Fky), to_f64(Fkz));
+      fix -= Fkx;
+      fiy -= Fky;
+      fiz -= Fkz;
+      w[0] += dxk * Fkx;
+      w[1] += dyk * Fky;
+      w[2] += dzk * Fkz;
+      w[3] += dxk * Fky;
+      w[4] += dxk * Fkz;
+      w[5] += dyk * Fkz;
+    }
+    atomic_add3(a.f, j, to_f64(Fjx), to_f64(Fjy), to_f64(Fjz));
+    fix -= Fjx;
+    fiy -= Fjy;
+    fiz -= Fjz;
+    w[0] += dxj * Fjx;
+    w[1] += dyj * Fjy;
+    w[2] += dzj * Fjz;
+    w[3] += dxj * Fjy;
+    w[4] += dxj * Fjz;
+    w[5] += dyj * Fjz;
+  }
+  atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+}
+
+// ---------------------------------------------------------------- reduction
+template <class T>
+__device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc) {
+  __shared__ double part[BLOCK / 32][7];
+  T v[7] = {ei, w[0], w[1], w[2], w[3], w[4], w[5]};
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 7; ++q) part[wid][q] = to_f64(v[q]);
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double s = 0.0;
+    for (int q = 0; q < BLOCK / 32; ++q) s += part[q][threadIdx.x];
+    atomicAdd(&acc[threadIdx.x], s);
+  }
+}
+
+// ---------------------------------------------------------------- the kernel
+template <class T, int NS, int ZC, bool LAM3>
+__global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
+  constexpr int SNS = NS > 0 ? NS : TERSOFF_MAX_SPECIES;
+  __shared__ T srec[SNS * SNS * SNS * RSTRIDE];
+  __shared__ T sfilt[SNS * SNS];
+  const int ns = NS > 0 ? NS : a.ns;
+  for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += BLOCK) srec[q] = a.rec[q];
+  if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+  __syncthreads();
+
+  const int i = blockIdx.x * BLOCK + threadIdx.x;
+  T ei = 0;
+  T w[6] = {0, 0, 0, 0, 0, 0};
+  if (i < a.n) {
+    T xi, yi, zi;
+    int ti;
+    Pos<T>::coarse(a, i, xi, yi, zi, ti);
+    const int c = min(a.cnt[i], a.cap);
+    // 1. filter the skin list into a bit mask
+    unsigned long long mask = 0ull;
+    const bool fits = c <= 64;
+    if (fits) {
+      for (int s = 0; s < c; ++s) {
+        const uint32_t e = a.nbr[(size_t)s * a.n + i];
+        int j, ox, oy, oz;
+        decode(e, j, ox, oy, oz);
+        T xj, yj, zj;
+        int tj;
+        Pos<T>::coarse(a, j, xj, yj, zj, tj);
+        const T dx = (xj - xi) + ox * a.h[0];
+        const T dy = (yj - yi) + oy * a.h[1];
+        const T dz = (zj - zi) + oz * a.h[2];
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
+      }
+    }
+    const int z = __popcll(mask);
+    if (!fits || z > ZC) {
+      atomicAdd(&a.flags[FLAG_FALLBACK], 1);
+      general_atom<T, NS, LAM3>(a, srec, i, ti, ei, w);
+    } else {
+      using P = typename SelfPos<T>::type;
+      const P pi = self_pos<T>(a, i);
+      // 2. short list into registers
+      T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC];
+      int jj[ZC], tt[ZC];
+#pragma unroll
+      for (int q = 0; q < ZC; ++q) {
+        ux[q] = uy[q] = uz[q] = T(0);
+        rr[q] = T(1);
+        ri[q] = T(1);
+        jj[q] = i;
+        tt[q] = 0;
+        if (q < z) {
+          const int s = __ffsll(mask) - 1;
+          mask &= mask - 1ull;
+          T dx, dy, dz;
+          int j, tj;
+          Bond<T>::vec(a, pi, a.nbr[(size_t)s * a.n + i], dx, dy, dz, j, tj);
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          const T inv = M<T>::rsqrt_nr(r2);
+          ri[q] = inv;
+          rr[q] = r2 * inv;
+          ux[q] = dx * inv;
+          uy[q] = dy * inv;
+          uz[q] = dz * inv;
+          jj[q] = j;
+          tt[q] = tj;
+        }
+      }
+      T fx[ZC], fy[ZC], fz[ZC];
+#pragma unroll
+      for (int q = 0; q < ZC; ++q) fx[q] = fy[q] = fz[q] = T(0);
+
+#pragma unroll
+      for (int qj = 0; qj < ZC; ++qj) {
+        if (qj < z) {
+          const T* p2 = srec + ((ti * ns + tt[qj]) * ns + tt[qj]) * RSTRIDE;
+          const T rij = rr[qj];
+          if (rij < p2[K_ROUT2]) {
+            // first K loop: zeta_ij and its derivatives (Sec. IV-A)
+            T zeta = 0, gjx = 0, gjy = 0, gjz = 0;
+            T gkx[ZC], gky[ZC], gkz[ZC];
+#pragma unroll
+            for (int qk = 0; qk < ZC; ++qk) {
+              gkx[qk] = gky[qk] = gkz[qk] = T(0);
+              if (qk != qj && qk < z) {
+                const T* p3 = srec + ((ti * ns + tt[qj]) * ns + tt[qk]) * RSTRIDE;
+                const T rik = rr[qk];
+                if (rik < p3[K_ROUT3]) {
+                  const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
+                  T zt, A1, A2, A3;
+                  triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+                  zeta += zt;
+                  const T a1j = A1 * ri[qj], a1k = A1 * ri[qk];
+                  gjx += a1j * (ux[qk] - cs * ux[qj]) + A2 * ux[qj];
+                  gjy += a1j * (uy[qk] - cs * uy[qj]) + A2 * uy[qj];
+                  gjz += a1j * (uz[qk] - cs * uz[qj]) + A2 * uz[qj];
+                  const T a3 = A3 - A2;
+                  gkx[qk] = a1k * (ux[qj] - cs * ux[qk]) + a3 * ux[qk];
+                  gky[qk] = a1k * (uy[qj] - cs * uy[qk]) + a3 * uy[qk];
+                  gkz[qk] = a1k * (uz[qj] - cs * uz[qk]) + a3 * uz[qk];
+                }
+              }
+            }
+            T V, dVdr, dz;
+            pair<T>(p2, rij, zeta, V, dVdr, dz);
+            ei += V;
+            fx[qj] -= dVdr * ux[qj] + dz * gjx;
+            fy[qj] -= dVdr * uy[qj] + dz * gjy;
+            fz[qj] -= dVdr * uz[qj] + dz * gjz;
+#pragma unroll
+            for (int qk = 0; qk < ZC; ++qk) {
+              if (qk != qj) {
+                fx[qk] -= dz * gkx[qk];
+                fy[qk] -= dz * gky[qk];
+                fz[qk] -= dz * gkz[qk];
+              }
+            }
+          }
+        }
+      }
+      // force on i and virial from the neighbour forces; scatter
+      T fix = 0, fiy = 0, fiz = 0;
+#pragma unroll
+      for (int q = 0; q < ZC; ++q) {
+        if (q < z) {
+          fix -= fx[q];
+          fiy -= fy[q];
+          fiz -= fz[q];
+          const T dx = ux[q] * rr[q], dy = uy[q] * rr[q], dz = uz[q] * rr[q];
+          w[0] += dx * fx[q];
+          w[1] += dy * fy[q];
+          w[2] += dz * fz[q];
+          w[3] += dx * fy[q];
+          w[4] += dx * fz[q];
+          w[5] += dy * fz[q];
+          atomic_add3(a.f, jj[q], to_f64(fx[q]), to_f64(fy[q]), to_f64(fz[q]));
+        }
+      }
+      atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+    }
+    if (a.eatom) a.eatom[i] = to_f64(ei);
+  }
+  block_reduce_store<T>(ei, w, a.acc);
+}
+
+}  // namespace fwd
+}  // namespace tgb
