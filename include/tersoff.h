@@ -157,6 +157,15 @@ int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int 
                          const double* mass, double dt, int nsteps, int rebuild_every,
                          double* thermo, void* stream);
 
+/* MD execution mode. With enable != 0 (the default) tersoff_md_step records
+ * its whole sequence of steps (integration, neighbour rebuilds, forces) once
+ * as a CUDA graph and replays it on later calls with the same arguments and
+ * context state; the state is snapshotted before each replay and, if a
+ * rebuild inside it exceeded the list capacity, restored and the steps rerun
+ * with host-checked rebuilds. With enable == 0 every step is launched
+ * directly. */
+int tersoff_set_graphs(tersoff_ctx* ctx, int enable);
+
 /* Number of kernel launches this context has enqueued since creation (host
  * output); used to report launch counts. */
 int tersoff_launch_count(const tersoff_ctx* ctx, long long* count);

@@ -45,6 +45,7 @@ _SIG = {
     "tersoff_md_step_host": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_launch_count": ([_P, _P], _I),
     "tersoff_set_timing": ([_P, _I], _I),
+    "tersoff_set_graphs": ([_P, _I], _I),
     "tersoff_timing": ([_P, _I, _P, _P], _I),
 }
 
@@ -186,6 +187,9 @@ class Context:
                                                   int(x.shape[0]), m.ctypes.data_as(_P),
                                                   float(dt), int(nsteps), int(rebuild_every),
                                                   _ptr(thermo), _stream(stream)))
+
+    def set_graphs(self, enable=True):
+        self._check(self.lib.tersoff_set_graphs(self.h, int(bool(enable))))
 
     def set_timing(self, enable=True):
         self._check(self.lib.tersoff_set_timing(self.h, int(bool(enable))))

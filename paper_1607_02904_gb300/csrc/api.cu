@@ -30,17 +30,49 @@ static cudaEvent_t take_event(Ctx* c) {
   return e;
 }
 
+// During stream capture the event records become graph nodes (external
+// records) and the pair is kept with the graph, read after every replay.
+static void record(Ctx* c, cudaEvent_t e, cudaStream_t s) {
+  if (c->capturing)
+    cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(e, s);
+}
+
 TimedRegion::TimedRegion(Ctx* c_, int kind_, cudaStream_t s_) : c(c_), kind(kind_), s(s_) {
   if (!c->timing) return;
   a = take_event(c);
   b = take_event(c);
-  if (a) cudaEventRecord(a, s);
+  if (a) record(c, a, s);
 }
 
 TimedRegion::~TimedRegion() {
   if (!c->timing || !a || !b) return;
-  cudaEventRecord(b, s);
-  c->pending.push_back({kind, a, b});
+  record(c, b, s);
+  (c->timer_sink ? c->timer_sink : &c->pending)->push_back({kind, a, b});
+}
+
+// adds the elapsed times of a replayed graph's timer pairs (events stay with
+// the graph)
+static void fold_graph_timers(Ctx* c) {
+  for (auto& p : c->graph.timers) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->t_ms[p.kind] += ms;
+      c->t_count[p.kind] += 1;
+    }
+  }
+}
+
+static void drop_graph(Ctx* c) {
+  if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+  c->graph.exec = nullptr;
+  for (auto& p : c->graph.timers) {
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->graph.timers.clear();
+  c->graph.gen = -1;
 }
 
 int fold_timing(Ctx* c) {
@@ -88,6 +120,10 @@ int ensure_atoms(Ctx* c, int n) {
   if ((st = dev_alloc(c, &c->d_posq, m))) return st;
   if ((st = dev_alloc(c, &c->d_pos64, m))) return st;
   if ((st = dev_alloc(c, &c->d_fbuf, 3 * m))) return st;
+  if ((st = dev_alloc(c, &c->d_qorg, 3 * m))) return st;
+  if ((st = dev_alloc(c, &c->d_qref, m))) return st;
+  if ((st = dev_alloc(c, &c->d_zcnt, m))) return st;
+  if ((st = dev_alloc(c, &c->d_bucket, 3 * m))) return st;
   c->atoms_alloc = m;
   c->nbr_alloc = 0;  // list storage depends on n
   return TERSOFF_OK;
@@ -95,9 +131,11 @@ int ensure_atoms(Ctx* c, int n) {
 
 int ensure_nbr(Ctx* c) {
   size_t need = (size_t)c->cap * (size_t)c->n;
-  if (need <= c->nbr_alloc && c->d_nbr) return TERSOFF_OK;
+  c->zs_cap = c->cap;  // a short list never exceeds the skin list
+  if (need <= c->nbr_alloc && c->d_nbr && c->d_short) return TERSOFF_OK;
   int st = dev_alloc(c, &c->d_nbr, need);
   if (st) return st;
+  if ((st = dev_alloc(c, &c->d_short, need))) return st;
   c->nbr_alloc = need;
   return TERSOFF_OK;
 }
@@ -137,18 +175,22 @@ int read_flags(Ctx* c, cudaStream_t s) {
   return TERSOFF_OK;
 }
 
-// neighbour build with overflow regrow; synchronises s
+// neighbour build (skin list, short list, displacement references) with
+// overflow regrow; synchronises s once per attempt
 int build_list(Ctx* c, const double* x, cudaStream_t s) {
   for (int attempt = 0; attempt < 4; ++attempt) {
     int st = ensure_nbr(c);
     if (st) return st;
-    TGB_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_COUNT, s));
+    TGB_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_BUILD_WORDS, s));
+    TGB_CUDA(c, cudaMemsetAsync(c->d_flags + FLAG_NONFINITE, 0, sizeof(int), s));
+    TGB_CUDA(c, cudaMemsetAsync(c->d_flags + FLAG_OVF_ANY, 0, sizeof(int), s));
     if ((st = launch_neighbor_build(c, x, s))) return st;
     if ((st = read_flags(c, s))) return st;
     if (c->h_flags[FLAG_NONFINITE])
       return fail(c, TERSOFF_E_NONFINITE, "non-finite position in neighbour build");
     c->max_cnt = c->h_flags[FLAG_OVERFLOW];
     c->max_short = c->h_flags[FLAG_SHORT_MAX];
+    for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[FLAG_BUCKET + b];
     if (c->max_cnt <= c->cap) {
       c->have_list = true;
       c->steps_since_build = 0;
@@ -156,8 +198,16 @@ int build_list(Ctx* c, const double* x, cudaStream_t s) {
     }
     // grow with headroom for atoms entering the skin before the next build
     c->cap = c->max_cnt + c->max_cnt / 4 + 4;
+    c->gen++;
   }
   return fail(c, TERSOFF_E_NEIGH_OVERFLOW, "neighbour capacity could not be grown");
+}
+
+// the same build without host synchronisation (inside MD sequences that may be
+// captured): capacity overflow and non-finite input raise sticky flags
+int build_list_async(Ctx* c, const double* x, cudaStream_t s) {
+  TGB_CUDA(c, cudaMemsetAsync(c->d_flags, 0, sizeof(int) * FLAG_BUILD_WORDS, s));
+  return launch_neighbor_build(c, x, s);
 }
 
 int check_ctx(Ctx* c) {
@@ -201,6 +251,15 @@ int tersoff_create(tersoff_ctx** out, int precision) {
   }
   cudaMemset(c->d_flags, 0, sizeof(int) * tgb::FLAG_COUNT);
   cudaMemset(c->d_acc, 0, sizeof(double) * 8);
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    c->cap_stream = nullptr;
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    c->side = nullptr;
+  }
   *out = p;
   return TERSOFF_OK;
 }
@@ -214,12 +273,18 @@ int tersoff_destroy(tersoff_ctx* p) {
                   c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
                   c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
-                  c->d_coef};
+                  c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
+                  c->d_bucket, c->d_snap};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_flags) cudaFreeHost(c->h_flags);
+  tgb::drop_graph(c);
   tgb::fold_timing(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete p;
   return TERSOFF_OK;
 }
@@ -235,6 +300,7 @@ int tersoff_set_precision(tersoff_ctx* p, int precision) {
   if (!tgb::valid_precision(precision))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "precision must be TERSOFF_FP64 or TERSOFF_MIXED");
   c->precision = precision;
+  c->gen++;
   return TERSOFF_OK;
 }
 
@@ -296,6 +362,20 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
     of[tgb::K_LAM1LO] = (float)(o[tgb::K_LAM1] - (double)of[tgb::K_LAM1]);
     of[tgb::K_LAM2LO] = (float)(o[tgb::K_LAM2] - (double)of[tgb::K_LAM2]);
   }
+  // symmetric three-body terms: gamma, c, d, h of (i,j,k) equal those of
+  // (i,k,j), and the R, D of f_C(r_ik) do not depend on j
+  bool sym = !lam3;
+  for (int i = 0; i < ns && sym; ++i)
+    for (int j = 0; j < ns && sym; ++j)
+      for (int k = 0; k < ns && sym; ++k) {
+        const double* a = table + (size_t)((i * ns + j) * ns + k) * TERSOFF_NPARAM;
+        const double* b = table + (size_t)((i * ns + k) * ns + j) * TERSOFF_NPARAM;
+        const double* e = table + (size_t)((i * ns + k) * ns + k) * TERSOFF_NPARAM;
+        for (int f : {TERSOFF_P_GAMMA, TERSOFF_P_C, TERSOFF_P_D, TERSOFF_P_H})
+          if (a[f] != b[f]) sym = false;
+        if (a[TERSOFF_P_R] != e[TERSOFF_P_R] || a[TERSOFF_P_D_CUT] != e[TERSOFF_P_D_CUT])
+          sym = false;
+      }
   // filter radius for (ti, tx): largest outer cutoff of any term in which an
   // atom of type tx is the bond partner j or the third atom k of a type-ti atom
   std::vector<double> filt((size_t)ns * ns, 0.0);
@@ -324,10 +404,14 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
   TGB_CUDA(c, cudaMemcpy(c->d_rec32, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
   TGB_CUDA(c, cudaMemcpy(c->d_filt64, f64.data(), sizeof(double) * f64.size(), cudaMemcpyHostToDevice));
   TGB_CUDA(c, cudaMemcpy(c->d_filt32, f32.data(), sizeof(float) * f32.size(), cudaMemcpyHostToDevice));
+  c->gen++;
   c->ns = ns;
+  c->h_rec64 = r64;
+  c->h_rec32 = r32;
   c->table.assign(table, table + (size_t)nrec * TERSOFF_NPARAM);
   c->filt = filt;
   c->has_lam3 = lam3;
+  c->sym_table = sym;
   c->rmax_cut = rmax;
   c->have_list = false;
   return TERSOFF_OK;
@@ -349,7 +433,9 @@ int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, in
   if ((st = tgb::setup_grid(c, box, r_list))) return st;
   c->n = n;
   c->r_list = r_list;
+  c->margin = 0.6 * (r_list - c->rmax_cut);
   c->have_list = false;
+  c->gen++;
   if ((st = tgb::ensure_atoms(c, n))) return st;
   if (n > 0)
     TGB_CUDA(c, cudaMemcpyAsync(c->d_types, types, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
@@ -380,6 +466,7 @@ int tersoff_set_neighbor_capacity(tersoff_ctx* p, int capacity) {
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "capacity must be in [1, 4096]");
   c->cap = capacity;
   c->have_list = false;
+  c->gen++;
   return TERSOFF_OK;
 }
 
@@ -404,7 +491,7 @@ static int compute_impl(Ctx* c, const double* x, int n, double* energy, double* 
   if (n != c->n || (n > 0 && !x))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
   double* f = forces ? forces : c->d_fbuf;
-  if ((st = tgb::launch_pack_positions(c, x, s))) return st;
+  if ((st = tgb::launch_pack_positions(c, x, false, s))) return st;
   if (n > 0) TGB_CUDA(c, cudaMemsetAsync(f, 0, sizeof(double) * 3 * (size_t)n, s));
   TGB_CUDA(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * 8, s));
   {
@@ -432,6 +519,47 @@ int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eato
   return compute_impl(c, x, n, nullptr, nullptr, nullptr, eatom, (cudaStream_t)stream);
 }
 
+// Enqueues nsteps velocity-Verlet steps. sync_builds: rebuild with a host
+// check (eager); otherwise without host synchronisation (graph capture).
+static int enqueue_md(Ctx* c, double* x, double* v, double* f, const double* coef, double dt,
+                      int nsteps, int rebuild_every, double* rows, double* thermo,
+                      bool sync_builds, cudaStream_t s) {
+  int st = TERSOFF_OK;
+  if (rows) TGB_CUDA(c, cudaMemsetAsync(rows, 0, sizeof(double) * 8 * (size_t)nsteps, s));
+  for (int step = 0; step < nsteps; ++step) {
+    c->steps_since_build++;
+    const bool rebuild = rebuild_every > 0 && c->steps_since_build >= rebuild_every;
+    // opening half kick (merged with the previous step's closing one), drift
+    double* ke_row = (rows && step > 0) ? rows + 8 * (size_t)(step - 1) + 7 : nullptr;
+    double* acc = rows ? rows + 8 * (size_t)step : c->d_acc;
+    {
+      tgb::TimedRegion tr(c, 2, s);
+      if ((st = tgb::launch_md_step(c, x, v, f, coef, dt, step == 0 ? 1 : 2, !rebuild, ke_row,
+                                    rows ? nullptr : c->d_acc, s)))
+        return st;
+    }
+    if (rebuild) {
+      {
+        tgb::TimedRegion tr(c, 1, s);
+        st = sync_builds ? tgb::build_list(c, x, s) : tgb::build_list_async(c, x, s);
+      }
+      if (st) return st;
+      c->steps_since_build = 0;
+    }
+    {
+      tgb::TimedRegion tr(c, 0, s);
+      if ((st = tgb::launch_forward(c, f, acc, nullptr, s))) return st;
+    }
+  }
+  {
+    tgb::TimedRegion tr(c, 2, s);
+    double* ke_row = rows ? rows + 8 * (size_t)(nsteps - 1) + 7 : nullptr;
+    if ((st = tgb::launch_final_kick(c, v, f, coef, ke_row, s))) return st;
+  }
+  if (thermo && (st = tgb::launch_thermo_rows(c, rows, nsteps, tgb::MVV2E, thermo, s))) return st;
+  return TERSOFF_OK;
+}
+
 static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double* mass,
                    double dt, int nsteps, int rebuild_every, double* thermo, cudaStream_t s) {
   int st = tgb::check_ctx(c);
@@ -443,42 +571,117 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   for (int t = 0; t < c->ns; ++t)
     if (!(mass[t] > 0.0)) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "masses must be positive");
   if (n == 0 || nsteps == 0) return TERSOFF_OK;
-  // per-species dt/2 * FTM2V / m and masses, kept in the accumulator tail
-  double hc[2 * TERSOFF_MAX_SPECIES];
+  // per-species dt/2 * FTM2V / m, then masses
+  double hc[2 * TERSOFF_MAX_SPECIES] = {0};
   for (int t = 0; t < c->ns; ++t) {
     hc[t] = 0.5 * dt * tgb::FTM2V / mass[t];
     hc[TERSOFF_MAX_SPECIES + t] = mass[t];
   }
   TGB_CUDA(c, cudaMemcpyAsync(c->d_coef, hc, sizeof(hc), cudaMemcpyHostToDevice, s));
-  const double* cdt = c->d_coef;
-  const double* dmass = c->d_coef + TERSOFF_MAX_SPECIES;
-  TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_FALLBACK, 0, sizeof(int), s));
-  for (int step = 0; step < nsteps; ++step) {
-    c->steps_since_build++;
-    const bool rebuild = rebuild_every > 0 && c->steps_since_build >= rebuild_every;
-    {
-      tgb::TimedRegion tr(c, 2, s);
-      if ((st = tgb::launch_kick_drift(c, x, v, f, cdt, dt, !rebuild, s))) break;
+  double* rows = nullptr;
+  if (thermo) {
+    const size_t need = 8 * (size_t)nsteps;
+    if (c->trow_alloc < need) {
+      if ((st = tgb::dev_alloc(c, &c->d_trow, need))) return st;
+      c->trow_alloc = need;
+      c->gen++;
     }
-    if (rebuild) {
-      {
-        tgb::TimedRegion tr(c, 1, s);
-        st = tgb::build_list(c, x, s);
-      }
-      if (st) break;
-      c->steps_since_build = 0;
-      if ((st = tgb::launch_pack_positions(c, x, s))) break;
-    }
-    {
-      tgb::TimedRegion tr(c, 0, s);
-      if ((st = tgb::launch_forward(c, f, c->d_acc, nullptr, s))) break;
-    }
-    {
-      tgb::TimedRegion tr(c, 2, s);
-      if ((st = tgb::launch_kick(c, v, f, cdt, dmass, thermo != nullptr, s))) break;
-    }
-    if (thermo && (st = tgb::launch_thermo(c, tgb::MVV2E, thermo + 3 * (size_t)step, s))) break;
+    rows = c->d_trow;
   }
+  TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_BUILD_WORDS, 0,
+                              sizeof(int) * (tgb::FLAG_COUNT - tgb::FLAG_BUILD_WORDS), s));
+  if (!c->use_graphs || !c->cap_stream) {
+    st = enqueue_md(c, x, v, f, c->d_coef, dt, nsteps, rebuild_every, rows, thermo, true, s);
+    if (st) return st;
+    TGB_CUDA(c, cudaStreamSynchronize(s));
+    return TERSOFF_OK;
+  }
+  // graph path: snapshot the state, replay (capturing on a new shape), check
+  const size_t m = 3 * (size_t)n;
+  if (c->snap_alloc < 3 * m) {
+    if ((st = tgb::dev_alloc(c, &c->d_snap, 3 * m))) return st;
+    c->snap_alloc = 3 * m;
+  }
+  TGB_CUDA(c, cudaMemcpyAsync(c->d_snap, x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  TGB_CUDA(c, cudaMemcpyAsync(c->d_snap + m, v, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  TGB_CUDA(c, cudaMemcpyAsync(c->d_snap + 2 * m, f, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  const int ssb0 = c->steps_since_build;
+  auto& G = c->graph;
+  const bool same = G.exec && G.gen == c->gen && G.x == x && G.v == v && G.f == f &&
+                    G.thermo == thermo && G.dt == dt && G.nsteps == nsteps &&
+                    G.rebuild_every == rebuild_every && G.ssb0 == ssb0 &&
+                    G.precision == c->precision && G.timing == c->timing;
+  if (!same) {
+    tgb::drop_graph(c);
+    cudaGraph_t graph = nullptr;
+    // capture on the context's own stream (the caller's may be the legacy
+    // default stream, which cannot be captured); replay on the caller's
+    cudaStream_t cs = c->cap_stream;
+    TGB_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const long long l0 = c->launches;
+    c->capturing = true;
+    c->timer_sink = &G.timers;
+    st = enqueue_md(c, x, v, f, c->d_coef, dt, nsteps, rebuild_every, rows, thermo, false, cs);
+    c->capturing = false;
+    c->timer_sink = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    cudaGetLastError();  // a failed capture leaves its error in the last-error slot
+    if (st == TERSOFF_OK && ce != cudaSuccess) st = tgb::cuda_fail(c, ce, "cudaStreamEndCapture");
+    if (st == TERSOFF_OK) {
+      ce = cudaGraphInstantiate(&G.exec, graph, 0);
+      if (ce != cudaSuccess) st = tgb::cuda_fail(c, ce, "cudaGraphInstantiate");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st) {
+      tgb::drop_graph(c);
+      c->steps_since_build = ssb0;
+      return st;
+    }
+    G.x = x;
+    G.v = v;
+    G.f = f;
+    G.thermo = thermo;
+    G.dt = dt;
+    G.nsteps = nsteps;
+    G.rebuild_every = rebuild_every;
+    G.ssb0 = ssb0;
+    G.precision = c->precision;
+    G.timing = c->timing;
+    G.gen = c->gen;
+    G.kernels = c->launches - l0;
+    c->launches = l0;
+  } else {
+    // host bookkeeping of the replayed sequence
+    for (int step = 0; step < nsteps; ++step) {
+      c->steps_since_build++;
+      if (rebuild_every > 0 && c->steps_since_build >= rebuild_every) c->steps_since_build = 0;
+    }
+  }
+  c->launches += G.kernels;
+  TGB_CUDA(c, cudaGraphLaunch(G.exec, s));
+  if ((st = tgb::read_flags(c, s))) return st;
+  if (c->timing) tgb::fold_graph_timers(c);
+  const bool bad = c->h_flags[tgb::FLAG_OVF_ANY] || c->h_flags[tgb::FLAG_NONFINITE];
+  if (!bad) {
+    c->max_cnt = c->h_flags[tgb::FLAG_OVERFLOW];
+    c->max_short = c->h_flags[tgb::FLAG_SHORT_MAX];
+    for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[tgb::FLAG_BUCKET + b];
+    return TERSOFF_OK;
+  }
+  // a build inside the sequence overflowed (or met non-finite positions):
+  // restore the state, rebuild with a host check, run the steps eagerly
+  TGB_CUDA(c, cudaMemcpyAsync(x, c->d_snap, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  TGB_CUDA(c, cudaMemcpyAsync(v, c->d_snap + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  TGB_CUDA(c, cudaMemcpyAsync(f, c->d_snap + 2 * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  if (c->h_flags[tgb::FLAG_NONFINITE]) {
+    c->steps_since_build = ssb0;
+    TGB_CUDA(c, cudaStreamSynchronize(s));
+    return tgb::fail(c, TERSOFF_E_NONFINITE, "non-finite position during MD (state restored)");
+  }
+  c->cap = c->cap + c->cap / 2 + 4;
+  c->gen++;
+  if ((st = tgb::build_list(c, x, s))) return st;
+  st = enqueue_md(c, x, v, f, c->d_coef, dt, nsteps, rebuild_every, rows, thermo, true, s);
   if (st) return st;
   TGB_CUDA(c, cudaStreamSynchronize(s));
   return TERSOFF_OK;
@@ -528,6 +731,14 @@ int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
 int tersoff_launch_count(const tersoff_ctx* p, long long* count) {
   if (!p || !count) return TERSOFF_E_INVALID_ARG;
   *count = p->impl.launches;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_graphs(tersoff_ctx* p, int enable) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  c->use_graphs = enable != 0;
+  tgb::drop_graph(c);
   return TERSOFF_OK;
 }
 

@@ -79,10 +79,16 @@ struct Ctx {
   std::vector<double> table;      // raw, host
   double* d_rec64 = nullptr;      // derived records, device
   float* d_rec32 = nullptr;
+  std::vector<double> h_rec64;    // host copies
+  std::vector<float> h_rec32;
+  cudaStream_t side = nullptr;    // side stream for small force launches
+  cudaStream_t cap_stream = nullptr;  // stream used to capture MD graphs
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* d_filt64 = nullptr;     // (ti,tj) filter radius^2
   float* d_filt32 = nullptr;
   std::vector<double> filt;       // host copy, radius (not squared)
   bool has_lam3 = false;
+  bool sym_table = false;         // angular terms symmetric in (j,k), f_C(r_ik) j-independent
   double rmax_cut = 0.0;          // largest f_C outer radius
 
   // atoms / list
@@ -106,6 +112,16 @@ struct Ctx {
   size_t cells_alloc = 0;
   size_t atoms_alloc = 0;
   size_t nbr_alloc = 0;
+  double* d_qorg = nullptr;       // n x 3: 1.5*2^52 - o_i 2^S (fixed-point origin)
+  int4* d_qref = nullptr;         // n: fixed-point offsets at the last build
+  uint32_t* d_short = nullptr;    // zs_cap * n, slot-major short list
+  int* d_zcnt = nullptr;          // n
+  int* d_bucket = nullptr;        // 3 x n: atom indices per short-list size bucket
+  int nbucket[3] = {0, 0, 0};     // bucket sizes at the last build
+  int zs_cap = 0;
+  double margin = 0.0;            // short-list radius margin beyond the cutoffs
+  double* d_trow = nullptr;       // MD thermo accumulation rows (8 doubles per step)
+  size_t trow_alloc = 0;
   float4* d_pos32 = nullptr;      // n: (u float, type bits)
   int4* d_posq = nullptr;         // n: (u fixed point, type)
   dpos4* d_pos64 = nullptr;     // n: (u double, type)
@@ -130,6 +146,25 @@ struct Ctx {
   std::vector<Pending> pending;
   double t_ms[3] = {0, 0, 0};
   long long t_count[3] = {0, 0, 0};
+  std::vector<Pending>* timer_sink = nullptr;  // capture: the graph's timer list
+  bool capturing = false;
+
+  // MD steps as one CUDA graph per call shape (replayed while the shape and
+  // the context state generation stay the same)
+  bool use_graphs = true;
+  long long gen = 0;  // bumped by params, builds from outside MD, capacity changes
+  struct MdGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<Pending> timers;
+    const double *x = nullptr, *v = nullptr, *f = nullptr, *thermo = nullptr;
+    double dt = 0.0;
+    int nsteps = 0, rebuild_every = 0, ssb0 = 0, precision = 0;
+    bool timing = false;
+    long long gen = -1;
+    long long kernels = 0;  // kernel launches inside the graph
+  } graph;
+  double* d_snap = nullptr;  // x, v, f at the start of a graph launch (rollback)
+  size_t snap_alloc = 0;
 };
 
 // Records an event pair around a launch sequence when timing is enabled.
@@ -143,12 +178,18 @@ struct TimedRegion {
 };
 int fold_timing(Ctx* c);
 
+// Device status words. Indices below FLAG_BUILD_WORDS are cleared at every
+// neighbour build; the others are sticky until the next compute/MD call.
 enum : int {
-  FLAG_OVERFLOW = 0,   // max neighbour count (atomicMax)
-  FLAG_NONFINITE = 1,  // non-finite position seen
-  FLAG_SHORT_MAX = 2,  // largest short-list count
-  FLAG_FALLBACK = 3,   // atoms handled by the general path
-  FLAG_COUNT = 8
+  FLAG_OVERFLOW = 0,     // largest neighbour count of the build (atomicMax)
+  FLAG_SHORT_MAX = 1,    // largest short-list count of the build
+  FLAG_DMAX = 2,         // running max squared displacement since the build (float bits)
+  FLAG_BUCKET = 3,       // 3, 4, 5: atoms per short-list size bucket (<= 4, <= 8, more)
+  FLAG_BUILD_WORDS = 8,
+  FLAG_NONFINITE = 8,    // non-finite position seen by a build
+  FLAG_FALLBACK = 9,     // atoms handled by the general path
+  FLAG_OVF_ANY = 10,     // some build exceeded the list capacity
+  FLAG_COUNT = 16
 };
 
 int fail(Ctx* c, int code, const std::string& msg);
@@ -165,21 +206,32 @@ int cuda_fail(Ctx* c, cudaError_t e, const char* where);
 int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s);
 int launch_neighbor_export(Ctx* c, int* cnt, int* nbr, int cap, cudaStream_t s);
 
-// Position packs for the force kernels (integrate.cu).
-int launch_pack_positions(Ctx* c, const double* x, cudaStream_t s);
+// Position packs for the force kernels (integrate.cu): fixed-point offsets
+// (both paths) and FP64 offsets (FP64 path). At a build (build = true) also
+// the float offsets and the displacement references; otherwise the running
+// maximum displacement since the build is updated.
+int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s);
 
-// Forces (tersoff_fwd.cu). Accumulates into f (zeroed by the caller), energy
-// and virial into acc[0..6] (zeroed by the caller); eatom optional.
+// Forces (fwd_f32.cu / fwd_f64.cu). Accumulates into f (zeroed by the caller),
+// energy and virial into acc[0..6] (zeroed by the caller); eatom optional.
 int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f32(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 
-// Velocity Verlet (integrate.cu). cdt[t] = dt/2 * (force-to-acceleration) / m_t.
-int launch_kick_drift(Ctx* c, double* x, double* v, double* f, const double* cdt, double dt,
-                      bool pack, cudaStream_t s);
-int launch_kick(Ctx* c, double* v, const double* f, const double* cdt, const double* mass,
-                bool want_ke, cudaStream_t s);
-int launch_thermo(Ctx* c, double mvv2e, double* row, cudaStream_t s);
-int launch_zero(Ctx* c, double* p, size_t count, cudaStream_t s);
+// Velocity Verlet (integrate.cu). coef[t] = dt/2 * (force-to-acceleration) / m_t,
+// coef[MAX_SPECIES + t] = m_t.
+//   step kernel: v += kick * coef f (kick = 1 on the first step of a call,
+//   2 afterwards: the closing half kick of the previous step and the opening
+//   half kick of this one); x += dt v; f = 0; pack; ke_row (optional) receives
+//   sum m (v_prev + coef f)^2 / 2 of the previous step; acc_zero (optional) is
+//   cleared for the coming force evaluation.
+int launch_md_step(Ctx* c, double* x, double* v, double* f, const double* coef, double dt,
+                   int kick, bool pack, double* ke_row, double* acc_zero, cudaStream_t s);
+// closing half kick of the last step; ke_row (optional) as above
+int launch_final_kick(Ctx* c, double* v, const double* f, const double* coef, double* ke_row,
+                      cudaStream_t s);
+// thermo (nsteps x 3: potential, kinetic [eV], total) from the 8-double rows
+int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, double* thermo,
+                       cudaStream_t s);
 
 }  // namespace tgb

@@ -41,14 +41,13 @@ GridDev to_dev(const Grid& g) {
   return d;
 }
 
-__global__ void k_bin(int n, const double* __restrict__ x, const int* __restrict__ types,
-                      GridDev g, int* __restrict__ cell_of, int* __restrict__ cell_count,
-                      double* __restrict__ origin, float4* __restrict__ pos32,
+__global__ void k_bin(int n, const double* __restrict__ x, GridDev g, double scale,
+                      int* __restrict__ cell_of, int* __restrict__ cell_count,
+                      double* __restrict__ origin, double* __restrict__ qorg,
                       int* __restrict__ flags) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int c3[3];
-  float uf[3];
   bool finite = true;
   for (int a = 0; a < 3; ++a) {
     double xa = x[3 * (size_t)i + a];
@@ -56,19 +55,20 @@ __global__ void k_bin(int n, const double* __restrict__ x, const int* __restrict
       finite = false;
       xa = 0.0;
     }
-    double w = xa - g.L[a] * floor(xa * g.invL[a]);
+    const double k = floor(xa * g.invL[a]);  // periodic image
+    const double w = xa - g.L[a] * k;
     int c = (int)(w * g.invh[a]);
     c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-    double u = w - c * g.h[a];
-    origin[3 * (size_t)i + a] = xa - u;
-    uf[a] = (float)u;
+    // origin = image corner of the cell; offsets x - o start inside the cell
+    const double o = fma(k, g.L[a], c * g.h[a]);
+    origin[3 * (size_t)i + a] = o;
+    qorg[3 * (size_t)i + a] = 6755399441055744.0 - o * scale;
     c3[a] = c;
   }
   if (!finite) atomicOr(&flags[FLAG_NONFINITE], 1);
   int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
   cell_of[i] = cell;
   atomicAdd(&cell_count[cell], 1);
-  pos32[i] = make_float4(uf[0], uf[1], uf[2], __int_as_float(types[i]));
 }
 
 // --- exclusive scan over m ints (three passes) ---
@@ -169,83 +169,121 @@ __device__ __forceinline__ bool exact_member(const double* __restrict__ x, int i
   return r2 <= rc2;
 }
 
-template <int NS>
+__device__ __forceinline__ void warp_atomic_max(int* dst, int v, bool active) {
+  v = active ? v : 0;
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(dst, v);
+}
+
+// squared short-list radii per (type i, type j): filter radius plus margin
+struct Radii {
+  float r2[TERSOFF_MAX_SPECIES * TERSOFF_MAX_SPECIES];
+};
+
+// Atoms of each cell in ascending index order, so that list order (stencil
+// order, then cell order) does not depend on the scatter's atomic order.
+__global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
+                            int* __restrict__ cell_atoms) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int s0 = cell_start[c], s1 = cell_start[c + 1];
+  for (int a = s0 + 1; a < s1; ++a) {
+    const int key = cell_atoms[a];
+    int b = a - 1;
+    while (b >= s0 && cell_atoms[b] > key) {
+      cell_atoms[b + 1] = cell_atoms[b];
+      --b;
+    }
+    cell_atoms[b + 1] = key;
+  }
+}
+
 __global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-    const int* __restrict__ cell_atoms, GridDev g, double rc2, float lo2, float hi2,
-    const float* __restrict__ filt2, int cap, uint32_t* __restrict__ nbr,
-    int* __restrict__ cnt, int* __restrict__ flags) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float4 pi = pos32[i];
-  const int ti = __float_as_int(pi.w);
-  const int ci = cell_of[i];
-  const int cx = ci % g.nc[0];
-  const int cy = (ci / g.nc[0]) % g.nc[1];
-  const int cz = ci / (g.nc[0] * g.nc[1]);
-  int count = 0, nshort = 0;
-  for (int oz = -1; oz <= 1; ++oz) {
-    int az = cz + oz;
-    az += (az < 0) ? g.nc[2] : 0;
-    az -= (az >= g.nc[2]) ? g.nc[2] : 0;
-    for (int oy = -1; oy <= 1; ++oy) {
-      int ay = cy + oy;
-      ay += (ay < 0) ? g.nc[1] : 0;
-      ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
-      for (int ox = -1; ox <= 1; ++ox) {
-        int ax = cx + ox;
-        ax += (ax < 0) ? g.nc[0] : 0;
-        ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
-        const int c = (az * g.nc[1] + ay) * g.nc[0] + ax;
-        const float sx = ox * g.hf[0], sy = oy * g.hf[1], sz = oz * g.hf[2];
-        const uint32_t code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) |
-                              ((uint32_t)(oz + 1) << 30);
-        const int s1 = cell_start[c + 1];
-        for (int s = cell_start[c]; s < s1; ++s) {
-          const int j = cell_atoms[s];
-          if (j == i) continue;
-          const float4 pj = pos32[j];
-          const float dx = (pj.x - pi.x) + sx;
-          const float dy = (pj.y - pi.y) + sy;
-          const float dz = (pj.z - pi.z) + sz;
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          bool in;
-          if (r2 < lo2)
-            in = true;
-          else if (r2 > hi2)
-            in = false;
-          else
-            in = exact_member(x, i, j, g, rc2, dx, dy, dz);
-          if (in) {
-            if (count < cap) nbr[(size_t)count * n + i] = (uint32_t)j | code;
-            ++count;
-            const int tj = __float_as_int(pj.w);
-            if (r2 <= filt2[ti * NS + tj]) ++nshort;
+    const int* __restrict__ cell_atoms, GridDev g, double rc2, float lo2, float hi2, int cap,
+    uint32_t* __restrict__ nbr, int* __restrict__ cnt, Radii lim, int ns,
+    uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
+    int* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < n;
+  int count = 0;
+  int z = 0;
+  if (active) {
+    const float4 pi = pos32[i];
+    const int ti = __float_as_int(pi.w);
+    const int ci = cell_of[i];
+    const int cx = ci % g.nc[0];
+    const int cy = (ci / g.nc[0]) % g.nc[1];
+    const int cz = ci / (g.nc[0] * g.nc[1]);
+    for (int oz = -1; oz <= 1; ++oz) {
+      int az = cz + oz;
+      az += (az < 0) ? g.nc[2] : 0;
+      az -= (az >= g.nc[2]) ? g.nc[2] : 0;
+      for (int oy = -1; oy <= 1; ++oy) {
+        int ay = cy + oy;
+        ay += (ay < 0) ? g.nc[1] : 0;
+        ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
+        for (int ox = -1; ox <= 1; ++ox) {
+          int ax = cx + ox;
+          ax += (ax < 0) ? g.nc[0] : 0;
+          ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
+          const int c = (az * g.nc[1] + ay) * g.nc[0] + ax;
+          const float sx = ox * g.hf[0], sy = oy * g.hf[1], sz = oz * g.hf[2];
+          const uint32_t code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) |
+                                ((uint32_t)(oz + 1) << 30);
+          const int s1 = cell_start[c + 1];
+          for (int s = cell_start[c]; s < s1; ++s) {
+            const int j = cell_atoms[s];
+            if (j == i) continue;
+            const float4 pj = pos32[j];
+            const float dx = (pj.x - pi.x) + sx;
+            const float dy = (pj.y - pi.y) + sy;
+            const float dz = (pj.z - pi.z) + sz;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            bool in;
+            if (r2 < lo2)
+              in = true;
+            else if (r2 > hi2)
+              in = false;
+            else
+              in = exact_member(x, i, j, g, rc2, dx, dy, dz);
+            if (in) {
+              const uint32_t e = (uint32_t)j | code;
+              if (count < cap) nbr[(size_t)count * n + i] = e;
+              ++count;
+              // short list: within the filter radius plus the margin
+              if (r2 <= lim.r2[ti * ns + __float_as_int(pj.w)]) {
+                if (z < cap) shortl[(size_t)z * n + i] = e;
+                ++z;
+              }
+            }
           }
         }
       }
     }
+    cnt[i] = count;
+    zcnt[i] = z;
   }
-  cnt[i] = count;
-  atomicMax(&flags[FLAG_OVERFLOW], count);
-  atomicMax(&flags[FLAG_SHORT_MAX], nshort);
-  // insertion sort of the stored entries by neighbour index
-  const int m = count < cap ? count : cap;
-  for (int a = 1; a < m; ++a) {
-    const uint32_t key = nbr[(size_t)a * n + i];
-    const uint32_t kj = key & ENTRY_JMASK;
-    int b = a - 1;
-    while (b >= 0) {
-      const uint32_t eb = nbr[(size_t)b * n + i];
-      if ((eb & ENTRY_JMASK) <= kj) break;
-      nbr[(size_t)(b + 1) * n + i] = eb;
-      --b;
-    }
-    nbr[(size_t)(b + 1) * n + i] = key;
+  warp_atomic_max(&flags[FLAG_OVERFLOW], count, active);
+  warp_atomic_max(&flags[FLAG_SHORT_MAX], z, active);
+  if (__any_sync(0xffffffffu, active && count > cap) && (threadIdx.x & 31) == 0)
+    atomicOr(&flags[FLAG_OVF_ANY], 1);
+  // bucket by short-list size (<= 4, <= 8, more); one atomic per warp and bucket
+  const int b = z <= 4 ? 0 : (z <= 8 ? 1 : 2);
+  const int lane = threadIdx.x & 31;
+  for (int q = 0; q < 3; ++q) {
+    const unsigned msk = __ballot_sync(0xffffffffu, active && b == q);
+    if (msk == 0u) continue;
+    const int leader = __ffs(msk) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&flags[FLAG_BUCKET + q], __popc(msk));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (active && b == q) bucket[(size_t)q * n + base + __popc(msk & ((1u << lane) - 1u))] = i;
   }
 }
 
+// Copies the lists out row-major, each row sorted by neighbour index.
 __global__ void k_export(int n, const uint32_t* __restrict__ nbr, const int* __restrict__ cnt,
                          int cap_in, int cap_out, int* __restrict__ out_cnt,
                          int* __restrict__ out_nbr) {
@@ -254,8 +292,18 @@ __global__ void k_export(int n, const uint32_t* __restrict__ nbr, const int* __r
   int c = cnt[i];
   out_cnt[i] = c;
   int m = c < cap_in ? c : cap_in;
-  for (int s = 0; s < cap_out; ++s)
-    out_nbr[(size_t)i * cap_out + s] = (s < m) ? (int)(nbr[(size_t)s * n + i] & ENTRY_JMASK) : -1;
+  m = m < cap_out ? m : cap_out;
+  int* row = out_nbr + (size_t)i * cap_out;
+  for (int s = 0; s < m; ++s) {
+    const int key = (int)(nbr[(size_t)s * n + i] & ENTRY_JMASK);
+    int b = s - 1;
+    while (b >= 0 && row[b] > key) {
+      row[b + 1] = row[b];
+      --b;
+    }
+    row[b + 1] = key;
+  }
+  for (int s = m; s < cap_out; ++s) row[s] = -1;
 }
 
 template <class T>
@@ -291,11 +339,14 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   GridDev g = to_dev(G);
   const int B = 256;
   const int nb = (n + B - 1) / B;
+  const double scale = ldexp(1.0, G.fix_shift);
   TGB_CUDA(c, cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (ncell + 1), s));
   if (n > 0) {
-    k_bin<<<nb, B, 0, s>>>(n, x, c->d_types, g, c->d_cell_of, c->d_cell_count, c->d_origin,
-                           c->d_pos32, c->d_flags);
+    k_bin<<<nb, B, 0, s>>>(n, x, g, scale, c->d_cell_of, c->d_cell_count, c->d_origin,
+                           c->d_qorg, c->d_flags);
     c->launches++;
+    int st = launch_pack_positions(c, x, true, s);
+    if (st) return st;
   }
   const int m = (int)ncell + 1;
   const int ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
@@ -305,7 +356,9 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   c->launches += 3;
   if (n > 0) {
     k_scatter<<<nb, B, 0, s>>>(n, c->d_cell_of, c->d_cell_fill, c->d_cell_atoms);
-    c->launches++;
+    k_cell_sort<<<(int)((ncell + 255) / 256), 256, 0, s>>>((int)ncell, c->d_cell_start,
+                                                           c->d_cell_atoms);
+    c->launches += 2;
   }
   const double rc2 = c->r_list * c->r_list;
   // FP32 classification band: the FP32 r^2 of a stencil candidate differs from
@@ -314,23 +367,18 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const double band = 64.0 * (4.0 * hmax) * (4.0 * hmax) * 1.2e-7 + 1e-6;
   const float lo2 = (float)(rc2 - band);
   const float hi2 = (float)(rc2 + band);
-  if (n > 0) {
-    switch (c->ns) {
-#define TGB_NEIGH(NSV)                                                                     \
-  case NSV:                                                                                \
-    k_neigh<NSV><<<(n + 127) / 128, 128, 0, s>>>(n, x, c->d_pos32, c->d_cell_of,          \
-                                                 c->d_cell_start, c->d_cell_atoms, g, rc2, \
-                                                 lo2, hi2, c->d_filt32, c->cap, c->d_nbr,  \
-                                                 c->d_cnt, c->d_flags);                    \
-    break;
-      TGB_NEIGH(1)
-      TGB_NEIGH(2)
-      TGB_NEIGH(3)
-      TGB_NEIGH(4)
-#undef TGB_NEIGH
-      default:
-        return fail(c, TERSOFF_E_STATE, "unsupported species count");
+  Radii lim;
+  for (int q = 0; q < TERSOFF_MAX_SPECIES * TERSOFF_MAX_SPECIES; ++q) lim.r2[q] = 0.0f;
+  for (int a = 0; a < c->ns; ++a)
+    for (int b = 0; b < c->ns; ++b) {
+      const double r = c->filt[(size_t)a * c->ns + b] + c->margin;
+      lim.r2[a * c->ns + b] = (float)(r * r * (1.0 + 1e-6));
     }
+  if (n > 0) {
+    k_neigh<<<(n + 127) / 128, 128, 0, s>>>(n, x, c->d_pos32, c->d_cell_of, c->d_cell_start,
+                                            c->d_cell_atoms, g, rc2, lo2, hi2, c->cap, c->d_nbr,
+                                            c->d_cnt, lim, c->ns, c->d_short, c->d_zcnt,
+                                            c->d_bucket, c->d_flags);
     c->launches++;
   }
   TGB_CUDA(c, cudaGetLastError());

@@ -123,14 +123,23 @@ template <class T> struct FwdArgs {
   int ns;                // species count (used when the kernel's NS is 0)
   const uint32_t* nbr;   // slot-major skin list
   const int* cnt;
+  const int* types;
   const float4* pos32;   // mixed: (u, type bits)
   const int4* posq;      // mixed: fixed-point u, type
   const dpos4* pos64;  // fp64: (u, type)
   const T* rec;          // ns^3 derived records
+  T prm1[RSTRIDE];       // the record of a one-species table (read from the
+                         // kernel-parameter constant bank)
   const T* filt2;        // ns x ns squared filter radii
   T h[3];                // cell edges
   int hq[3];             // cell edges in fixed point
   float qinv;            // 2^-fix_shift
+  const uint32_t* shortl;  // slot-major short list (filter radius + margin)
+  const int* zcnt;       // short-list counts
+  int zs_cap;            // short-list capacity
+  const int* order;      // atoms of this launch (a short-list size bucket)
+  const int* n_items;    // device count of atoms in order
+  float dlim2;           // short list valid while max squared displacement <= dlim2
   double* f;             // forces, accumulated
   double* acc;           // energy, virial (6)
   double* eatom;         // optional per-atom energy
@@ -143,11 +152,11 @@ template <> struct Pos<float> {
   // filter precision (cheap): float offsets
   static __device__ __forceinline__ void coarse(const FwdArgs<float>& a, int j, float& x,
                                                 float& y, float& z, int& t) {
-    float4 p = __ldg(&a.pos32[j]);
-    x = p.x;
-    y = p.y;
-    z = p.z;
-    t = __float_as_int(p.w);
+    int4 p = __ldg(&a.posq[j]);
+    x = (float)p.x * a.qinv;
+    y = (float)p.y * a.qinv;
+    z = (float)p.z * a.qinv;
+    t = p.w;
   }
 };
 template <> struct Pos<double> {
@@ -286,19 +295,24 @@ __device__ __forceinline__ void atomic_add3(double* f, int j, double a, double b
 
 // ---------------------------------------------------------------- general path
 // Algorithm 2 directly over S_i, cutoff tests inside the loops.
+// record offset of (ti, tj, tk); a one-species table has a single record
+template <int NS>
+__device__ __forceinline__ int rec_off(int ns, int ti, int tj, int tk) {
+  return NS == 1 ? 0 : ((ti * ns + tj) * ns + tk) * RSTRIDE;
+}
+
 template <class T, int NS, bool LAM3>
-__device__ __noinline__ void general_atom(const FwdArgs<T>& a, const T* srec, int i, int ti,
-                                          T& ei, T* w) {
+__device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec, int i, int ti,
+                                          const uint32_t* list, int c, T& ei, T* w) {
   using P = typename SelfPos<T>::type;
   const int ns = NS > 0 ? NS : a.ns;
   const P pi = self_pos<T>(a, i);
-  const int c = min(a.cnt[i], a.cap);
   T fix = 0, fiy = 0, fiz = 0;
   for (int sj = 0; sj < c; ++sj) {
     T dxj, dyj, dzj;
     int j, tj;
-    Bond<T>::vec(a, pi, a.nbr[(size_t)sj * a.n + i], dxj, dyj, dzj, j, tj);
-    const T* p2 = srec + ((ti * ns + tj) * ns + tj) * RSTRIDE;
+    Bond<T>::vec(a, pi, list[(size_t)sj * a.n + i], dxj, dyj, dzj, j, tj);
+    const T* p2 = srec + rec_off<NS>(ns, ti, tj, tj);
     const T r2j = dxj * dxj + dyj * dyj + dzj * dzj;
     const T rij = r2j * M<T>::rsqrt_nr(r2j);
     if (!(rij < p2[K_ROUT2])) continue;
@@ -309,8 +323,8 @@ __device__ __noinline__ void general_atom(const FwdArgs<T>& a, const T* srec, in
       if (sk == sj) continue;
       T dxk, dyk, dzk;
       int k, tk;
-      Bond<T>::vec(a, pi, a.nbr[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
-      const T* p3 = srec + ((ti * ns + tj) * ns + tk) * RSTRIDE;
+      Bond<T>::vec(a, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
+      const T* p3 = srec + rec_off<NS>(ns, ti, tj, tk);
       const T r2k = dxk * dxk + dyk * dyk + dzk * dzk;
       const T rik = r2k * M<T>::rsqrt_nr(r2k);
       if (!(rik < p3[K_ROUT3])) continue;
@@ -327,8 +341,8 @@ __device__ __noinline__ void general_atom(const FwdArgs<T>& a, const T* srec, in
       if (sk == sj) continue;
       T dxk, dyk, dzk;
       int k, tk;
-      Bond<T>::vec(a, pi, a.nbr[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
-      const T* p3 = srec + ((ti * ns + tj) * ns + tk) * RSTRIDE;
+      Bond<T>::vec(a, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
+      const T* p3 = srec + rec_off<NS>(ns, ti, tj, tk);
       const T r2k = dxk * dxk + dyk * dyk + dzk * dzk;
       const T rik = r2k * M<T>::rsqrt_nr(r2k);
       if (!(rik < p3[K_ROUT3])) continue;
@@ -374,17 +388,41 @@ __device__ __noinline__ void general_atom(const FwdArgs<T>& a, const T* srec, in
 }
 
 // ---------------------------------------------------------------- reduction
+// Energy and virial: the 7 per-thread values (padded to 8) are reduce-scattered
+// across the warp (halving exchanges: 4, 2, 1 values), then summed over the
+// remaining lanes; lanes 0, 4, ..., 28 end with the 8 warp totals. Warp totals
+// are summed in double over the block and added to acc with one atomic each.
 template <class T>
 __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc) {
-  __shared__ double part[BLOCK / 32][7];
-  T v[7] = {ei, w[0], w[1], w[2], w[3], w[4], w[5]};
-#pragma unroll
-  for (int q = 0; q < 7; ++q)
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  __shared__ double part[BLOCK / 32][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0)
+  T v[8] = {ei, w[0], w[1], w[2], w[3], w[4], w[5], T(0)};
+  const bool hi16 = lane & 16;
 #pragma unroll
-    for (int q = 0; q < 7; ++q) part[wid][q] = to_f64(v[q]);
+  for (int q = 0; q < 4; ++q) {
+    const T send = hi16 ? v[q] : v[q + 4];
+    const T keep = hi16 ? v[q + 4] : v[q];
+    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  const bool hi8 = lane & 8;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const T send = hi8 ? v[q] : v[q + 2];
+    const T keep = hi8 ? v[q + 2] : v[q];
+    v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const bool hi4 = lane & 4;
+  {
+    const T send = hi4 ? v[0] : v[1];
+    const T keep = hi4 ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  if ((lane & 3) == 0) {
+    const int idx = (hi16 ? 4 : 0) + (hi8 ? 2 : 0) + (hi4 ? 1 : 0);
+    part[wid][idx] = to_f64(v[0]);
+  }
   __syncthreads();
   if (threadIdx.x < 7) {
     double s = 0.0;
@@ -394,46 +432,79 @@ __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc
 }
 
 // ---------------------------------------------------------------- the kernel
-template <class T, int NS, int ZC, bool LAM3>
-__global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
-  constexpr int SNS = NS > 0 ? NS : TERSOFF_MAX_SPECIES;
-  __shared__ T srec[SNS * SNS * SNS * RSTRIDE];
+template <class T, int NS, int ZC, int MODE>
+__global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
+  constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
+  constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
+  __shared__ T srec_s[SREC];
   __shared__ T sfilt[SNS * SNS];
   const int ns = NS > 0 ? NS : a.ns;
-  for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += BLOCK) srec[q] = a.rec[q];
+  if (NS != 1)
+    for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += BLOCK) srec_s[q] = a.rec[q];
   if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = a.filt2[threadIdx.x];
   __syncthreads();
+  // parameters: shared memory for several species (type-dependent records),
+  // the constant bank for one species (uniform, operands of the FP instructions)
+  const T* srec = NS == 1 ? a.prm1 : srec_s;
+  constexpr bool LAM3 = MODE == 1;
 
-  const int i = blockIdx.x * BLOCK + threadIdx.x;
+  const int n_items = *a.n_items;
+  // the stored short list holds every atom that can be inside a cutoff while no
+  // atom has moved more than half the list margin since the build (uniform)
+  const bool use_short =
+      __int_as_float(*(volatile const int*)&a.flags[FLAG_DMAX]) <= a.dlim2;
   T ei = 0;
   T w[6] = {0, 0, 0, 0, 0, 0};
-  if (i < a.n) {
-    T xi, yi, zi;
+  bool any = false;
+  for (int item = blockIdx.x * BLOCK + threadIdx.x; item < n_items;
+       item += gridDim.x * BLOCK) {
+    any = true;
+    const int i = a.order[item];
+    T eatom_i = T(0);
     int ti;
-    Pos<T>::coarse(a, i, xi, yi, zi, ti);
-    const int c = min(a.cnt[i], a.cap);
-    // 1. filter the skin list into a bit mask
+    int z;
     unsigned long long mask = 0ull;
-    const bool fits = c <= 64;
-    if (fits) {
-      for (int s = 0; s < c; ++s) {
-        const uint32_t e = a.nbr[(size_t)s * a.n + i];
-        int j, ox, oy, oz;
-        decode(e, j, ox, oy, oz);
-        T xj, yj, zj;
-        int tj;
-        Pos<T>::coarse(a, j, xj, yj, zj, tj);
-        const T dx = (xj - xi) + ox * a.h[0];
-        const T dy = (yj - yi) + oy * a.h[1];
-        const T dz = (zj - zi) + oz * a.h[2];
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
+    const uint32_t* list;
+    int c;
+    bool general;
+    if (use_short) {
+      z = a.zcnt[i];
+      ti = a.types[i];
+      list = a.shortl;
+      c = z;
+      general = z > ZC || z > a.zs_cap;
+      if (z > a.zs_cap) {  // short list truncated: use the skin list
+        list = a.nbr;
+        c = min(a.cnt[i], a.cap);
       }
+    } else {
+      // filter the skin list into a bit mask (Sec. IV-D)
+      T xi, yi, zi;
+      Pos<T>::coarse(a, i, xi, yi, zi, ti);
+      c = min(a.cnt[i], a.cap);
+      list = a.nbr;
+      const bool fits = c <= 64;
+      if (fits) {
+        for (int s = 0; s < c; ++s) {
+          const uint32_t e = a.nbr[(size_t)s * a.n + i];
+          int j, ox, oy, oz;
+          decode(e, j, ox, oy, oz);
+          T xj, yj, zj;
+          int tj;
+          Pos<T>::coarse(a, j, xj, yj, zj, tj);
+          const T dx = (xj - xi) + ox * a.h[0];
+          const T dy = (yj - yi) + oy * a.h[1];
+          const T dz = (zj - zi) + oz * a.h[2];
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
+        }
+      }
+      z = __popcll(mask);
+      general = !fits || z > ZC;
     }
-    const int z = __popcll(mask);
-    if (!fits || z > ZC) {
+    if (general) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
-      general_atom<T, NS, LAM3>(a, srec, i, ti, ei, w);
+      general_atom<T, NS, LAM3>(a, srec, i, ti, list, c, eatom_i, w);
     } else {
       using P = typename SelfPos<T>::type;
       const P pi = self_pos<T>(a, i);
@@ -448,11 +519,17 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
         jj[q] = i;
         tt[q] = 0;
         if (q < z) {
-          const int s = __ffsll(mask) - 1;
-          mask &= mask - 1ull;
+          uint32_t e;
+          if (use_short) {
+            e = a.shortl[(size_t)q * a.n + i];
+          } else {
+            const int s = __ffsll(mask) - 1;
+            mask &= mask - 1ull;
+            e = a.nbr[(size_t)s * a.n + i];
+          }
           T dx, dy, dz;
           int j, tj;
-          Bond<T>::vec(a, pi, a.nbr[(size_t)s * a.n + i], dx, dy, dz, j, tj);
+          Bond<T>::vec(a, pi, e, dx, dy, dz, j, tj);
           const T r2 = dx * dx + dy * dy + dz * dz;
           const T inv = M<T>::rsqrt_nr(r2);
           ri[q] = inv;
@@ -468,10 +545,80 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
 #pragma unroll
       for (int q = 0; q < ZC; ++q) fx[q] = fy[q] = fz[q] = T(0);
 
+      if (MODE == 2) {
+        // Symmetric tables without a lambda3 term: the angular part of
+        // zeta(i,j,k) and zeta(i,k,j) is the same, and f_C(r_ik) does not
+        // depend on j. Each unordered neighbour pair {j,k} is evaluated once
+        // for the zeta sums and once (recomputed) for the forces.
+        T fc3[ZC], dfc3[ZC], zeta[ZC], dzt[ZC];
+#pragma unroll
+        for (int q = 0; q < ZC; ++q) {
+          fc3[q] = dfc3[q] = zeta[q] = dzt[q] = T(0);
+          if (q < z) {
+            const T* pq = srec + rec_off<NS>(ns, ti, tt[q], tt[q]);
+            if (rr[q] < pq[K_ROUT3])
+              cutoff<T>(pq, K_R3, K_PID3, K_DFC3, K_RIN3, rr[q], fc3[q], dfc3[q]);
+          }
+        }
+        // pass 1: zeta_ij = sum_k f_C(r_ik) g(theta_ijk)
+#pragma unroll
+        for (int qj = 0; qj < ZC; ++qj)
+#pragma unroll
+          for (int qk = qj + 1; qk < ZC; ++qk)
+            if (qk < z) {
+              const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
+              const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
+              const T t = p3[K_H] - cs;
+              const T t2 = t * t;
+              const T q = M<T>::rcp_nr(p3[K_D2] + t2);
+              const T g = p3[K_GC2D2] * (t2 * q) + p3[K_GAMMA];
+              zeta[qj] += fc3[qk] * g;
+              zeta[qk] += fc3[qj] * g;
+            }
+        // pair terms, b_ij and dV/dzeta
+#pragma unroll
+        for (int qj = 0; qj < ZC; ++qj)
+          if (qj < z) {
+            const T* p2 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qj]);
+            if (rr[qj] < p2[K_ROUT2]) {
+              T V, dVdr, dz;
+              pair<T>(p2, rr[qj], zeta[qj], V, dVdr, dz);
+              eatom_i += V;
+              dzt[qj] = dz;
+              fx[qj] -= dVdr * ux[qj];
+              fy[qj] -= dVdr * uy[qj];
+              fz[qj] -= dVdr * uz[qj];
+            }
+          }
+        // pass 2: -dV/dzeta_ij d zeta_ij/dx - dV/dzeta_ik d zeta_ik/dx per pair {j,k}
+#pragma unroll
+        for (int qj = 0; qj < ZC; ++qj)
+#pragma unroll
+          for (int qk = qj + 1; qk < ZC; ++qk)
+            if (qk < z) {
+              const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
+              const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
+              const T t = p3[K_H] - cs;
+              const T t2 = t * t;
+              const T q = M<T>::rcp_nr(p3[K_D2] + t2);
+              const T g = p3[K_GC2D2] * (t2 * q) + p3[K_GAMMA];
+              const T dg = -p3[K_G2C2] * t * q * q;
+              const T A = -(dzt[qj] * fc3[qk] + dzt[qk] * fc3[qj]) * dg;
+              const T cj = A * ri[qj], ck = A * ri[qk];
+              const T bj = -dzt[qk] * dfc3[qj] * g;
+              const T bk = -dzt[qj] * dfc3[qk] * g;
+              fx[qj] += cj * (ux[qk] - cs * ux[qj]) + bj * ux[qj];
+              fy[qj] += cj * (uy[qk] - cs * uy[qj]) + bj * uy[qj];
+              fz[qj] += cj * (uz[qk] - cs * uz[qj]) + bj * uz[qj];
+              fx[qk] += ck * (ux[qj] - cs * ux[qk]) + bk * ux[qk];
+              fy[qk] += ck * (uy[qj] - cs * uy[qk]) + bk * uy[qk];
+              fz[qk] += ck * (uz[qj] - cs * uz[qk]) + bk * uz[qk];
+            }
+      } else
 #pragma unroll
       for (int qj = 0; qj < ZC; ++qj) {
         if (qj < z) {
-          const T* p2 = srec + ((ti * ns + tt[qj]) * ns + tt[qj]) * RSTRIDE;
+          const T* p2 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qj]);
           const T rij = rr[qj];
           if (rij < p2[K_ROUT2]) {
             // first K loop: zeta_ij and its derivatives (Sec. IV-A)
@@ -481,7 +628,7 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
             for (int qk = 0; qk < ZC; ++qk) {
               gkx[qk] = gky[qk] = gkz[qk] = T(0);
               if (qk != qj && qk < z) {
-                const T* p3 = srec + ((ti * ns + tt[qj]) * ns + tt[qk]) * RSTRIDE;
+                const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
                 const T rik = rr[qk];
                 if (rik < p3[K_ROUT3]) {
                   const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
@@ -501,7 +648,7 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
             }
             T V, dVdr, dz;
             pair<T>(p2, rij, zeta, V, dVdr, dz);
-            ei += V;
+            eatom_i += V;
             fx[qj] -= dVdr * ux[qj] + dz * gjx;
             fy[qj] -= dVdr * uy[qj] + dz * gjy;
             fz[qj] -= dVdr * uz[qj] + dz * gjz;
@@ -536,9 +683,10 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const FwdArgs<T> a) {
       }
       atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
     }
-    if (a.eatom) a.eatom[i] = to_f64(ei);
+    if (a.eatom) a.eatom[i] = to_f64(eatom_i);
+    ei += eatom_i;
   }
-  block_reduce_store<T>(ei, w, a.acc);
+  if (__syncthreads_or(any)) block_reduce_store<T>(ei, w, a.acc);
 }
 
 }  // namespace fwd

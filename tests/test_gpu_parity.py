@@ -331,3 +331,56 @@ def test_md_mixed_energy_conservation_and_host_api(T):
     assert np.abs(thh.numpy()[:, 2] - thermo[:, 2]).max() < 1e-3
     ctx.close()
     ctx2.close()
+
+
+def test_md_graph_replay_matches_eager(T):
+    # the same FP64 MD through direct launches and through a replayed CUDA graph
+    x, v, t, box = _md_inputs(ncell=4, seed=52)
+    table = si_table()
+    mass = [W.MASS_AMU["Si"]]
+    out = []
+    for graphs in (False, True):
+        ctx = T.Context(T.FP64)
+        ctx.set_graphs(graphs)
+        ctx.params(table)
+        xd, vd = dev(x), dev(v)
+        ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+        fd = torch.zeros_like(xd)
+        ctx.compute(xd, None, fd)
+        th = torch.zeros((10, 3), dtype=torch.float64, device="cuda")
+        for _ in range(3):  # capture once, replay twice
+            ctx.md_step(xd, vd, fd, mass, 0.001, 10, 10, th)
+        torch.cuda.synchronize()
+        out.append((xd.cpu().numpy(), vd.cpu().numpy(), th.cpu().numpy()))
+        ctx.close()
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-10
+    assert np.abs(out[0][1] - out[1][1]).max() < 1e-8
+    assert np.abs(out[0][2] - out[1][2]).max() < 1e-8
+
+
+def test_md_graph_overflow_rolls_back(T):
+    # a hot random packing with the list capacity set to the initial maximum:
+    # a rebuild inside the replayed graph overflows, the state is restored and
+    # the steps rerun; the trajectory still matches the oracle
+    x, t, box = S.packing_cell(n=300, c_frac=0.0, seed=61)
+    table = sic_table()
+    mass = [W.MASS_AMU["Si"], W.MASS_AMU["C"]]
+    rng = np.random.Generator(np.random.Philox(62))
+    v = W.maxwell_velocities(t, np.array(mass), 6000.0, rng)
+    nsteps, every = 40, 2
+    xo, vo, thermo_o, fo = oracle.md_run(x, v, t, box, table, mass, 0.001, nsteps, RC + 1.0,
+                                         every, cap=96)
+    cnt_ref, _ = oracle.neighbors(x, box, RC + 1.0)
+    ctx = T.Context(T.FP64)
+    ctx.params(table)
+    ctx.set_neighbor_capacity(int(cnt_ref.max()))
+    xd, vd = dev(x), dev(v)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+    fd = torch.zeros_like(xd)
+    ctx.compute(xd, None, fd)
+    ctx.md_step(xd, vd, fd, mass, 0.001, nsteps, every)
+    torch.cuda.synchronize()
+    cap, _ = ctx.neighbor_capacity()
+    assert cap > cnt_ref.max()  # the overflow was caught and the capacity grown
+    assert np.abs(xd.cpu().numpy() - xo).max() < 1e-8
+    ctx.close()
