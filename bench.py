@@ -87,6 +87,8 @@ class ClockSampler:
         self.path = None
 
     def start(self):
+        """Starts sampling and waits until the first sample is written, so the
+        sampler's start-up does not fall inside the timed region."""
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
@@ -95,6 +97,9 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=self.fh, stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.05)
         except Exception:
             self.proc = None
 
@@ -210,11 +215,15 @@ def run_ours(args):
         ctx.compute(xd, e, fd, w)
         return ctx, xd, vd, td, fd, e, w
 
-    def timed(ctx, xd, vd, fd, steps, warmup, sampler=None):
+    def timed(ctx, xd, vd, fd, steps, warmup, sampler=None, instrument=False):
+        """Sum of per-step device times (CUDA events on the launching stream,
+        L2 flushed before each step). instrument: also record CUDA events
+        around the force kernel, neighbour builds and integration kernels
+        inside the steps (this slows the steps, so it is a separate pass)."""
         for _ in range(warmup):
             ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
         torch.cuda.synchronize()
-        ctx.set_timing(True)
+        ctx.set_timing(instrument)
         l0 = ctx.launch_count()
         stream = torch.cuda.current_stream()
         ms = []
@@ -264,12 +273,30 @@ def run_ours(args):
                    FLOP_TRIPLET * ntrip)
     mufu_launch = MUFU_SHORT * nshort + MUFU_PAIR * npair + MUFU_TRIPLET * ntrip
 
-    # ---------------- timed: mixed (headline), then FP64
+    # ---------------- scatter mode chosen by measurement (short trial of each)
+    trial = {}
+    for name, mode in (("gather", T.SCATTER_GATHER), ("atomic", T.SCATTER_ATOMIC)):
+        ctxm.set_scatter(mode)
+        trial[name] = timed(ctxm, xdm, vdm, fm, max(3, args.steps // 5), 2)[0]
+    best = min(trial, key=trial.get)
+    ctxm.set_scatter(T.SCATTER_GATHER if best == "gather" else T.SCATTER_ATOMIC)
+    trial64 = {}
+    for name, mode in (("gather", T.SCATTER_GATHER), ("atomic", T.SCATTER_ATOMIC)):
+        ctx64.set_scatter(mode)
+        trial64[name] = timed(ctx64, xd64, vd64, f64, 2, 1)[0]
+    best64 = min(trial64, key=trial64.get)
+    ctx64.set_scatter(T.SCATTER_GATHER if best64 == "gather" else T.SCATTER_ATOMIC)
+
+    # ---------------- timed: mixed (headline), then FP64; then instrumented
+    # passes of the same length for the kernel durations
     sampler = ClockSampler(smi_index(local))
-    ms_m, launches_m, kern_m, build_m, integ_m, clocks = timed(ctxm, xdm, vdm, fm, args.steps,
-                                                               args.warmup, sampler)
-    ms_d, launches_d, kern_d, build_d, integ_d, _ = timed(ctx64, xd64, vd64, f64, args.steps,
-                                                          args.warmup)
+    ms_m, launches_m, _, _, _, clocks = timed(ctxm, xdm, vdm, fm, args.steps, args.warmup,
+                                              sampler)
+    ms_d, launches_d, _, _, _, _ = timed(ctx64, xd64, vd64, f64, args.steps, args.warmup)
+    ms_mi, _, kern_m, build_m, integ_m, _ = timed(ctxm, xdm, vdm, fm, args.steps, 1,
+                                                  instrument=True)
+    ms_di, _, kern_d, build_d, integ_d, _ = timed(ctx64, xd64, vd64, f64, args.steps, 1,
+                                                  instrument=True)
     units = float(n) * MD_PER_STEP * args.steps
     tmax_m, units_all = aggregate(ms_m, units, world)
     tmax_d, _ = aggregate(ms_d, units, world)
@@ -329,6 +356,8 @@ def run_ours(args):
             "r_list_A": R_LIST,
             "l2": "flushed before each timed step (512 MiB write, outside the timed events)",
             "parallelism": f"replicas x{world}",
+            "scatter": best,
+            "scatter_trial_ms_per_step": {k: v / max(3, args.steps // 5) for k, v in trial.items()},
         },
         "force_error": {
             "reference": "FP64 GPU path (itself within 1e-10 of the FP64 CPU oracle in tests)",
@@ -341,6 +370,7 @@ def run_ours(args):
             "unit": UNIT,
             "ms_per_step": tmax_d / args.steps,
             "dtype": "f64",
+            "scatter": best64,
             "force_kernel_ms": kern_ms_d,
             "force_kernel_tflops": flop_launch / (kern_ms_d * 1e-3) / 1e12,
             "force_kernel_frac_of_fp64_nominal": flop_launch / (kern_ms_d * 1e-3) / 1e12 /
@@ -363,9 +393,13 @@ def run_ours(args):
                                 "triplets": ntrip},
             "kernel_ms": kern_ms,
             "kernel_launches_timed": kern_m[1],
+            "kernel_timing": "CUDA events around each force-kernel launch on its stream, in an "
+                             "instrumented pass of the same steps right after the headline pass",
         },
         "breakdown_ms_per_step": {
-            "force": kern_m[0] / args.steps,
+            "note": "instrumented pass (CUDA events inside the steps; that pass took "
+                    f"{ms_mi / args.steps:.3f} ms per step)",
+            "force_kernel": kern_m[0] / args.steps,
             "neighbor_build": build_m[0] / args.steps,
             "integrate": integ_m[0] / args.steps,
         },
@@ -468,6 +502,7 @@ def run_profile_case(args):
     table = T.mix_tersoff89(*W.element_records(names))
     mass = [W.MASS_AMU[s] for s in names]
     ctx = T.Context(T.MIXED if args.precision == "mixed" else T.FP64)
+    ctx.set_scatter(T.SCATTER_ATOMIC if args.scatter == "atomic" else T.SCATTER_GATHER)
     ctx.params(table)
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
     vd = torch.tensor(v, dtype=torch.float64, device="cuda")
@@ -487,7 +522,7 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -495,6 +530,7 @@ def main():
                     help="profiling case: K force evaluations (or K MD rebuild periods) of "
                          "the benchmark workload, nothing printed")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--scatter", choices=["gather", "atomic"], default="atomic")
     args = ap.parse_args()
     if args.only:
         run_profile_case(args)

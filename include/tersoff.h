@@ -157,6 +157,19 @@ int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int 
                          const double* mass, double dt, int nsteps, int rebuild_every,
                          double* thermo, void* stream);
 
+/* Force scatter. TERSOFF_SCATTER_GATHER (default): every atom stores the
+ * forces its own terms put on each short-list neighbour in per-neighbour
+ * slots (plain stores), and the force on an atom is gathered from its
+ * neighbours' slots in a fixed order, summed with exact error compensation
+ * (mixed path; the rounding error of every float addition is carried and
+ * added in double) or in double (FP64 path): deterministic, no atomics.
+ * TERSOFF_SCATTER_ATOMIC: every force contribution is added to the force
+ * array with FP64 atomics. Results agree to rounding; speed differs by
+ * workload (the benchmark measures both). */
+#define TERSOFF_SCATTER_GATHER 0
+#define TERSOFF_SCATTER_ATOMIC 1
+int tersoff_set_scatter(tersoff_ctx* ctx, int mode);
+
 /* MD execution mode. With enable != 0 (the default) tersoff_md_step records
  * its whole sequence of steps (integration, neighbour rebuilds, forces) once
  * as a CUDA graph and replays it on later calls with the same arguments and

@@ -10,6 +10,8 @@ from ._lib import (  # noqa: F401
     TersoffError,
     FP64,
     MIXED,
+    SCATTER_GATHER,
+    SCATTER_ATOMIC,
     NPARAM,
     load,
     library_path,

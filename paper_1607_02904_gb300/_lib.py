@@ -22,6 +22,8 @@ E_CUDA = 6
 E_STATE = 7
 FP64 = 0
 MIXED = 1
+SCATTER_GATHER = 0
+SCATTER_ATOMIC = 1
 NPARAM = 14
 
 _lib = None
@@ -46,6 +48,7 @@ _SIG = {
     "tersoff_launch_count": ([_P, _P], _I),
     "tersoff_set_timing": ([_P, _I], _I),
     "tersoff_set_graphs": ([_P, _I], _I),
+    "tersoff_set_scatter": ([_P, _I], _I),
     "tersoff_timing": ([_P, _I, _P, _P], _I),
 }
 
@@ -187,6 +190,9 @@ class Context:
                                                   int(x.shape[0]), m.ctypes.data_as(_P),
                                                   float(dt), int(nsteps), int(rebuild_every),
                                                   _ptr(thermo), _stream(stream)))
+
+    def set_scatter(self, mode):
+        self._check(self.lib.tersoff_set_scatter(self.h, int(mode)))
 
     def set_graphs(self, enable=True):
         self._check(self.lib.tersoff_set_graphs(self.h, int(bool(enable))))

@@ -14,6 +14,7 @@ int fail(Ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_fail(Ctx* c, cudaError_t e, const char* where) {
+  cudaGetLastError();  // do not leave a (non-sticky) error for the next caller
   std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" +
                   cudaGetErrorString(e) + ") in " + where;
   return fail(c, TERSOFF_E_CUDA, m);
@@ -124,19 +125,40 @@ int ensure_atoms(Ctx* c, int n) {
   if ((st = dev_alloc(c, &c->d_qref, m))) return st;
   if ((st = dev_alloc(c, &c->d_zcnt, m))) return st;
   if ((st = dev_alloc(c, &c->d_bucket, 3 * m))) return st;
+  if ((st = dev_alloc(c, &c->d_extra, 3 * (m ? m : 1)))) return st;
+  TGB_CUDA(c, cudaMemset(c->d_extra, 0, sizeof(double) * 3 * (m ? m : 1)));
   c->atoms_alloc = m;
   c->nbr_alloc = 0;  // list storage depends on n
   return TERSOFF_OK;
 }
 
 int ensure_nbr(Ctx* c) {
-  size_t need = (size_t)c->cap * (size_t)c->n;
-  c->zs_cap = c->cap;  // a short list never exceeds the skin list
-  if (need <= c->nbr_alloc && c->d_nbr && c->d_short) return TERSOFF_OK;
-  int st = dev_alloc(c, &c->d_nbr, need);
-  if (st) return st;
-  if ((st = dev_alloc(c, &c->d_short, need))) return st;
-  c->nbr_alloc = need;
+  // at least 8 slots per atom: the force kernel loads up to 8 short-list
+  // entries before it reads the count
+  size_t need = (size_t)(c->cap > 8 ? c->cap : 8) * (size_t)c->n;
+  // a short list never exceeds the skin list; reverse slots are bytes
+  c->zs_cap = c->cap < 255 ? c->cap : 255;
+  int st;
+  if (!(need <= c->nbr_alloc && c->d_nbr && c->d_short)) {
+    if ((st = dev_alloc(c, &c->d_nbr, need))) return st;
+    if ((st = dev_alloc(c, &c->d_short, need))) return st;
+    if ((st = dev_alloc(c, &c->d_rev, need))) return st;
+    c->nbr_alloc = need;
+    c->contrib_alloc = 0;
+  }
+  // per-slot force contributions of the current precision
+  const size_t e4 = c->precision == TERSOFF_MIXED ? 16 : 32;
+  const size_t bytes = e4 * (size_t)c->zs_cap * (size_t)c->n;
+  if (c->contrib_alloc < bytes || c->contrib_prec != c->precision || !c->d_contrib) {
+    cudaFree(c->d_contrib);
+    cudaFree(c->d_own);
+    c->d_contrib = c->d_own = nullptr;
+    TGB_CUDA(c, cudaMalloc(&c->d_contrib, bytes ? bytes : 16));
+    TGB_CUDA(c, cudaMalloc(&c->d_own, e4 * (c->n ? c->n : 1)));
+    TGB_CUDA(c, cudaMemset(c->d_own, 0, e4 * (c->n ? c->n : 1)));
+    c->contrib_alloc = bytes;
+    c->contrib_prec = c->precision;
+  }
   return TERSOFF_OK;
 }
 
@@ -190,7 +212,7 @@ int build_list(Ctx* c, const double* x, cudaStream_t s) {
       return fail(c, TERSOFF_E_NONFINITE, "non-finite position in neighbour build");
     c->max_cnt = c->h_flags[FLAG_OVERFLOW];
     c->max_short = c->h_flags[FLAG_SHORT_MAX];
-    for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[FLAG_BUCKET + b];
+    for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[flag_bucket(b)];
     if (c->max_cnt <= c->cap) {
       c->have_list = true;
       c->steps_since_build = 0;
@@ -242,7 +264,7 @@ int tersoff_create(tersoff_ctx** out, int precision) {
   }
   if (cudaMalloc(&c->d_flags, sizeof(int) * tgb::FLAG_COUNT) != cudaSuccess ||
       cudaMallocHost(&c->h_flags, sizeof(int) * tgb::FLAG_COUNT) != cudaSuccess ||
-      cudaMalloc(&c->d_acc, sizeof(double) * 8) != cudaSuccess ||
+      cudaMalloc(&c->d_acc, sizeof(double) * tgb::ACC_LEN) != cudaSuccess ||
       cudaMalloc(&c->d_coef, sizeof(double) * 2 * TERSOFF_MAX_SPECIES) != cudaSuccess) {
     cudaFree(c->d_flags);
     cudaFreeHost(c->h_flags);
@@ -250,7 +272,7 @@ int tersoff_create(tersoff_ctx** out, int precision) {
     return TERSOFF_E_CUDA;
   }
   cudaMemset(c->d_flags, 0, sizeof(int) * tgb::FLAG_COUNT);
-  cudaMemset(c->d_acc, 0, sizeof(double) * 8);
+  cudaMemset(c->d_acc, 0, sizeof(double) * tgb::ACC_LEN);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     c->cap_stream = nullptr;
   int prio_lo = 0, prio_hi = 0;
@@ -274,7 +296,8 @@ int tersoff_destroy(tersoff_ctx* p) {
                   c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
-                  c->d_bucket, c->d_snap};
+                  c->d_bucket, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
+                  c->d_extra};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -491,18 +514,18 @@ static int compute_impl(Ctx* c, const double* x, int n, double* energy, double* 
   if (n != c->n || (n > 0 && !x))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
   double* f = forces ? forces : c->d_fbuf;
+  if ((st = tgb::ensure_nbr(c))) return st;
   if ((st = tgb::launch_pack_positions(c, x, false, s))) return st;
-  if (n > 0) TGB_CUDA(c, cudaMemsetAsync(f, 0, sizeof(double) * 3 * (size_t)n, s));
-  TGB_CUDA(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * 8, s));
-  {
-    tgb::TimedRegion tr(c, 0, s);
-    if ((st = tgb::launch_forward(c, f, c->d_acc, eatom, s))) return st;
-  }
+  TGB_CUDA(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * tgb::ACC_LEN, s));
+  TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_EXTRA_STICKY, 0, sizeof(int), s));
+  if ((st = tgb::launch_forward(c, c->d_extra, c->d_acc, eatom, s))) return st;
+  if ((st = tgb::launch_gather(c, f, s))) return st;
   if (energy)
     TGB_CUDA(c, cudaMemcpyAsync(energy, c->d_acc, sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (virial)
-    TGB_CUDA(c, cudaMemcpyAsync(virial, c->d_acc + 1, sizeof(double) * 6,
-                                cudaMemcpyDeviceToDevice, s));
+    TGB_CUDA(c, cudaMemcpy2DAsync(virial, sizeof(double), c->d_acc + tgb::ACC_STRIDE,
+                                  sizeof(double) * tgb::ACC_STRIDE, sizeof(double), 6,
+                                  cudaMemcpyDeviceToDevice, s));
   return TERSOFF_OK;
 }
 
@@ -521,20 +544,21 @@ int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eato
 
 // Enqueues nsteps velocity-Verlet steps. sync_builds: rebuild with a host
 // check (eager); otherwise without host synchronisation (graph capture).
-static int enqueue_md(Ctx* c, double* x, double* v, double* f, const double* coef, double dt,
+static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
                       int nsteps, int rebuild_every, double* rows, double* thermo,
                       bool sync_builds, cudaStream_t s) {
   int st = TERSOFF_OK;
-  if (rows) TGB_CUDA(c, cudaMemsetAsync(rows, 0, sizeof(double) * 8 * (size_t)nsteps, s));
+  if (rows) TGB_CUDA(c, cudaMemsetAsync(rows, 0, sizeof(double) * tgb::ACC_LEN * (size_t)nsteps, s));
   for (int step = 0; step < nsteps; ++step) {
     c->steps_since_build++;
     const bool rebuild = rebuild_every > 0 && c->steps_since_build >= rebuild_every;
     // opening half kick (merged with the previous step's closing one), drift
-    double* ke_row = (rows && step > 0) ? rows + 8 * (size_t)(step - 1) + 7 : nullptr;
-    double* acc = rows ? rows + 8 * (size_t)step : c->d_acc;
+    double* ke_row =
+        (rows && step > 0) ? rows + tgb::ACC_LEN * (size_t)(step - 1) + 7 * tgb::ACC_STRIDE : nullptr;
+    double* acc = rows ? rows + tgb::ACC_LEN * (size_t)step : c->d_acc;
     {
       tgb::TimedRegion tr(c, 2, s);
-      if ((st = tgb::launch_md_step(c, x, v, f, coef, dt, step == 0 ? 1 : 2, !rebuild, ke_row,
+      if ((st = tgb::launch_md_step(c, x, v, f, dt, step == 0 ? 1 : 2, !rebuild, ke_row,
                                     rows ? nullptr : c->d_acc, s)))
         return st;
     }
@@ -546,15 +570,13 @@ static int enqueue_md(Ctx* c, double* x, double* v, double* f, const double* coe
       if (st) return st;
       c->steps_since_build = 0;
     }
-    {
-      tgb::TimedRegion tr(c, 0, s);
-      if ((st = tgb::launch_forward(c, f, acc, nullptr, s))) return st;
-    }
+    if ((st = tgb::launch_forward(c, c->d_extra, acc, nullptr, s))) return st;
   }
   {
     tgb::TimedRegion tr(c, 2, s);
-    double* ke_row = rows ? rows + 8 * (size_t)(nsteps - 1) + 7 : nullptr;
-    if ((st = tgb::launch_final_kick(c, v, f, coef, ke_row, s))) return st;
+    double* ke_row =
+        rows ? rows + tgb::ACC_LEN * (size_t)(nsteps - 1) + 7 * tgb::ACC_STRIDE : nullptr;
+    if ((st = tgb::launch_final_kick(c, v, f, ke_row, s))) return st;
   }
   if (thermo && (st = tgb::launch_thermo_rows(c, rows, nsteps, tgb::MVV2E, thermo, s))) return st;
   return TERSOFF_OK;
@@ -578,9 +600,17 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     hc[TERSOFF_MAX_SPECIES + t] = mass[t];
   }
   TGB_CUDA(c, cudaMemcpyAsync(c->d_coef, hc, sizeof(hc), cudaMemcpyHostToDevice, s));
+  for (int t = 0; t < TERSOFF_MAX_SPECIES; ++t) {
+    c->coef.c[t] = hc[t];
+    c->coef.c2[t] = 2.0 * hc[t];
+    c->coef.cf[t] = (float)hc[t];
+    c->coef.c2f[t] = (float)(2.0 * hc[t]);
+    c->coef.m[t] = hc[TERSOFF_MAX_SPECIES + t];
+  }
+  if ((st = tgb::ensure_nbr(c))) return st;
   double* rows = nullptr;
   if (thermo) {
-    const size_t need = 8 * (size_t)nsteps;
+    const size_t need = tgb::ACC_LEN * (size_t)nsteps;
     if (c->trow_alloc < need) {
       if ((st = tgb::dev_alloc(c, &c->d_trow, need))) return st;
       c->trow_alloc = need;
@@ -591,7 +621,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_BUILD_WORDS, 0,
                               sizeof(int) * (tgb::FLAG_COUNT - tgb::FLAG_BUILD_WORDS), s));
   if (!c->use_graphs || !c->cap_stream) {
-    st = enqueue_md(c, x, v, f, c->d_coef, dt, nsteps, rebuild_every, rows, thermo, true, s);
+    st = enqueue_md(c, x, v, f, dt, nsteps, rebuild_every, rows, thermo, true, s);
     if (st) return st;
     TGB_CUDA(c, cudaStreamSynchronize(s));
     return TERSOFF_OK;
@@ -610,7 +640,8 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   const bool same = G.exec && G.gen == c->gen && G.x == x && G.v == v && G.f == f &&
                     G.thermo == thermo && G.dt == dt && G.nsteps == nsteps &&
                     G.rebuild_every == rebuild_every && G.ssb0 == ssb0 &&
-                    G.precision == c->precision && G.timing == c->timing;
+                    G.precision == c->precision && G.timing == c->timing &&
+                    std::memcmp(&G.coef, &c->coef, sizeof(tgb::Coef)) == 0;
   if (!same) {
     tgb::drop_graph(c);
     cudaGraph_t graph = nullptr;
@@ -621,14 +652,15 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     const long long l0 = c->launches;
     c->capturing = true;
     c->timer_sink = &G.timers;
-    st = enqueue_md(c, x, v, f, c->d_coef, dt, nsteps, rebuild_every, rows, thermo, false, cs);
+    st = enqueue_md(c, x, v, f, dt, nsteps, rebuild_every, rows, thermo, false, cs);
     c->capturing = false;
     c->timer_sink = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     cudaGetLastError();  // a failed capture leaves its error in the last-error slot
     if (st == TERSOFF_OK && ce != cudaSuccess) st = tgb::cuda_fail(c, ce, "cudaStreamEndCapture");
     if (st == TERSOFF_OK) {
-      ce = cudaGraphInstantiate(&G.exec, graph, 0);
+      // node priorities (the side stream's small-bucket launches are high priority)
+      ce = cudaGraphInstantiate(&G.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
       if (ce != cudaSuccess) st = tgb::cuda_fail(c, ce, "cudaGraphInstantiate");
     }
     if (graph) cudaGraphDestroy(graph);
@@ -642,6 +674,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     G.f = f;
     G.thermo = thermo;
     G.dt = dt;
+    G.coef = c->coef;
     G.nsteps = nsteps;
     G.rebuild_every = rebuild_every;
     G.ssb0 = ssb0;
@@ -665,7 +698,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   if (!bad) {
     c->max_cnt = c->h_flags[tgb::FLAG_OVERFLOW];
     c->max_short = c->h_flags[tgb::FLAG_SHORT_MAX];
-    for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[tgb::FLAG_BUCKET + b];
+    for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[tgb::flag_bucket(b)];
     return TERSOFF_OK;
   }
   // a build inside the sequence overflowed (or met non-finite positions):
@@ -681,7 +714,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   c->cap = c->cap + c->cap / 2 + 4;
   c->gen++;
   if ((st = tgb::build_list(c, x, s))) return st;
-  st = enqueue_md(c, x, v, f, c->d_coef, dt, nsteps, rebuild_every, rows, thermo, true, s);
+  st = enqueue_md(c, x, v, f, dt, nsteps, rebuild_every, rows, thermo, true, s);
   if (st) return st;
   TGB_CUDA(c, cudaStreamSynchronize(s));
   return TERSOFF_OK;
@@ -731,6 +764,16 @@ int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
 int tersoff_launch_count(const tersoff_ctx* p, long long* count) {
   if (!p || !count) return TERSOFF_E_INVALID_ARG;
   *count = p->impl.launches;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_scatter(tersoff_ctx* p, int mode) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (mode != TERSOFF_SCATTER_GATHER && mode != TERSOFF_SCATTER_ATOMIC)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "unknown scatter mode");
+  c->scatter_atomic = mode == TERSOFF_SCATTER_ATOMIC;
+  c->gen++;
   return TERSOFF_OK;
 }
 

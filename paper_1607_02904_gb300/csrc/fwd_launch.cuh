@@ -29,32 +29,48 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
   c->launches++;
 }
 
-// One launch per short-list size bucket (built with the list): register
-// capacity 4 for atoms with at most 4 short-list entries, 8 for at most 8;
-// longer lists take the general path inside the capacity-4 instance.
-// One launch per short-list size bucket (built with the list): register
-// capacity 4 for atoms with at most 4 short-list entries, 8 for at most 8;
-// longer lists take the general path inside the capacity-4 instance. The small
-// buckets (few atoms, latency-bound) run on a side stream next to bucket 0.
+// Launches per short-list size bucket (built with the list). Bucket 0 (at
+// most 4 stored entries) runs with register capacity 4. Bucket 1 (5 to 8) runs
+// with capacity 8 when it is a sizeable share of the atoms (many atoms with
+// more than 4 neighbours inside the cutoffs, e.g. SiC); when it is small (the
+// extra entries are only inside the list margin) it is appended to the
+// capacity-4 launch, whose atoms keep the entries inside the cutoffs at each
+// step. Bucket 2 and atoms with too many entries take the general path, on a
+// side stream next to the main launch.
 template <class T, int NS>
 void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
   const int full = (c->n + BLOCK - 1) / BLOCK;
-  const int small = full < 2 * 152 ? full : 2 * 152;
-  const bool fork = c->side != nullptr;
+  const bool split1 = (long long)c->nbucket[1] * 20 > (long long)c->nbucket[0];
+  const bool fork = split1 && c->side != nullptr;
+  cudaStream_t s2 = s;
   if (fork) {
     cudaEventRecord(c->ev_fork, s);
     cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+    s2 = c->side;
   }
-  cudaStream_t s2 = fork ? c->side : s;
-  for (int b = 2; b >= 0; --b) {
-    a.order = c->d_bucket + (size_t)b * c->n;
-    a.n_items = c->d_flags + FLAG_BUCKET + b;
-    if (b == 0)
-      launch_t<T, NS, 4>(c, a, full, s);
-    else if (b == 1)
-      launch_t<T, NS, 8>(c, a, small, s2);
-    else
-      launch_t<T, NS, 4>(c, a, small, s2);
+  if (split1) {
+    FwdArgs<T> b1 = a;
+    b1.order = c->d_bucket + 1 * (size_t)c->n;
+    b1.n_items = c->d_flags + flag_bucket(1);
+    b1.order2 = b1.order3 = nullptr;
+    b1.n_items2 = b1.n_items3 = nullptr;
+    b1.identity = 0;
+    launch_t<T, NS, 8>(c, b1, full, s2);
+  }
+  // bucket 0, then bucket 1 (unless split off), then bucket 2 (general path)
+  FwdArgs<T> b0 = a;
+  b0.order = c->d_bucket;
+  b0.n_items = c->d_flags + flag_bucket(0);
+  b0.order2 = split1 ? nullptr : c->d_bucket + 1 * (size_t)c->n;
+  b0.n_items2 = split1 ? nullptr : c->d_flags + flag_bucket(1);
+  b0.order3 = c->d_bucket + 2 * (size_t)c->n;
+  b0.n_items3 = c->d_flags + flag_bucket(2);
+  // all buckets in one launch: atoms in index order (spatial order, and no
+  // indirection); atoms with longer lists take the masked or general path
+  b0.identity = split1 ? 0 : 1;
+  {
+    TimedRegion tr(c, 0, s);
+    launch_t<T, NS, 4>(c, b0, full, s);
   }
   if (fork) {
     cudaEventRecord(c->ev_join, c->side);
@@ -88,6 +104,9 @@ int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
   a.zs_cap = c->zs_cap;
   a.dlim2 = (float)(0.25 * c->margin * c->margin);
   a.f = f;
+  a.contrib = c->d_contrib;
+  a.atomic_mode = c->scatter_atomic ? 1 : 0;
+  a.own = c->d_own;
   a.acc = acc;
   a.eatom = eatom;
   a.flags = c->d_flags;

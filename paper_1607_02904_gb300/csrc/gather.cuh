@@ -1,0 +1,169 @@
+// Force gathering from per-slot contributions (no atomics on the fast path).
+//
+// The force kernel stores, for every atom i, the force its own terms put on
+// each short-list neighbour (slot q of i) and on i itself. The force on atom j
+// is own_j plus, for every short-list neighbour i of j, the contribution in
+// the slot of i's list that holds j (the reverse slot, found at the build;
+// short-list membership is symmetric). Mixed path: the float contributions are
+// summed with error-free transformations (each float addition's rounding
+// error is recovered exactly and accumulated), and the sum and its error term
+// are converted to double and added once: the result carries the exact sum to
+// within a double rounding. FP64 path: summed in double.
+#pragma once
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace tgb {
+
+struct GatherArgs {
+  int n;
+  int cap;
+  int fp64;
+  int atomic_mode;  // forces were scattered with FP64 atomics into extra
+  const uint32_t* shortl;
+  const int* zcnt;
+  const uint8_t* rev;
+  const void* contrib;
+  const void* own;
+  double* extra;
+  const int* flags;
+};
+
+// float -> double through the IEEE-754 bit layouts (exact; float subnormals
+// flush to signed zero). Integer operations only.
+__device__ __forceinline__ double gather_f2d(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  const uint32_t mag = u & 0x7fffffffu;
+  uint32_t hi = (mag >> 3) + 0x38000000u;
+  uint32_t lo = mag << 29;
+  const bool tiny = mag < 0x00800000u;
+  hi = tiny ? 0u : hi;
+  lo = tiny ? 0u : lo;
+  hi = (mag >= 0x7f800000u) ? ((mag >> 3) | 0x7ff00000u) : hi;
+  return __hiloint2double((int)(hi | sign), (int)lo);
+}
+
+// s += x with the rounding error of the addition added to c (Knuth's TwoSum:
+// the error is exact for round-to-nearest float arithmetic).
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float x) {
+  const float t = __fadd_rn(s, x);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+  s = t;
+  c = __fadd_rn(c, err);
+}
+
+// Total force on atom j in eV/A (clears j's fallback-buffer entry when it is
+// used). Mixed path: also the float pair (s, c) with s + c = the exact sum of
+// the contributions (fixed order) plus the fallback term; FP64 path: s, c = 0.
+__device__ __forceinline__ void gather_force(const GatherArgs& g, int j, double& fx,
+                                             double& fy, double& fz, float* sc = nullptr) {
+  if (g.atomic_mode) {
+    double* e = g.extra + 3 * (size_t)j;
+    fx = e[0];
+    fy = e[1];
+    fz = e[2];
+    e[0] = e[1] = e[2] = 0.0;
+    if (sc) sc[0] = sc[1] = sc[2] = sc[3] = sc[4] = sc[5] = 0.0f;
+    return;
+  }
+  int z = g.zcnt[j];
+  z = z < g.cap ? z : g.cap;
+  double ex = 0.0, ey = 0.0, ez = 0.0;
+  const bool extra = g.flags[FLAG_EXTRA] | g.flags[FLAG_EXTRA_STICKY];
+  if (extra) {
+    double* e = g.extra + 3 * (size_t)j;
+    ex = e[0];
+    ey = e[1];
+    ez = e[2];
+    e[0] = e[1] = e[2] = 0.0;
+  }
+  // neighbour indices and reverse slots of the first GU entries, loaded
+  // together (independent loads), then the contributions
+  // (the lists have at least GU slots per atom, so these loads do not wait
+  // for the count)
+  constexpr int GU = 8;
+  int nb[GU], rq[GU];
+#pragma unroll
+  for (int p = 0; p < GU; ++p) {
+    const uint32_t e = g.shortl[(size_t)p * g.n + j];
+    const int r = g.rev[(size_t)p * g.n + j];
+    nb[p] = p < z ? (int)(e & ENTRY_JMASK) : 0;
+    rq[p] = p < z ? r : 255;
+  }
+  if (!g.fp64) {
+    const float4* c = (const float4*)g.contrib;
+    const float4 o = ((const float4*)g.own)[j];
+    float4 v[GU];
+#pragma unroll
+    for (int p = 0; p < GU; ++p)
+      v[p] = (p < z && rq[p] != 255) ? c[(size_t)rq[p] * g.n + nb[p]] : make_float4(0, 0, 0, 0);
+    float sx = o.x, sy = o.y, sz = o.z, cx = 0.0f, cy = 0.0f, cz = 0.0f;
+#pragma unroll
+    for (int p = 0; p < GU; ++p) {
+      two_sum_acc(sx, cx, v[p].x);
+      two_sum_acc(sy, cy, v[p].y);
+      two_sum_acc(sz, cz, v[p].z);
+    }
+    for (int p = GU; p < z; ++p) {
+      const int i = (int)(g.shortl[(size_t)p * g.n + j] & ENTRY_JMASK);
+      const int q = g.rev[(size_t)p * g.n + j];
+      if (q == 255) continue;  // no reverse slot: that force went through atomics
+      const float4 w = c[(size_t)q * g.n + i];
+      two_sum_acc(sx, cx, w.x);
+      two_sum_acc(sy, cy, w.y);
+      two_sum_acc(sz, cz, w.z);
+    }
+    if (sc) {  // the caller works with the pair and the fallback term separately
+      sc[0] = sx;
+      sc[1] = sy;
+      sc[2] = sz;
+      sc[3] = cx;
+      sc[4] = cy;
+      sc[5] = cz;
+      fx = ex;
+      fy = ey;
+      fz = ez;
+    } else {
+      fx = gather_f2d(sx) + (gather_f2d(cx) + ex);
+      fy = gather_f2d(sy) + (gather_f2d(cy) + ey);
+      fz = gather_f2d(sz) + (gather_f2d(cz) + ez);
+    }
+  } else {
+    const dpos4* c = (const dpos4*)g.contrib;
+    const dpos4 o = ((const dpos4*)g.own)[j];
+    fx = o.x + ex;
+    fy = o.y + ey;
+    fz = o.z + ez;
+    for (int p = 0; p < z; ++p) {
+      const int i = p < GU ? nb[p] : (int)(g.shortl[(size_t)p * g.n + j] & ENTRY_JMASK);
+      const int q = p < GU ? rq[p] : g.rev[(size_t)p * g.n + j];
+      if (q == 255) continue;
+      const dpos4 w = c[(size_t)q * g.n + i];
+      fx += w.x;
+      fy += w.y;
+      fz += w.z;
+    }
+    if (sc) sc[0] = sc[1] = sc[2] = sc[3] = sc[4] = sc[5] = 0.0f;
+  }
+}
+
+inline GatherArgs make_gather(Ctx* c) {
+  GatherArgs g;
+  g.n = c->n;
+  g.cap = c->zs_cap;
+  g.fp64 = c->precision == TERSOFF_FP64;
+  g.atomic_mode = c->scatter_atomic ? 1 : 0;
+  g.shortl = c->d_short;
+  g.zcnt = c->d_zcnt;
+  g.rev = c->d_rev;
+  g.contrib = c->d_contrib;
+  g.own = c->d_own;
+  g.extra = c->d_extra;
+  g.flags = c->d_flags;
+  return g;
+}
+
+}  // namespace tgb

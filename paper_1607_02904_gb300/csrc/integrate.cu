@@ -1,5 +1,6 @@
 // Per-step atom kernels: position packing for the force kernels and the
 // velocity-Verlet kick/drift on the FP64 state (x, v, f).
+#include "gather.cuh"
 #include "internal.cuh"
 
 namespace tgb {
@@ -26,30 +27,36 @@ struct PackArgs {
   int* flags;
 };
 
-// Packs atom i at position (x0, x1, x2); returns its squared displacement
-// since the build (A^2) when tracking.
-__device__ __forceinline__ float pack_one(const PackArgs& a, int i, double x0, double x1,
+// Packs atom i (species t) at position (x0, x1, x2); qo: its fixed-point
+// origin words; returns its squared displacement since the build (A^2) when
+// tracking. Loads are issued before any store.
+__device__ __forceinline__ float pack_one(const PackArgs& a, int i, int t, double x0, double x1,
                                           double x2) {
   const double* qo = a.qorg + 3 * (size_t)i;
-  const int t = a.types[i];
+  const double qo0 = qo[0], qo1 = qo[1], qo2 = qo[2];
+  int4 r = make_int4(0, 0, 0, 0);
+  if (a.track) r = a.qref[i];
+  double o0 = 0.0, o1 = 0.0, o2 = 0.0;
+  if (a.fp64) {
+    const double* o = a.origin + 3 * (size_t)i;
+    o0 = o[0];
+    o1 = o[1];
+    o2 = o[2];
+  }
   // q = round((x - o) 2^S) with one rounding: fma(x, 2^S, magic - o 2^S)
   const long long mb = __double_as_longlong(ROUND_MAGIC);
-  const int q0 = (int)(__double_as_longlong(fma(x0, a.scale, qo[0])) - mb);
-  const int q1 = (int)(__double_as_longlong(fma(x1, a.scale, qo[1])) - mb);
-  const int q2 = (int)(__double_as_longlong(fma(x2, a.scale, qo[2])) - mb);
+  const int q0 = (int)(__double_as_longlong(fma(x0, a.scale, qo0)) - mb);
+  const int q1 = (int)(__double_as_longlong(fma(x1, a.scale, qo1)) - mb);
+  const int q2 = (int)(__double_as_longlong(fma(x2, a.scale, qo2)) - mb);
   a.posq[i] = make_int4(q0, q1, q2, t);
   if (a.build) {
     a.pos32[i] = make_float4((float)q0 * a.inv_scale, (float)q1 * a.inv_scale,
                              (float)q2 * a.inv_scale, __int_as_float(t));
     a.qref[i] = make_int4(q0, q1, q2, t);
   }
-  if (a.fp64) {
-    const double* o = a.origin + 3 * (size_t)i;
-    a.pos64[i] = dpos4{x0 - o[0], x1 - o[1], x2 - o[2], (double)t};
-  }
+  if (a.fp64) a.pos64[i] = dpos4{x0 - o0, x1 - o1, x2 - o2, (double)t};
   float d2 = 0.0f;
   if (a.track) {
-    const int4 r = a.qref[i];
     const float d0 = (float)(q0 - r.x) * a.inv_scale;
     const float d1 = (float)(q1 - r.y) * a.inv_scale;
     const float dd = (float)(q2 - r.z) * a.inv_scale;
@@ -58,11 +65,18 @@ __device__ __forceinline__ float pack_one(const PackArgs& a, int i, double x0, d
   return d2;
 }
 
-// warp max, one atomic per warp (non-negative floats order like their bits)
+// block max, one atomic per block (non-negative floats order like their bits)
 __device__ __forceinline__ void track_max(const PackArgs& a, float d2) {
   if (!a.track) return;
+  __shared__ float wmax[32];
   for (int o = 16; o > 0; o >>= 1) d2 = fmaxf(d2, __shfl_xor_sync(0xffffffffu, d2, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(&a.flags[FLAG_DMAX], __float_as_int(d2));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = d2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wmax[w]);
+    atomicMax(&a.flags[FLAG_DMAX], __float_as_int(m));
+  }
 }
 
 __global__ void k_pack(PackArgs a, const double* __restrict__ x) {
@@ -70,7 +84,7 @@ __global__ void k_pack(PackArgs a, const double* __restrict__ x) {
   float d2 = 0.0f;
   if (i < a.n) {
     const double* xi = x + 3 * (size_t)i;
-    d2 = pack_one(a, i, xi[0], xi[1], xi[2]);
+    d2 = pack_one(a, i, a.types[i], xi[0], xi[1], xi[2]);
   }
   track_max(a, d2);
 }
@@ -88,65 +102,122 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst) {
   }
 }
 
-// v += kick coef f ; x += dt v ; f = 0 ; pack ; optional kinetic energy of the
-// previous step ; clear the accumulator for the coming force evaluation
-__global__ void k_step(PackArgs pk, double* __restrict__ x, double* __restrict__ v,
-                       double* __restrict__ f, const double* __restrict__ coef, double dt,
-                       double kick, int do_pack, double* ke_row, double* acc_zero) {
+// v += kick coef F ; x += dt v ; pack ; optional kinetic energy of the
+// previous step ; clear the accumulator for the coming force evaluation.
+// F: from f on the first step of a call, gathered from the last force
+// evaluation afterwards. All loads of an atom are issued before its stores.
+__global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restrict__ x,
+                       double* __restrict__ v, const double* __restrict__ f, Coef cf,
+                       double dt, int kick, int do_pack, double* ke_row, double* acc_zero) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (acc_zero && i < 8) acc_zero[i] = 0.0;
+  if (acc_zero && i < 8) acc_zero[i * ACC_STRIDE] = 0.0;
   float d2 = 0.0f;
   double ke = 0.0;
   if (i < pk.n) {
     const int t = pk.types[i];
-    const double c = coef[t];
-    double xn[3];
-    for (int a = 0; a < 3; ++a) {
-      const size_t k = 3 * (size_t)i + a;
-      const double fk = f[k];
-      const double vk = v[k];
-      if (ke_row) {
-        const double vf = fma(c, fk, vk);  // full-step velocity of the previous step
-        ke = fma(vf, vf, ke);
-      }
-      const double vv = fma(kick * c, fk, vk);
-      v[k] = vv;
-      xn[a] = fma(dt, vv, x[k]);
-      x[k] = xn[a];
-      f[k] = 0.0;
+    const size_t b = 3 * (size_t)i;
+    const double x0 = x[b], x1 = x[b + 1], x2 = x[b + 2];
+    const double v0 = v[b], v1 = v[b + 1], v2 = v[b + 2];
+    double F0, F1, F2;
+    float sc[6] = {0, 0, 0, 0, 0, 0};
+    const bool mixed = gather && !ga.fp64 && !ga.atomic_mode;
+    if (gather) {
+      gather_force(ga, i, F0, F1, F2, mixed ? sc : nullptr);
+    } else {
+      F0 = f[b];
+      F1 = f[b + 1];
+      F2 = f[b + 2];
     }
-    if (ke_row) ke *= 0.5 * coef[TERSOFF_MAX_SPECIES + t];
-    if (do_pack) d2 = pack_one(pk, i, xn[0], xn[1], xn[2]);
+    const double cu = cf.c[t];
+    const double kcu = kick == 2 ? cf.c2[t] : cu;
+    double vn0, vn1, vn2;
+    if (mixed) {
+      // the velocity increment from the float force pair in float (the forces
+      // are float-accurate), accumulated into the double velocity; F0..2 hold
+      // the (rare) fallback-buffer forces
+      const float kf = kick == 2 ? cf.c2f[t] : cf.cf[t];
+      const float d0 = kf * sc[0] + kf * sc[3];
+      const float d1 = kf * sc[1] + kf * sc[4];
+      const float d2v = kf * sc[2] + kf * sc[5];
+      if (ke_row) {
+        const float hf = cf.cf[t];
+        const double w0 = v0 + gather_f2d(hf * sc[0] + hf * sc[3]);
+        const double w1 = v1 + gather_f2d(hf * sc[1] + hf * sc[4]);
+        const double w2 = v2 + gather_f2d(hf * sc[2] + hf * sc[5]);
+        ke = 0.5 * cf.m[t] * fma(w0, w0, fma(w1, w1, w2 * w2));
+      }
+      vn0 = v0 + gather_f2d(d0);
+      vn1 = v1 + gather_f2d(d1);
+      vn2 = v2 + gather_f2d(d2v);
+      if (ga.flags[FLAG_EXTRA] | ga.flags[FLAG_EXTRA_STICKY]) {
+        vn0 = fma(kcu, F0, vn0);
+        vn1 = fma(kcu, F1, vn1);
+        vn2 = fma(kcu, F2, vn2);
+      }
+    } else {
+      if (ke_row) {
+        // full-step velocity of the previous step
+        const double w0 = fma(cu, F0, v0), w1 = fma(cu, F1, v1), w2 = fma(cu, F2, v2);
+        ke = 0.5 * cf.m[t] * fma(w0, w0, fma(w1, w1, w2 * w2));
+      }
+      vn0 = fma(kcu, F0, v0);
+      vn1 = fma(kcu, F1, v1);
+      vn2 = fma(kcu, F2, v2);
+    }
+    const double xn0 = fma(dt, vn0, x0), xn1 = fma(dt, vn1, x1), xn2 = fma(dt, vn2, x2);
+    v[b] = vn0;
+    v[b + 1] = vn1;
+    v[b + 2] = vn2;
+    x[b] = xn0;
+    x[b + 1] = xn1;
+    x[b + 2] = xn2;
+    if (do_pack) d2 = pack_one(pk, i, t, xn0, xn1, xn2);
   }
   if (do_pack) track_max(pk, d2);
   if (ke_row) block_sum_add(ke, ke_row);
 }
 
-__global__ void k_final_kick(int n, const int* __restrict__ types, double* __restrict__ v,
-                             const double* __restrict__ f, const double* __restrict__ coef,
+// closing half kick with gathered forces, which are also written to f
+__global__ void k_final_kick(GatherArgs ga, const int* __restrict__ types,
+                             double* __restrict__ v, double* __restrict__ f, Coef cf,
                              double* ke_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double ke = 0.0;
-  if (i < n) {
+  if (i < ga.n) {
     const int t = types[i];
-    const double c = coef[t];
-    for (int a = 0; a < 3; ++a) {
-      const size_t k = 3 * (size_t)i + a;
-      const double vv = fma(c, f[k], v[k]);
-      v[k] = vv;
-      ke = fma(vv, vv, ke);
-    }
-    ke *= 0.5 * coef[TERSOFF_MAX_SPECIES + t];
+    const size_t b = 3 * (size_t)i;
+    const double v0 = v[b], v1 = v[b + 1], v2 = v[b + 2];
+    double F0, F1, F2;
+    gather_force(ga, i, F0, F1, F2);
+    const double cu = cf.c[t];
+    const double w0 = fma(cu, F0, v0), w1 = fma(cu, F1, v1), w2 = fma(cu, F2, v2);
+    f[b] = F0;
+    f[b + 1] = F1;
+    f[b + 2] = F2;
+    v[b] = w0;
+    v[b + 1] = w1;
+    v[b + 2] = w2;
+    ke = 0.5 * cf.m[t] * fma(w0, w0, fma(w1, w1, w2 * w2));
   }
   if (ke_row) block_sum_add(ke, ke_row);
 }
 
-// rows: 8 doubles per step (energy, virial[6], kinetic in mass units)
+__global__ void k_gather(GatherArgs ga, double* __restrict__ f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ga.n) return;
+  double F[3];
+  gather_force(ga, i, F[0], F[1], F[2]);
+  f[3 * (size_t)i] = F[0];
+  f[3 * (size_t)i + 1] = F[1];
+  f[3 * (size_t)i + 2] = F[2];
+}
+
+// rows: ACC_LEN doubles per step (energy, virial[6], kinetic in mass units)
 __global__ void k_thermo_rows(const double* rows, int nsteps, double mvv2e, double* out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nsteps) return;
-  const double pe = rows[8 * (size_t)s];
-  const double ke = rows[8 * (size_t)s + 7] * mvv2e;
+  const double pe = rows[ACC_LEN * (size_t)s];
+  const double ke = rows[ACC_LEN * (size_t)s + 7 * ACC_STRIDE] * mvv2e;
   out[3 * (size_t)s + 0] = pe;
   out[3 * (size_t)s + 1] = ke;
   out[3 * (size_t)s + 2] = pe + ke;
@@ -181,18 +252,27 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s) {
   return TERSOFF_OK;
 }
 
-int launch_md_step(Ctx* c, double* x, double* v, double* f, const double* coef, double dt,
-                   int kick, bool pack, double* ke_row, double* acc_zero, cudaStream_t s) {
-  k_step<<<(c->n + 255) / 256, 256, 0, s>>>(make_pack(c, true), x, v, f, coef, dt,
-                                            (double)kick, pack ? 1 : 0, ke_row, acc_zero);
+int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick, bool pack,
+                   double* ke_row, double* acc_zero, cudaStream_t s) {
+  k_step<<<(c->n + 255) / 256, 256, 0, s>>>(make_pack(c, true), make_gather(c), kick == 2 ? 1 : 0,
+                                            x, v, f, c->coef, dt, kick, pack ? 1 : 0, ke_row,
+                                            acc_zero);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;
 }
 
-int launch_final_kick(Ctx* c, double* v, const double* f, const double* coef, double* ke_row,
-                      cudaStream_t s) {
-  k_final_kick<<<(c->n + 255) / 256, 256, 0, s>>>(c->n, c->d_types, v, f, coef, ke_row);
+int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t s) {
+  k_final_kick<<<(c->n + 255) / 256, 256, 0, s>>>(make_gather(c), c->d_types, v, f, c->coef,
+                                                  ke_row);
+  c->launches++;
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+int launch_gather(Ctx* c, double* f, cudaStream_t s) {
+  if (c->n == 0) return TERSOFF_OK;
+  k_gather<<<(c->n + 255) / 256, 256, 0, s>>>(make_gather(c), f);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

@@ -67,6 +67,15 @@ struct Grid {
   int fix_shift;  // fixed-point scale 2^fix_shift for mixed positions
 };
 
+// MD coefficients per species: c = dt/2 * (force-to-acceleration) / m, and m
+struct Coef {
+  double c[TERSOFF_MAX_SPECIES];   // dt/2 * (force-to-acceleration) / m
+  double c2[TERSOFF_MAX_SPECIES];  // 2 c (merged closing and opening half kicks)
+  double m[TERSOFF_MAX_SPECIES];
+  float cf[TERSOFF_MAX_SPECIES];   // c and 2c rounded to float (mixed-path increments)
+  float c2f[TERSOFF_MAX_SPECIES];
+};
+
 // ------------------------------------------------------------------ context
 struct Ctx {
   int precision = TERSOFF_FP64;
@@ -117,18 +126,26 @@ struct Ctx {
   uint32_t* d_short = nullptr;    // zs_cap * n, slot-major short list
   int* d_zcnt = nullptr;          // n
   int* d_bucket = nullptr;        // 3 x n: atom indices per short-list size bucket
+  uint8_t* d_rev = nullptr;       // zs_cap x n: slot of j in the short list of its p-th neighbour
+  void* d_contrib = nullptr;      // zs_cap x n force contributions (float4 or dpos4)
+  void* d_own = nullptr;          // n: force of each atom's own terms on itself
+  double* d_extra = nullptr;      // n x 3: atomically scattered forces (fallback mode)
+  size_t contrib_alloc = 0;       // bytes of d_contrib
+  int contrib_prec = -1;
+  bool scatter_atomic = false;    // forces by FP64 atomics instead of slots + gather
   int nbucket[3] = {0, 0, 0};     // bucket sizes at the last build
   int zs_cap = 0;
   double margin = 0.0;            // short-list radius margin beyond the cutoffs
-  double* d_trow = nullptr;       // MD thermo accumulation rows (8 doubles per step)
+  double* d_trow = nullptr;       // MD thermo accumulation rows (ACC_LEN doubles per step)
   size_t trow_alloc = 0;
   float4* d_pos32 = nullptr;      // n: (u float, type bits)
   int4* d_posq = nullptr;         // n: (u fixed point, type)
   dpos4* d_pos64 = nullptr;     // n: (u double, type)
   int* d_flags = nullptr;         // device status words (see FLAG_*)
   int* h_flags = nullptr;         // pinned mirror
-  double* d_acc = nullptr;        // energy (1) + virial (6) + kinetic (1)
+  double* d_acc = nullptr;        // ACC_LEN: energy, virial (6), kinetic at stride ACC_STRIDE
   double* d_coef = nullptr;       // MD: dt/2 F->a / m per species, then masses
+  Coef coef{};                    // the same, passed to the kernels by value
   int steps_since_build = 0;
   double* d_fbuf = nullptr;       // scratch forces (n x 3) for calls without output
   double* d_stage = nullptr;      // host-call staging: x, v, f (3 x n x 3)
@@ -158,6 +175,7 @@ struct Ctx {
     std::vector<Pending> timers;
     const double *x = nullptr, *v = nullptr, *f = nullptr, *thermo = nullptr;
     double dt = 0.0;
+    Coef coef{};
     int nsteps = 0, rebuild_every = 0, ssb0 = 0, precision = 0;
     bool timing = false;
     long long gen = -1;
@@ -178,19 +196,30 @@ struct TimedRegion {
 };
 int fold_timing(Ctx* c);
 
-// Device status words. Indices below FLAG_BUILD_WORDS are cleared at every
-// neighbour build; the others are sticky until the next compute/MD call.
+// Device status words, each in its own 128-byte line (words that many blocks
+// update or read would otherwise serialise on one L2 slice). Words below
+// FLAG_BUILD_WORDS are cleared at every neighbour build; the others are sticky
+// until the next compute/MD call.
+constexpr int FLAG_STRIDE = 32;
 enum : int {
-  FLAG_OVERFLOW = 0,     // largest neighbour count of the build (atomicMax)
-  FLAG_SHORT_MAX = 1,    // largest short-list count of the build
-  FLAG_DMAX = 2,         // running max squared displacement since the build (float bits)
-  FLAG_BUCKET = 3,       // 3, 4, 5: atoms per short-list size bucket (<= 4, <= 8, more)
-  FLAG_BUILD_WORDS = 8,
-  FLAG_NONFINITE = 8,    // non-finite position seen by a build
-  FLAG_FALLBACK = 9,     // atoms handled by the general path
-  FLAG_OVF_ANY = 10,     // some build exceeded the list capacity
-  FLAG_COUNT = 16
+  FLAG_OVERFLOW = 0 * FLAG_STRIDE,      // largest neighbour count of the build
+  FLAG_SHORT_MAX = 1 * FLAG_STRIDE,     // largest short-list count of the build
+  FLAG_DMAX = 2 * FLAG_STRIDE,          // running max squared displacement since the build (float bits)
+  FLAG_BUCKET = 3 * FLAG_STRIDE,        // 3 words: atoms per short-list size bucket (<= 4, <= 8, more)
+  FLAG_REV_MISS = 6 * FLAG_STRIDE,      // a short-list entry has no reverse entry
+  FLAG_BUILD_WORDS = 8 * FLAG_STRIDE,
+  FLAG_NONFINITE = 8 * FLAG_STRIDE,     // non-finite position seen by a build
+  FLAG_FALLBACK = 9 * FLAG_STRIDE,      // atoms handled by the general path
+  FLAG_OVF_ANY = 10 * FLAG_STRIDE,      // some build exceeded the list capacity
+  FLAG_EXTRA = 11 * FLAG_STRIDE,        // last force evaluation scattered through atomics
+  FLAG_EXTRA_STICKY = 13 * FLAG_STRIDE, // some evaluation since the call began did
+  FLAG_COUNT = 16 * FLAG_STRIDE
 };
+__host__ __device__ constexpr int flag_bucket(int b) { return FLAG_BUCKET + b * FLAG_STRIDE; }
+
+// Energy / virial / kinetic accumulators: 8 components, each in its own line.
+constexpr int ACC_STRIDE = 16;            // doubles
+constexpr int ACC_LEN = 8 * ACC_STRIDE;   // one accumulator row
 
 int fail(Ctx* c, int code, const std::string& msg);
 int cuda_fail(Ctx* c, cudaError_t e, const char* where);
@@ -213,24 +242,31 @@ int launch_neighbor_export(Ctx* c, int* cnt, int* nbr, int cap, cudaStream_t s);
 int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s);
 
 // Forces (fwd_f32.cu / fwd_f64.cu). Accumulates into f (zeroed by the caller),
-// energy and virial into acc[0..6] (zeroed by the caller); eatom optional.
+// energy and virial into acc components 0..6 (zeroed by the caller); eatom optional.
 int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f32(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 
-// Velocity Verlet (integrate.cu). coef[t] = dt/2 * (force-to-acceleration) / m_t,
-// coef[MAX_SPECIES + t] = m_t.
-//   step kernel: v += kick * coef f (kick = 1 on the first step of a call,
-//   2 afterwards: the closing half kick of the previous step and the opening
-//   half kick of this one); x += dt v; f = 0; pack; ke_row (optional) receives
-//   sum m (v_prev + coef f)^2 / 2 of the previous step; acc_zero (optional) is
+// Force gathering (integrate.cu): F_j = own_j + contributions of the terms of
+// j's short-list neighbours (+ the atomic fallback buffer when flagged), in
+// exact 64-bit fixed point (mixed) or double (FP64), written to f.
+int launch_gather(Ctx* c, double* f, cudaStream_t s);
+// Reverse short-list slots (neighbor.cu); after a build.
+int launch_reverse_slots(Ctx* c, cudaStream_t s);
+
+// Velocity Verlet (integrate.cu) with the coefficients c->coef.
+//   step kernel: v += kick * c F (kick = 1 on the first step of a call, with
+//   F read from f; 2 afterwards, with F gathered from the last force
+//   evaluation: the closing half kick of the previous step and the opening
+//   half kick of this one); x += dt v; pack; ke_row (optional) receives
+//   sum m (v_prev + c F)^2 / 2 of the previous step; acc_zero (optional) is
 //   cleared for the coming force evaluation.
-int launch_md_step(Ctx* c, double* x, double* v, double* f, const double* coef, double dt,
-                   int kick, bool pack, double* ke_row, double* acc_zero, cudaStream_t s);
-// closing half kick of the last step; ke_row (optional) as above
-int launch_final_kick(Ctx* c, double* v, const double* f, const double* coef, double* ke_row,
-                      cudaStream_t s);
-// thermo (nsteps x 3: potential, kinetic [eV], total) from the 8-double rows
+int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick, bool pack,
+                   double* ke_row, double* acc_zero, cudaStream_t s);
+// closing half kick of the last step with gathered forces, which are also
+// written to f; ke_row (optional) as above
+int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t s);
+// thermo (nsteps x 3: potential, kinetic [eV], total) from the accumulator rows
 int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, double* thermo,
                        cudaStream_t s);
 

@@ -265,21 +265,70 @@ __global__ void __launch_bounds__(128) k_neigh(
     cnt[i] = count;
     zcnt[i] = z;
   }
-  warp_atomic_max(&flags[FLAG_OVERFLOW], count, active);
-  warp_atomic_max(&flags[FLAG_SHORT_MAX], z, active);
-  if (__any_sync(0xffffffffu, active && count > cap) && (threadIdx.x & 31) == 0)
-    atomicOr(&flags[FLAG_OVF_ANY], 1);
-  // bucket by short-list size (<= 4, <= 8, more); one atomic per warp and bucket
+  // block-level aggregation: one atomic per block and word
+  __shared__ int s_max[2], s_ovf, s_cnt[3], s_base[3], s_wcnt[4][3];
+  if (threadIdx.x == 0) {
+    s_max[0] = s_max[1] = 0;
+    s_ovf = 0;
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+  }
+  __syncthreads();
+  int mc = active ? count : 0, mz = active ? z : 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    mc = max(mc, __shfl_xor_sync(0xffffffffu, mc, o));
+    mz = max(mz, __shfl_xor_sync(0xffffffffu, mz, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool ovf = __any_sync(0xffffffffu, active && count > cap);
+  // bucket by short-list size (<= 4, <= 8, more)
   const int b = z <= 4 ? 0 : (z <= 8 ? 1 : 2);
-  const int lane = threadIdx.x & 31;
-  for (int q = 0; q < 3; ++q) {
-    const unsigned msk = __ballot_sync(0xffffffffu, active && b == q);
-    if (msk == 0u) continue;
-    const int leader = __ffs(msk) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(&flags[FLAG_BUCKET + q], __popc(msk));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (active && b == q) bucket[(size_t)q * n + base + __popc(msk & ((1u << lane) - 1u))] = i;
+  unsigned msk[3];
+  for (int q = 0; q < 3; ++q) msk[q] = __ballot_sync(0xffffffffu, active && b == q);
+  if (lane == 0) {
+    atomicMax(&s_max[0], mc);
+    atomicMax(&s_max[1], mz);
+    if (ovf) s_ovf = 1;
+    for (int q = 0; q < 3; ++q) s_wcnt[wid][q] = __popc(msk[q]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_max[0] > 0) atomicMax(&flags[FLAG_OVERFLOW], s_max[0]);
+    if (s_max[1] > 0) atomicMax(&flags[FLAG_SHORT_MAX], s_max[1]);
+    if (s_ovf) atomicOr(&flags[FLAG_OVF_ANY], 1);
+    for (int q = 0; q < 3; ++q) {
+      int tot = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wcnt[w][q];
+      s_base[q] = tot ? atomicAdd(&flags[flag_bucket(q)], tot) : 0;
+    }
+  }
+  __syncthreads();
+  if (active) {
+    int off = s_base[b];
+    for (int w = 0; w < wid; ++w) off += s_wcnt[w][b];
+    bucket[(size_t)b * n + off + __popc(msk[b] & ((1u << lane) - 1u))] = i;
+  }
+}
+
+// Reverse slots: for each short-list entry (j -> i), the slot of j in i's
+// short list (255 if absent), used to gather forces without atomics.
+__global__ void k_rev(int n, const uint32_t* __restrict__ shortl, const int* __restrict__ zcnt,
+                      int cap, uint8_t* __restrict__ rev, int* __restrict__ flags) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int z = zcnt[j];
+  z = z < cap ? z : cap;
+  for (int p = 0; p < z; ++p) {
+    const int i = (int)(shortl[(size_t)p * n + j] & ENTRY_JMASK);
+    int zi = zcnt[i];
+    zi = zi < cap ? zi : cap;
+    int q = 255;
+    for (int s = 0; s < zi; ++s)
+      if ((int)(shortl[(size_t)s * n + i] & ENTRY_JMASK) == j) {
+        q = s;
+        break;
+      }
+    if (q == 255) atomicOr(&flags[FLAG_REV_MISS], 1);
+    rev[(size_t)p * n + j] = (uint8_t)q;
   }
 }
 
@@ -369,9 +418,11 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const float hi2 = (float)(rc2 + band);
   Radii lim;
   for (int q = 0; q < TERSOFF_MAX_SPECIES * TERSOFF_MAX_SPECIES; ++q) lim.r2[q] = 0.0f;
+  // symmetric in the two species, so that short-list membership is mutual
   for (int a = 0; a < c->ns; ++a)
     for (int b = 0; b < c->ns; ++b) {
-      const double r = c->filt[(size_t)a * c->ns + b] + c->margin;
+      const double rf = fmax(c->filt[(size_t)a * c->ns + b], c->filt[(size_t)b * c->ns + a]);
+      const double r = rf + c->margin;
       lim.r2[a * c->ns + b] = (float)(r * r * (1.0 + 1e-6));
     }
   if (n > 0) {
@@ -379,7 +430,9 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
                                             c->d_cell_atoms, g, rc2, lo2, hi2, c->cap, c->d_nbr,
                                             c->d_cnt, lim, c->ns, c->d_short, c->d_zcnt,
                                             c->d_bucket, c->d_flags);
-    c->launches++;
+    k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
+                                          c->d_flags);
+    c->launches += 2;
   }
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

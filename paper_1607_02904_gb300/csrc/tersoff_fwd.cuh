@@ -78,11 +78,25 @@ template <> struct M<float> {
   static __device__ __forceinline__ void sincospi_(float x, float* s, float* c) {
     sincospif(x, s, c);
   }
-  // b = (1 + (beta zeta)^n)^(-1/(2n)),  db/dzeta
+  // hardware base-2 exponential and logarithm (special function unit)
+  static __device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  static __device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+  }
+  // b = (1 + (beta zeta)^n)^(-1/(2n)),  db/dzeta. The inner power u goes
+  // through the hardware log2/exp2: b depends weakly on u (relative
+  // sensitivity u / (2 n (1 + u)) ~ 0.03 for Si), so their few-ulp errors move
+  // b by ~1e-9. The outer power uses the accurate log2f/exp2f.
   static __device__ __forceinline__ void bond(float zeta, float beta, float n, float ninv2,
                                               float& b, float& db) {
     if (zeta > 0.0f) {
-      float u = exp2f(n * log2f(beta * zeta));
+      float u = ex2(n * lg2(beta * zeta));
       float opu = 1.0f + u;
       b = exp2f(ninv2 * log2f(opu));
       db = -0.5f * b * u * rcp_nr(opu * zeta);
@@ -137,10 +151,18 @@ template <class T> struct FwdArgs {
   const uint32_t* shortl;  // slot-major short list (filter radius + margin)
   const int* zcnt;       // short-list counts
   int zs_cap;            // short-list capacity
-  const int* order;      // atoms of this launch (a short-list size bucket)
-  const int* n_items;    // device count of atoms in order
+  const int* order;      // atoms of this launch (a short-list size bucket) ...
+  const int* n_items;    // ... and their device count
+  const int* order2;     // optional second and third buckets processed after the first
+  const int* n_items2;
+  const int* order3;
+  const int* n_items3;
+  int identity;          // process atoms 0..n-1 directly (no bucket order)
   float dlim2;           // short list valid while max squared displacement <= dlim2
-  double* f;             // forces, accumulated
+  void* contrib;         // slot-major per-neighbour force contributions (T4)
+  void* own;             // per-atom force of its own terms (T4)
+  int atomic_mode;       // scatter every force with FP64 atomics (no slots)
+  double* f;             // fallback forces, accumulated atomically
   double* acc;           // energy, virial (6)
   double* eatom;         // optional per-atom energy
   int* flags;
@@ -287,6 +309,35 @@ __device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, 
   dz = T(0.5) * fc * fa * db;
 }
 
+template <class T> struct C4;
+template <> struct C4<float> {
+  using type = float4;
+  static __device__ __forceinline__ float4 make(float x, float y, float z) {
+    return make_float4(x, y, z, 0.0f);
+  }
+};
+template <> struct C4<double> {
+  using type = dpos4;
+  static __device__ __forceinline__ dpos4 make(double x, double y, double z) {
+    return dpos4{x, y, z, 0.0};
+  }
+};
+
+template <class T>
+__device__ __forceinline__ void store_slot(const FwdArgs<T>& a, void* base, size_t idx, T x, T y,
+                                           T z) {
+  ((typename C4<T>::type*)base)[idx] = C4<T>::make(x, y, z);
+}
+template <class T>
+__device__ __forceinline__ void add_slot(const FwdArgs<T>& a, size_t idx, T x, T y, T z) {
+  typename C4<T>::type* p = (typename C4<T>::type*)a.contrib + idx;
+  typename C4<T>::type v = *p;
+  v.x += x;
+  v.y += y;
+  v.z += z;
+  *p = v;
+}
+
 __device__ __forceinline__ void atomic_add3(double* f, int j, double a, double b, double c) {
   atomicAdd(f + 3 * (size_t)j + 0, a);
   atomicAdd(f + 3 * (size_t)j + 1, b);
@@ -301,13 +352,18 @@ __device__ __forceinline__ int rec_off(int ns, int ti, int tj, int tk) {
   return NS == 1 ? 0 : ((ti * ns + tj) * ns + tk) * RSTRIDE;
 }
 
+// slots: forces go to the per-slot contributions of the list (the short list),
+// otherwise to the fallback buffer through FP64 atomics.
 template <class T, int NS, bool LAM3>
 __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec, int i, int ti,
-                                          const uint32_t* list, int c, T& ei, T* w) {
+                                          const uint32_t* list, int c, bool slots, T& ei,
+                                          T* w) {
   using P = typename SelfPos<T>::type;
   const int ns = NS > 0 ? NS : a.ns;
   const P pi = self_pos<T>(a, i);
   T fix = 0, fiy = 0, fiz = 0;
+  if (slots)
+    for (int q = 0; q < c; ++q) store_slot<T>(a, a.contrib, (size_t)q * a.n + i, T(0), T(0), T(0));
   for (int sj = 0; sj < c; ++sj) {
     T dxj, dyj, dzj;
     int j, tj;
@@ -362,7 +418,10 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
       Fjy -= dz * gjy;
       Fjz -= dz * gjz;
       const T Fkx = -dz * gkx, Fky = -dz * gky, Fkz = -dz * gkz;
-      atomic_add3(a.f, k, to_f64(Fkx), to_f64(Fky), to_f64(Fkz));
+      if (slots)
+        add_slot<T>(a, (size_t)sk * a.n + i, Fkx, Fky, Fkz);
+      else
+        atomic_add3(a.f, k, to_f64(Fkx), to_f64(Fky), to_f64(Fkz));
       fix -= Fkx;
       fiy -= Fky;
       fiz -= Fkz;
@@ -373,7 +432,10 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
       w[4] += dxk * Fkz;
       w[5] += dyk * Fkz;
     }
-    atomic_add3(a.f, j, to_f64(Fjx), to_f64(Fjy), to_f64(Fjz));
+    if (slots)
+      add_slot<T>(a, (size_t)sj * a.n + i, Fjx, Fjy, Fjz);
+    else
+      atomic_add3(a.f, j, to_f64(Fjx), to_f64(Fjy), to_f64(Fjz));
     fix -= Fjx;
     fiy -= Fjy;
     fiz -= Fjz;
@@ -384,7 +446,19 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
     w[4] += dxj * Fjz;
     w[5] += dyj * Fjz;
   }
-  atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+  if (slots)
+    store_slot<T>(a, a.own, (size_t)i, fix, fiy, fiz);
+  else
+    atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+}
+
+// atomic mode: the gather must see zero in the atom's own and short-list slots
+template <class T>
+__device__ __forceinline__ void clear_slots(const FwdArgs<T>& a, int i) {
+  store_slot<T>(a, a.own, (size_t)i, T(0), T(0), T(0));
+  int z = a.zcnt[i];
+  z = z < a.zs_cap ? z : a.zs_cap;
+  for (int q = 0; q < z; ++q) store_slot<T>(a, a.contrib, (size_t)q * a.n + i, T(0), T(0), T(0));
 }
 
 // ---------------------------------------------------------------- reduction
@@ -427,13 +501,13 @@ __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc
   if (threadIdx.x < 7) {
     double s = 0.0;
     for (int q = 0; q < BLOCK / 32; ++q) s += part[q][threadIdx.x];
-    atomicAdd(&acc[threadIdx.x], s);
+    atomicAdd(&acc[threadIdx.x * ACC_STRIDE], s);
   }
 }
 
 // ---------------------------------------------------------------- the kernel
 template <class T, int NS, int ZC, int MODE>
-__global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
+__global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
   __shared__ T srec_s[SREC];
@@ -448,18 +522,36 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdAr
   const T* srec = NS == 1 ? a.prm1 : srec_s;
   constexpr bool LAM3 = MODE == 1;
 
-  const int n_items = *a.n_items;
+  // launch-uniform words, read once per block
+  __shared__ int uni[5];
+  if (threadIdx.x == 0) {
+    uni[0] = *a.n_items;
+    uni[1] = a.flags[FLAG_REV_MISS];
+    uni[2] = a.flags[FLAG_DMAX];
+    uni[3] = a.n_items2 ? *a.n_items2 : 0;
+    uni[4] = a.n_items3 ? *a.n_items3 : 0;
+  }
+  __syncthreads();
+  const int n_first = uni[0];
+  const int n_second = uni[0] + uni[3];
+  const int n_items = a.identity ? a.n : n_second + uni[4];
+  // slots: contributions go to per-slot stores (needs the stored short list and
+  // its reverse map); otherwise FP64 atomics into the fallback buffer
+  const bool slots_ok = uni[1] == 0;
   // the stored short list holds every atom that can be inside a cutoff while no
   // atom has moved more than half the list margin since the build (uniform)
-  const bool use_short =
-      __int_as_float(*(volatile const int*)&a.flags[FLAG_DMAX]) <= a.dlim2;
+  const bool use_short = __int_as_float(uni[2]) <= a.dlim2;
+  const bool slots = !a.atomic_mode && use_short && slots_ok;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[FLAG_EXTRA] = slots ? 0 : 1;
   T ei = 0;
   T w[6] = {0, 0, 0, 0, 0, 0};
   bool any = false;
   for (int item = blockIdx.x * BLOCK + threadIdx.x; item < n_items;
        item += gridDim.x * BLOCK) {
     any = true;
-    const int i = a.order[item];
+    const int i = a.identity ? item
+                  : (item < n_first ? a.order[item]
+                     : (item < n_second ? a.order2[item - n_first] : a.order3[item - n_second]));
     T eatom_i = T(0);
     int ti;
     int z;
@@ -467,18 +559,45 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdAr
     const uint32_t* list;
     int c;
     bool general;
+    bool filtered = false;  // the register slots come from a cutoff mask over list
+    int z_list = 0;         // stored short-list length (slots mode bookkeeping)
     if (use_short) {
-      z = a.zcnt[i];
+      z_list = a.zcnt[i];
       ti = a.types[i];
       list = a.shortl;
-      c = z;
-      general = z > ZC || z > a.zs_cap;
-      if (z > a.zs_cap) {  // short list truncated: use the skin list
+      c = z_list;
+      z = z_list;
+      general = z_list > a.zs_cap;
+      if (general) {  // short list truncated: use the skin list
         list = a.nbr;
         c = min(a.cnt[i], a.cap);
+      } else if (z_list > ZC) {
+        // more stored entries than registers: keep those inside the cutoffs now
+        filtered = true;
+        T xi, yi, zi;
+        int tii;
+        Pos<T>::coarse(a, i, xi, yi, zi, tii);
+        const bool fits = z_list <= 64;
+        if (fits)
+          for (int s = 0; s < z_list; ++s) {
+            const uint32_t e = a.shortl[(size_t)s * a.n + i];
+            int j, ox, oy, oz;
+            decode(e, j, ox, oy, oz);
+            T xj, yj, zj;
+            int tj;
+            Pos<T>::coarse(a, j, xj, yj, zj, tj);
+            const T dx = (xj - xi) + ox * a.h[0];
+            const T dy = (yj - yi) + oy * a.h[1];
+            const T dz = (zj - zi) + oz * a.h[2];
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
+          }
+        z = __popcll(mask);
+        general = !fits || z > ZC;
       }
     } else {
       // filter the skin list into a bit mask (Sec. IV-D)
+      filtered = true;
       T xi, yi, zi;
       Pos<T>::coarse(a, i, xi, yi, zi, ti);
       c = min(a.cnt[i], a.cap);
@@ -502,15 +621,26 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdAr
       z = __popcll(mask);
       general = !fits || z > ZC;
     }
+    if (!slots && !a.atomic_mode) clear_slots<T>(a, i);
     if (general) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
-      general_atom<T, NS, LAM3>(a, srec, i, ti, list, c, eatom_i, w);
+      if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
+      general_atom<T, NS, LAM3>(a, srec, i, ti, list, c, slots && list == a.shortl, eatom_i,
+                                w);
     } else {
       using P = typename SelfPos<T>::type;
       const P pi = self_pos<T>(a, i);
       // 2. short list into registers
       T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC];
       int jj[ZC], tt[ZC];
+      const unsigned long long kept = mask;
+      // stored short list, not filtered: the ZC entries are loaded without
+      // waiting for the count (the list has at least ZC slots per atom)
+      uint32_t pre[ZC];
+      if (!filtered) {
+#pragma unroll
+        for (int q = 0; q < ZC; ++q) pre[q] = list[(size_t)q * a.n + i];
+      }
 #pragma unroll
       for (int q = 0; q < ZC; ++q) {
         ux[q] = uy[q] = uz[q] = T(0);
@@ -520,12 +650,12 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdAr
         tt[q] = 0;
         if (q < z) {
           uint32_t e;
-          if (use_short) {
-            e = a.shortl[(size_t)q * a.n + i];
-          } else {
-            const int s = __ffsll(mask) - 1;
+          if (filtered) {
+            const int sl = __ffsll(mask) - 1;
             mask &= mask - 1ull;
-            e = a.nbr[(size_t)s * a.n + i];
+            e = list[(size_t)sl * a.n + i];
+          } else {
+            e = pre[q];
           }
           T dx, dy, dz;
           int j, tj;
@@ -665,9 +795,15 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdAr
       }
       // force on i and virial from the neighbour forces; scatter
       T fix = 0, fiy = 0, fiz = 0;
+      unsigned long long left = kept;
 #pragma unroll
       for (int q = 0; q < ZC; ++q) {
         if (q < z) {
+          int sl = q;
+          if (filtered) {
+            sl = __ffsll(left) - 1;
+            left &= left - 1ull;
+          }
           fix -= fx[q];
           fiy -= fy[q];
           fiz -= fz[q];
@@ -678,10 +814,20 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff(const __grid_constant__ FwdAr
           w[3] += dx * fy[q];
           w[4] += dx * fz[q];
           w[5] += dy * fz[q];
-          atomic_add3(a.f, jj[q], to_f64(fx[q]), to_f64(fy[q]), to_f64(fz[q]));
+          if (slots)
+            store_slot<T>(a, a.contrib, (size_t)sl * a.n + i, fx[q], fy[q], fz[q]);
+          else
+            atomic_add3(a.f, jj[q], to_f64(fx[q]), to_f64(fy[q]), to_f64(fz[q]));
         }
       }
-      atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+      if (slots && filtered)  // stored entries outside the cutoffs now get zero
+        for (int s = 0; s < z_list; ++s)
+          if (!((kept >> s) & 1ull))
+            store_slot<T>(a, a.contrib, (size_t)s * a.n + i, T(0), T(0), T(0));
+      if (slots)
+        store_slot<T>(a, a.own, (size_t)i, fix, fiy, fiz);
+      else
+        atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
     }
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     ei += eatom_i;

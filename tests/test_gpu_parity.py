@@ -37,8 +37,9 @@ def dev(a, dtype=torch.float64):
     return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def gpu_eval(T, prec, x, t, box, table, r_list):
+def gpu_eval(T, prec, x, t, box, table, r_list, scatter=0):
     ctx = T.Context(prec)
+    ctx.set_scatter(scatter)
     ctx.params(table)
     xd, td = dev(x), dev(t, torch.int32)
     ctx.neighbor_build(xd, td, box, r_list)
@@ -117,11 +118,12 @@ def test_neighbor_lists_bit_exact(T, sysd, r_list):
 
 @pytest.mark.parametrize("sysd", SMALL, ids=IDS)
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-def test_compute_matches_oracle(T, sysd, prec):
+@pytest.mark.parametrize("scatter", [0, 1], ids=["gather", "atomic"])
+def test_compute_matches_oracle(T, sysd, prec, scatter):
     _, x, t, box, table = sysd
     r_list = RC + 0.5 if box.min() >= 2 * (RC + 0.5) else RC
     ref = oracle.compute(x, t, box, table, oracle.neighbors(x, box, RC), nthreads=4)
-    got = gpu_eval(T, prec, x, t, box, table, r_list)
+    got = gpu_eval(T, prec, x, t, box, table, r_list, scatter)
     check(prec, got, ref)
 
 
@@ -282,7 +284,8 @@ def _md_inputs(ncell=3, seed=50):
     return x, v, t, box
 
 
-def test_md_fp64_matches_oracle(T):
+@pytest.mark.parametrize("scatter", [0, 1], ids=["gather", "atomic"])
+def test_md_fp64_matches_oracle(T, scatter):
     x, v, t, box = _md_inputs(ncell=4)
     table = si_table()
     mass = [W.MASS_AMU["Si"]]
@@ -290,6 +293,7 @@ def test_md_fp64_matches_oracle(T):
     xo, vo, thermo_o, fo = oracle.md_run(x, v, t, box, table, mass, 0.001, nsteps, RC + 1.0,
                                          every)
     ctx = T.Context(T.FP64)
+    ctx.set_scatter(scatter)
     ctx.params(table)
     xd, vd = dev(x), dev(v)
     ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
@@ -383,4 +387,22 @@ def test_md_graph_overflow_rolls_back(T):
     cap, _ = ctx.neighbor_capacity()
     assert cap > cnt_ref.max()  # the overflow was caught and the capacity grown
     assert np.abs(xd.cpu().numpy() - xo).max() < 1e-8
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_forces_bitwise_reproducible(T, prec):
+    # forces are gathered from per-slot contributions in a fixed order (exact
+    # fixed point on the mixed path): two evaluations agree bit for bit
+    x, t, box = S.sic_cell(n=6, seed=70)
+    ctx = T.Context(prec)
+    ctx.params(sic_table())
+    xd = dev(x)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 0.5)
+    f1 = torch.zeros_like(xd)
+    f2 = torch.zeros_like(xd)
+    ctx.compute(xd, None, f1)
+    ctx.compute(xd, None, f2)
+    torch.cuda.synchronize()
+    assert torch.equal(f1, f2)
     ctx.close()
