@@ -129,6 +129,38 @@ int tersoff_neighbor_export(tersoff_ctx* ctx, int* cnt, int* nbr, int cap, void*
 int tersoff_compute(tersoff_ctx* ctx, const double* x, int n, double* energy,
                     double* forces, double* virial, void* stream);
 
+/* Largest atom count accepted by tersoff_compute_noalloc. */
+#define TERSOFF_NOALLOC_MAX_ATOMS 65536
+
+/* The energy, forces and virial of tersoff_compute (same arguments, same
+ * results up to rounding order), computed without allocating any memory in
+ * this call. The paper has no counterpart: this is a library facility.
+ *
+ * Who needs it: callers that must not ask the CUDA runtime for memory while
+ * they run. Examples are a program that has handed nearly all device memory
+ * to its own pool (an allocation could fail, or force that pool to give memory
+ * back), and a latency-sensitive loop sharing the GPU with other streams
+ * (freeing device memory waits for the whole device). tersoff_compute may
+ * allocate per-neighbour buffers on its first call and after a precision or
+ * capacity change; this call never does.
+ *
+ * How: forces are added with FP64 atomics (as with TERSOFF_SCATTER_ATOMIC,
+ * whatever the context's scatter mode) into a scratch array of fixed size
+ * that is part of the library (one per device, about 1.5 MiB), then copied to
+ * the outputs. The first call on a device looks up that array's address (and
+ * makes the CUDA runtime load the library's device code there if it has not
+ * yet); make that first call before any stream capture.
+ *
+ * Limits: n <= TERSOFF_NOALLOC_MAX_ATOMS, else TERSOFF_E_INVALID_ARG with
+ * nothing enqueued. Every call on a device, from any context, uses the same
+ * scratch array: two calls whose work overlaps on the GPU (different streams
+ * without an ordering between them) race and give wrong results. Each call
+ * clears the parts it accumulates into before use. The context must hold a
+ * neighbour list built for these atoms (tersoff_neighbor_build, which does
+ * allocate). */
+int tersoff_compute_noalloc(tersoff_ctx* ctx, const double* x, int n, double* energy,
+                            double* forces, double* virial, void* stream);
+
 /* Per-atom energy of the last tersoff_compute (device, N doubles): the pair
  * terms V(i, j, zeta_ij) summed over j, assigned to the centre atom i. */
 int tersoff_compute_peratom(tersoff_ctx* ctx, const double* x, int n, double* eatom,

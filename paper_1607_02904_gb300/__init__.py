@@ -13,6 +13,7 @@ from ._lib import (  # noqa: F401
     SCATTER_GATHER,
     SCATTER_ATOMIC,
     NPARAM,
+    NOALLOC_MAX_ATOMS,
     load,
     library_path,
     declared_symbols,

@@ -25,6 +25,7 @@ MIXED = 1
 SCATTER_GATHER = 0
 SCATTER_ATOMIC = 1
 NPARAM = 14
+NOALLOC_MAX_ATOMS = 65536
 
 _lib = None
 
@@ -43,6 +44,7 @@ _SIG = {
     "tersoff_neighbor_export": ([_P, _P, _P, _I, _P], _I),
     "tersoff_compute": ([_P, _P, _I, _P, _P, _P, _P], _I),
     "tersoff_compute_peratom": ([_P, _P, _I, _P, _P], _I),
+    "tersoff_compute_noalloc": ([_P, _P, _I, _P, _P, _P, _P], _I),
     "tersoff_md_step": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_md_step_host": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_launch_count": ([_P, _P], _I),
@@ -170,6 +172,14 @@ class Context:
     def compute(self, x, energy=None, forces=None, virial=None, stream=None):
         self._check(self.lib.tersoff_compute(self.h, _ptr(x), int(x.shape[0]), _ptr(energy),
                                              _ptr(forces), _ptr(virial), _stream(stream)))
+
+    def compute_noalloc(self, x, energy=None, forces=None, virial=None, stream=None):
+        """tersoff_compute without any memory allocation in the call (fixed
+        scratch inside the library; at most NOALLOC_MAX_ATOMS atoms; calls
+        that overlap on the GPU share that scratch and race)."""
+        self._check(self.lib.tersoff_compute_noalloc(self.h, _ptr(x), int(x.shape[0]),
+                                                     _ptr(energy), _ptr(forces), _ptr(virial),
+                                                     _stream(stream)))
 
     def compute_peratom(self, x, eatom, stream=None):
         self._check(self.lib.tersoff_compute_peratom(self.h, _ptr(x), int(x.shape[0]),

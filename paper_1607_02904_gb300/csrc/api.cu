@@ -542,6 +542,38 @@ int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eato
   return compute_impl(c, x, n, nullptr, nullptr, nullptr, eatom, (cudaStream_t)stream);
 }
 
+// The compute sequence with the force kernel's accumulators in the fixed
+// scratch array (forces scattered with atomics, so no per-slot buffers); uses
+// only buffers that the neighbour build has already sized.
+int tersoff_compute_noalloc(tersoff_ctx* p, const double* x, int n, double* energy,
+                            double* forces, double* virial, void* stream) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (n < 0 || n > TERSOFF_NOALLOC_MAX_ATOMS)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG,
+                     "tersoff_compute_noalloc: n exceeds TERSOFF_NOALLOC_MAX_ATOMS (65536)");
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (n != c->n || (n > 0 && !x))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
+  double* scr = nullptr;
+  size_t len = 0;
+  if ((st = tgb::noalloc_scratch(c, &scr, &len))) return st;
+  const size_t used = (size_t)tgb::ACC_LEN + 3 * (size_t)n;
+  if (used > len) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "fixed scratch too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = tgb::launch_pack_positions(c, x, false, s))) return st;
+  TGB_CUDA(c, cudaMemsetAsync(scr, 0, sizeof(double) * used, s));
+  TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_EXTRA_STICKY, 0, sizeof(int), s));
+  const bool was_atomic = c->scatter_atomic;
+  c->scatter_atomic = true;  // read by the launch below only
+  st = tgb::launch_forward(c, scr + tgb::ACC_LEN, scr, nullptr, s);
+  c->scatter_atomic = was_atomic;
+  if (st) return st;
+  return tgb::launch_noalloc_out(c, scr, n, forces, energy, virial, s);
+}
+
 // Enqueues nsteps velocity-Verlet steps. sync_builds: rebuild with a host
 // check (eager); otherwise without host synchronisation (graph capture).
 static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,

@@ -269,5 +269,10 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
 // thermo (nsteps x 3: potential, kinetic [eV], total) from the accumulator rows
 int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, double* thermo,
                        cudaStream_t s);
+// Fixed scratch of tersoff_compute_noalloc (noalloc.cu): the current device's
+// array and its length in doubles; and the copy of its results to the outputs.
+int noalloc_scratch(Ctx* c, double** out, size_t* doubles);
+int launch_noalloc_out(Ctx* c, const double* scr, int n, double* forces, double* energy,
+                       double* virial, cudaStream_t s);
 
 }  // namespace tgb
