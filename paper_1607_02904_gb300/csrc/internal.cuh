@@ -134,6 +134,7 @@ struct Ctx {
   int contrib_prec = -1;
   bool scatter_atomic = false;    // forces by FP64 atomics instead of slots + gather
   int nbucket[3] = {0, 0, 0};     // bucket sizes at the last build
+  int nwide = 0;                  // FLAG_WIDE at the last build
   int zs_cap = 0;
   double margin = 0.0;            // short-list radius margin beyond the cutoffs
   double* d_trow = nullptr;       // MD thermo accumulation rows (ACC_LEN doubles per step)
@@ -207,6 +208,8 @@ enum : int {
   FLAG_DMAX = 2 * FLAG_STRIDE,          // running max squared displacement since the build (float bits)
   FLAG_BUCKET = 3 * FLAG_STRIDE,        // 3 words: atoms per short-list size bucket (<= 4, <= 8, more)
   FLAG_REV_MISS = 6 * FLAG_STRIDE,      // a short-list entry has no reverse entry
+  FLAG_WIDE = 7 * FLAG_STRIDE,          // atoms with more than 4 list entries inside the
+                                        // filter radii themselves (no margin)
   FLAG_BUILD_WORDS = 8 * FLAG_STRIDE,
   FLAG_NONFINITE = 8 * FLAG_STRIDE,     // non-finite position seen by a build
   FLAG_FALLBACK = 9 * FLAG_STRIDE,      // atoms handled by the general path

@@ -202,13 +202,14 @@ __global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
     const int* __restrict__ cell_atoms, GridDev g, double rc2, float lo2, float hi2, int cap,
-    uint32_t* __restrict__ nbr, int* __restrict__ cnt, Radii lim, int ns,
+    uint32_t* __restrict__ nbr, int* __restrict__ cnt, Radii lim, Radii core, int ns,
     uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
     int* __restrict__ flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
   int count = 0;
   int z = 0;
+  int zw = 0;  // entries inside the filter radii without the margin
   if (active) {
     const float4 pi = pos32[i];
     const int ti = __float_as_int(pi.w);
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(128) k_neigh(
               if (r2 <= lim.r2[ti * ns + __float_as_int(pj.w)]) {
                 if (z < cap) shortl[(size_t)z * n + i] = e;
                 ++z;
+                zw += r2 <= core.r2[ti * ns + __float_as_int(pj.w)] ? 1 : 0;
               }
             }
           }
@@ -266,10 +268,11 @@ __global__ void __launch_bounds__(128) k_neigh(
     zcnt[i] = z;
   }
   // block-level aggregation: one atomic per block and word
-  __shared__ int s_max[2], s_ovf, s_cnt[3], s_base[3], s_wcnt[4][3];
+  __shared__ int s_max[2], s_ovf, s_wide, s_cnt[3], s_base[3], s_wcnt[4][3];
   if (threadIdx.x == 0) {
     s_max[0] = s_max[1] = 0;
     s_ovf = 0;
+    s_wide = 0;
     s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
   }
   __syncthreads();
@@ -280,6 +283,7 @@ __global__ void __launch_bounds__(128) k_neigh(
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool ovf = __any_sync(0xffffffffu, active && count > cap);
+  const int wide = __popc(__ballot_sync(0xffffffffu, active && zw > 4));
   // bucket by short-list size (<= 4, <= 8, more)
   const int b = z <= 4 ? 0 : (z <= 8 ? 1 : 2);
   unsigned msk[3];
@@ -288,6 +292,7 @@ __global__ void __launch_bounds__(128) k_neigh(
     atomicMax(&s_max[0], mc);
     atomicMax(&s_max[1], mz);
     if (ovf) s_ovf = 1;
+    if (wide) atomicAdd(&s_wide, wide);
     for (int q = 0; q < 3; ++q) s_wcnt[wid][q] = __popc(msk[q]);
   }
   __syncthreads();
@@ -295,6 +300,7 @@ __global__ void __launch_bounds__(128) k_neigh(
     if (s_max[0] > 0) atomicMax(&flags[FLAG_OVERFLOW], s_max[0]);
     if (s_max[1] > 0) atomicMax(&flags[FLAG_SHORT_MAX], s_max[1]);
     if (s_ovf) atomicOr(&flags[FLAG_OVF_ANY], 1);
+    if (s_wide) atomicAdd(&flags[FLAG_WIDE], s_wide);
     for (int q = 0; q < 3; ++q) {
       int tot = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wcnt[w][q];
@@ -416,19 +422,20 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const double band = 64.0 * (4.0 * hmax) * (4.0 * hmax) * 1.2e-7 + 1e-6;
   const float lo2 = (float)(rc2 - band);
   const float hi2 = (float)(rc2 + band);
-  Radii lim;
-  for (int q = 0; q < TERSOFF_MAX_SPECIES * TERSOFF_MAX_SPECIES; ++q) lim.r2[q] = 0.0f;
+  Radii lim, core;
+  for (int q = 0; q < TERSOFF_MAX_SPECIES * TERSOFF_MAX_SPECIES; ++q) lim.r2[q] = core.r2[q] = 0.0f;
   // symmetric in the two species, so that short-list membership is mutual
   for (int a = 0; a < c->ns; ++a)
     for (int b = 0; b < c->ns; ++b) {
       const double rf = fmax(c->filt[(size_t)a * c->ns + b], c->filt[(size_t)b * c->ns + a]);
       const double r = rf + c->margin;
       lim.r2[a * c->ns + b] = (float)(r * r * (1.0 + 1e-6));
+      core.r2[a * c->ns + b] = (float)(rf * rf);
     }
   if (n > 0) {
     k_neigh<<<(n + 127) / 128, 128, 0, s>>>(n, x, c->d_pos32, c->d_cell_of, c->d_cell_start,
                                             c->d_cell_atoms, g, rc2, lo2, hi2, c->cap, c->d_nbr,
-                                            c->d_cnt, lim, c->ns, c->d_short, c->d_zcnt,
+                                            c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
                                             c->d_bucket, c->d_flags);
     k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
                                           c->d_flags);
