@@ -129,6 +129,23 @@ int tersoff_neighbor_export(tersoff_ctx* ctx, int* cnt, int* nbr, int cap, void*
 int tersoff_compute(tersoff_ctx* ctx, const double* x, int n, double* energy,
                     double* forces, double* virial, void* stream);
 
+/* Adjoint of tersoff_compute (for fitting the parameters). The paper has no
+ * backward pass; this is the derivative of Eq. 5-7 with respect to the table
+ * entries and the positions. For the weights gE (device, 1 double: the
+ * derivative of the caller's loss with respect to E) and gF (device, N x 3,
+ * the derivative with respect to the forces; NULL means zero):
+ *   grad_table (device, n_species^3 x TERSOFF_NPARAM doubles, table layout)
+ *       = d/dtheta [ gE E + sum_a gF_a . F_a ]      (field m gets 0: integer)
+ *   grad_x (device, N x 3) = gE dE/dx = -gE F.
+ * The three-body sums are recomputed, not stored by the forward call. Either
+ * output may be NULL. grad_x with gF != NULL (the position derivative of the
+ * force term, a Hessian-vector product) is not provided and returns
+ * TERSOFF_E_INVALID_ARG. x: positions of the atoms of the last neighbour build
+ * (as for tersoff_compute). Arithmetic follows the context's precision (mixed:
+ * per-term float, gradient sums in double). */
+int tersoff_backward(tersoff_ctx* ctx, const double* x, int n, const double* gE,
+                     const double* gF, double* grad_x, double* grad_table, void* stream);
+
 /* Largest atom count accepted by tersoff_compute_noalloc. */
 #define TERSOFF_NOALLOC_MAX_ATOMS 65536
 

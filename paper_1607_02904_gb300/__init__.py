@@ -3,7 +3,8 @@
 The compute path is the CUDA library ``libtersoff_gb300.so`` (C ABI in
 ``include/tersoff.h``); this package binds it (``Context``), builds the
 per-triplet parameter table from element parameters (``params``), and wraps
-the energy in a ``torch.autograd.Function``.
+energy and forces in a ``torch.autograd.Function`` whose backward is the
+library's adjoint kernel (``autograd``).
 """
 from ._lib import (  # noqa: F401
     Context,
@@ -19,3 +20,4 @@ from ._lib import (  # noqa: F401
     declared_symbols,
 )
 from .params import mix_tersoff89, FIELDS  # noqa: F401
+from .autograd import TersoffSystem, TersoffFunction, energy_forces  # noqa: F401

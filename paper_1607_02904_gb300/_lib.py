@@ -45,6 +45,7 @@ _SIG = {
     "tersoff_compute": ([_P, _P, _I, _P, _P, _P, _P], _I),
     "tersoff_compute_peratom": ([_P, _P, _I, _P, _P], _I),
     "tersoff_compute_noalloc": ([_P, _P, _I, _P, _P, _P, _P], _I),
+    "tersoff_backward": ([_P, _P, _I, _P, _P, _P, _P, _P], _I),
     "tersoff_md_step": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_md_step_host": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_launch_count": ([_P, _P], _I),
@@ -172,6 +173,12 @@ class Context:
     def compute(self, x, energy=None, forces=None, virial=None, stream=None):
         self._check(self.lib.tersoff_compute(self.h, _ptr(x), int(x.shape[0]), _ptr(energy),
                                              _ptr(forces), _ptr(virial), _stream(stream)))
+
+    def backward(self, x, gE, gF=None, grad_x=None, grad_table=None, stream=None):
+        """gE: device float64 (1,); gF: device (N, 3) or None. Writes grad_x
+        (-gE F) and grad_table (d/dtheta [gE E + sum gF . F], flat table layout)."""
+        self._check(self.lib.tersoff_backward(self.h, _ptr(x), int(x.shape[0]), _ptr(gE), _ptr(gF),
+                                              _ptr(grad_x), _ptr(grad_table), _stream(stream)))
 
     def compute_noalloc(self, x, energy=None, forces=None, virial=None, stream=None):
         """tersoff_compute without any memory allocation in the call (fixed

@@ -1,0 +1,103 @@
+"""Energy and forces as differentiable functions of positions and parameters.
+
+``energy_forces(system, x, table)`` returns (E, F) from the CUDA library's
+``tersoff_compute``; its backward runs the library's adjoint kernel
+(``tersoff_backward``): the gradient of ``gE E + sum_a gF_a . F_a`` with respect
+to the parameter table, and ``dE/dx = -F`` for the positions. The position
+derivative of the forces (a Hessian-vector product) is not provided: a loss
+that uses the forces can be differentiated with respect to the table, not the
+positions. Everything here marshals arguments; the arithmetic runs in the
+library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from ._lib import MIXED, NPARAM, Context
+
+
+class TersoffSystem:
+    """One periodic system: a library context holding the species, box,
+    neighbour list and the parameter table last uploaded.
+
+    types: (N,) int species; box: 3 edges (A); r_list: cutoff plus skin (A).
+    The list is rebuilt whenever a new table is uploaded (the filter radii
+    depend on the cutoffs) or ``rebuild(x)`` is called."""
+
+    def __init__(self, types, box, r_list, precision=MIXED, device=None):
+        self.device = torch.device(device if device is not None else "cuda")
+        self.ctx = Context(precision)
+        self.types = torch.as_tensor(np.asarray(types), dtype=torch.int32,
+                                     device=self.device).contiguous()
+        self.box = np.ascontiguousarray(box, dtype=np.float64)
+        self.r_list = float(r_list)
+        self._table = None
+        self.version = 0
+        self.ntable = 0
+
+    def load(self, x, table):
+        """Upload ``table`` (if its values changed) and build the list at x."""
+        t = table.detach().to("cpu", torch.float64).contiguous().numpy().ravel()
+        if self._table is None or t.shape != self._table.shape or not np.array_equal(t, self._table):
+            self.ctx.params(t)
+            self._table = t.copy()
+            self.ntable = t.size
+            self.version += 1
+            self.rebuild(x)
+
+    def rebuild(self, x):
+        self.ctx.neighbor_build(x.detach().contiguous(), self.types, self.box, self.r_list)
+
+
+class TersoffFunction(torch.autograd.Function):
+    """(E, F) = f(x, table) for one ``TersoffSystem``."""
+
+    @staticmethod
+    def forward(fctx, x, table, system):
+        xd = x.detach().contiguous()
+        system.load(xd, table)
+        e = torch.empty(1, dtype=torch.float64, device=xd.device)
+        f = torch.empty_like(xd)
+        system.ctx.compute(xd, e, f)
+        fctx.system = system
+        fctx.version = system.version
+        fctx.table_shape = table.shape
+        fctx.table_device = table.device
+        fctx.set_materialize_grads(False)
+        fctx.save_for_backward(xd)
+        return e.reshape(()), f
+
+    @staticmethod
+    def backward(fctx, gE, gF):
+        (x,) = fctx.saved_tensors
+        system = fctx.system
+        if system.version != fctx.version:
+            raise RuntimeError("the system's parameter table changed after this forward call")
+        need_x, need_t = fctx.needs_input_grad[0], fctx.needs_input_grad[1]
+        dev = x.device
+        if gE is None:
+            ge = torch.zeros(1, dtype=torch.float64, device=dev)
+        else:
+            ge = gE.reshape(1).to(dev, torch.float64).contiguous()
+        gf = None if gF is None else gF.to(dev, torch.float64).contiguous()
+        if need_x and gf is not None:
+            raise RuntimeError("the position derivative of the forces (a Hessian-vector "
+                               "product) is not provided; differentiate a force loss with "
+                               "respect to the table only")
+        gx = torch.empty_like(x) if need_x else None
+        gt = torch.empty(system.ntable, dtype=torch.float64, device=dev) if need_t else None
+        if need_x or need_t:
+            system.ctx.backward(x, ge, gf, gx, gt)
+        if gt is not None:
+            gt = gt.reshape(fctx.table_shape).to(fctx.table_device)
+        return gx, gt, None
+
+
+def energy_forces(system: TersoffSystem, x: torch.Tensor, table: torch.Tensor):
+    """Energy (0-dim) and forces (N, 3), differentiable in ``table`` (both) and
+    in ``x`` (energy only)."""
+    return TersoffFunction.apply(x, table, system)
+
+
+__all__ = ["TersoffSystem", "TersoffFunction", "energy_forces", "NPARAM"]

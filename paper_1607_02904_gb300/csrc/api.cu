@@ -292,8 +292,8 @@ int tersoff_destroy(tersoff_ctx* p) {
   Ctx* c = &p->impl;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  void* bufs[] = {c->d_rec64, c->d_rec32, c->d_filt64, c->d_filt32, c->d_types, c->d_cnt,
-                  c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
+  void* bufs[] = {c->d_rec64, c->d_rec32, c->d_raw64, c->d_raw32, c->d_filt64, c->d_filt32,
+                  c->d_types, c->d_cnt, c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
                   c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
@@ -426,6 +426,16 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
   if ((st = tgb::dev_alloc(c, &c->d_filt32, f32.size()))) return st;
   TGB_CUDA(c, cudaMemcpy(c->d_rec64, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
   TGB_CUDA(c, cudaMemcpy(c->d_rec32, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
+  {
+    // raw records for the backward pass (table layout, both precisions)
+    const size_t nraw = (size_t)nrec * TERSOFF_NPARAM;
+    std::vector<float> raw32(nraw);
+    for (size_t q = 0; q < nraw; ++q) raw32[q] = (float)table[q];
+    if ((st = tgb::dev_alloc(c, &c->d_raw64, nraw))) return st;
+    if ((st = tgb::dev_alloc(c, &c->d_raw32, nraw))) return st;
+    TGB_CUDA(c, cudaMemcpy(c->d_raw64, table, sizeof(double) * nraw, cudaMemcpyHostToDevice));
+    TGB_CUDA(c, cudaMemcpy(c->d_raw32, raw32.data(), sizeof(float) * nraw, cudaMemcpyHostToDevice));
+  }
   TGB_CUDA(c, cudaMemcpy(c->d_filt64, f64.data(), sizeof(double) * f64.size(), cudaMemcpyHostToDevice));
   TGB_CUDA(c, cudaMemcpy(c->d_filt32, f32.data(), sizeof(float) * f32.size(), cudaMemcpyHostToDevice));
   c->gen++;
@@ -541,6 +551,33 @@ int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eato
   if (!c) return TERSOFF_E_INVALID_ARG;
   if (!eatom && n > 0) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "eatom is null");
   return compute_impl(c, x, n, nullptr, nullptr, nullptr, eatom, (cudaStream_t)stream);
+}
+
+int tersoff_backward(tersoff_ctx* p, const double* x, int n, const double* gE, const double* gF,
+                     double* grad_x, double* grad_table, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (n != c->n || (n > 0 && !x))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
+  if (!gE) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "gE is null");
+  if (grad_x && gF)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG,
+                     "the position derivative of the force term (a Hessian-vector product) "
+                     "is not provided: grad_x requires gF == NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (grad_table) {
+    const size_t nraw = (size_t)c->ns * c->ns * c->ns * TERSOFF_NPARAM;
+    if ((st = tgb::launch_pack_positions(c, x, false, s))) return st;
+    TGB_CUDA(c, cudaMemsetAsync(grad_table, 0, sizeof(double) * nraw, s));
+    if ((st = tgb::launch_backward(c, gE, gF, grad_table, s))) return st;
+  }
+  if (grad_x) {
+    if ((st = compute_impl(c, x, n, nullptr, grad_x, nullptr, nullptr, s))) return st;
+    if ((st = tgb::launch_scale_forces(c, grad_x, gE, s))) return st;
+  }
+  return TERSOFF_OK;
 }
 
 // The compute sequence with the force kernel's accumulators in the fixed

@@ -88,6 +88,8 @@ struct Ctx {
   std::vector<double> table;      // raw, host
   double* d_rec64 = nullptr;      // derived records, device
   float* d_rec32 = nullptr;
+  double* d_raw64 = nullptr;      // raw table (backward pass), device
+  float* d_raw32 = nullptr;
   std::vector<double> h_rec64;    // host copies
   std::vector<float> h_rec32;
   cudaStream_t side = nullptr;    // side stream for small force launches
@@ -272,6 +274,10 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
 // thermo (nsteps x 3: potential, kinetic [eV], total) from the accumulator rows
 int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, double* thermo,
                        cudaStream_t s);
+// Parameter adjoint (tersoff_bwd.cu): adds d/dtheta [gE E + sum gF . F] to
+// grad (ns^3 x TERSOFF_NPARAM); positions must be packed. And f = -gE f.
+int launch_backward(Ctx* c, const double* gE, const double* gF, double* grad, cudaStream_t s);
+int launch_scale_forces(Ctx* c, double* f, const double* gE, cudaStream_t s);
 // Fixed scratch of tersoff_compute_noalloc (noalloc.cu): the current device's
 // array and its length in doubles; and the copy of its results to the outputs.
 int noalloc_scratch(Ctx* c, double** out, size_t* doubles);

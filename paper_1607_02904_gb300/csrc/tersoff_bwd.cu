@@ -1,0 +1,456 @@
+// Adjoint of the Tersoff energy and forces with respect to the parameter table
+// (the derivative of Sec. III Eq. 5-7 in the table entries; the paper itself
+// has no backward pass).
+//
+// For weights gE (energy) and gF (one 3-vector per atom) the kernel adds
+//   d/dtheta [ gE E + sum_a gF_a . F_a ]
+// to grad (n_species^3 records of TERSOFF_NPARAM doubles, table layout).
+//
+// With F_a = -dE/dx_a and E = sum_i E_i (E_i: the terms centred on atom i,
+// which depend on the bond vectors d_ij = x_j - x_i only), the force term is
+//   sum_a gF_a . F_a = - sum_i D_w E_i,   D_w E_i = sum_j dE_i/dd_ij . w_ij,
+// with w_ij = gF_j - gF_i: minus the derivative of E_i along the bond
+// perturbations w. Per centre atom the kernel evaluates
+//   L_i = gE E_i - D_w E_i
+// forward (each quantity together with its derivative along w: r_j and its
+// rate rd_j = u_j . w_j, cos(theta_jk) and its rate, zeta_ij and its rate) and
+// differentiates L_i with respect to the parameters in reverse, in the loop
+// order of Algorithm 2: a first K loop forms zeta_ij and its rate, the pair
+// level gives the adjoints of zeta and its rate, and a second K loop
+// recomputes every three-body term and adds the adjoints of its parameters.
+// Nothing per triplet is stored.
+//
+// Record roles as in the forward evaluation: record (ti,tj,tj) supplies the
+// pair terms of bond i-j (A, lambda1, B, lambda2, beta, n and the R, D of
+// f_C(r_ij)); record (ti,tj,tk) supplies the three-body terms (gamma, c, d, h,
+// lambda3, m and the R, D of f_C(r_ik)). m is an integer and gets no gradient.
+//
+// Per-term arithmetic in T (float on the mixed path, double on the FP64
+// path); every gradient sum is accumulated in double.
+#include <cstring>
+
+#include "tersoff_fwd.cuh"
+
+namespace tgb {
+namespace bwd {
+
+using fwd::Bond;
+using fwd::SelfPos;
+using fwd::self_pos;
+using fwd::to_f64;
+
+constexpr int BLOCK = 128;
+constexpr int NP = TERSOFF_NPARAM;
+
+template <class T> struct BwdArgs {
+  fwd::FwdArgs<T> g;      // geometry: packed positions, skin list, filter radii
+  const T* raw;           // ns^3 raw records (table layout)
+  const double* gE;       // energy weight(s): gE[cell(i)]
+  const int* atom_cell;   // optional: cell of each atom (NULL: one cell)
+  const double* gF;       // optional: N x 3 force weights
+  double* grad;           // ns^3 x NP, accumulated
+};
+
+// ------------------------------------------------------------------ math
+template <class T> struct BM;
+template <> struct BM<float> {
+  static __device__ __forceinline__ float ex(float x) { return expf(x); }
+  static __device__ __forceinline__ float ln(float x) { return logf(x); }
+  static __device__ __forceinline__ float ln1p(float x) { return log1pf(x); }
+  static __device__ __forceinline__ float pw(float x, float y) { return powf(x, y); }
+  static __device__ __forceinline__ void scpi(float x, float* s, float* c) {
+    sincospif(x, s, c);
+  }
+  static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+};
+template <> struct BM<double> {
+  static __device__ __forceinline__ double ex(double x) { return exp(x); }
+  static __device__ __forceinline__ double ln(double x) { return log(x); }
+  static __device__ __forceinline__ double ln1p(double x) { return log1p(x); }
+  static __device__ __forceinline__ double pw(double x, double y) { return pow(x, y); }
+  static __device__ __forceinline__ void scpi(double x, double* s, double* c) {
+    sincospi(x, s, c);
+  }
+  static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+};
+
+// f_C(r; R, D), its r-derivative, and the R- and D-derivatives of both.
+template <class T> struct Cut {
+  T fc, dfc, fc_R, fc_D, dfc_R, dfc_D;
+};
+template <class T>
+__device__ __forceinline__ Cut<T> cutoff_ad(T r, T R, T D) {
+  Cut<T> o;
+  if (r <= R - D) {
+    o.fc = T(1);
+    o.dfc = o.fc_R = o.fc_D = o.dfc_R = o.dfc_D = T(0);
+    return o;
+  }
+  if (r >= R + D) {
+    o.fc = o.dfc = o.fc_R = o.fc_D = o.dfc_R = o.dfc_D = T(0);
+    return o;
+  }
+  // x = pi (r - R) / (2 D)
+  const T q = (r - R) / (T(2) * D);
+  T s, c;
+  BM<T>::scpi(q, &s, &c);
+  const T PI = T(3.14159265358979323846);
+  const T x = PI * q;
+  const T k = PI / (T(4) * D);  // pi / (4 D)
+  o.fc = T(0.5) - T(0.5) * s;
+  o.dfc = -k * c;
+  o.fc_R = k * c;
+  o.fc_D = T(0.5) * c * x / D;
+  o.dfc_R = -k * PI / (T(2) * D) * s;
+  o.dfc_D = k / D * (c - x * s);
+  return o;
+}
+
+// g(cos) = gamma (1 + c^2/d^2 - c^2/(d^2 + (h - cos)^2)), its cos-derivative,
+// and the gamma, c, d, h derivatives of both. With t = h - cos and
+// Den = d^2 + t^2 the forms below have no cancellation.
+template <class T> struct Ang {
+  T g, dg, g_ga, g_c, g_d, g_h, dg_ga, dg_c, dg_d, dg_h;
+};
+template <class T>
+__device__ __forceinline__ Ang<T> angular_ad(T cs, T ga, T c, T d, T h) {
+  Ang<T> o;
+  const T t = h - cs;
+  const T t2 = t * t;
+  const T d2 = d * d;
+  const T den = d2 + t2;
+  const T iden = T(1) / den;
+  const T iden2 = iden * iden;
+  const T c2 = c * c;
+  const T r = t2 / (d2 * den);  // (1/d^2 - 1/Den)
+  o.g_ga = T(1) + c2 * r;
+  o.g = ga * o.g_ga;
+  o.g_c = T(2) * ga * c * r;
+  o.g_d = -T(2) * ga * c2 * t2 * (T(2) * d2 + t2) / (d2 * d * den * den);
+  o.dg = -T(2) * ga * c2 * t * iden2;
+  o.g_h = -o.dg;
+  o.dg_ga = -T(2) * c2 * t * iden2;
+  o.dg_c = -T(4) * ga * c * t * iden2;
+  o.dg_d = T(8) * ga * c2 * t * d * iden2 * iden;
+  o.dg_h = -T(2) * ga * c2 * (den - T(4) * t2) * iden2 * iden;
+  return o;
+}
+
+// X(Delta) = exp((lambda3 Delta)^m), dX/dDelta, and their lambda3-derivatives.
+template <class T> struct Expo {
+  T x, dx, x_l, dx_l;
+};
+template <class T>
+__device__ __forceinline__ Expo<T> expo_ad(T delta, T l3, int m) {
+  Expo<T> o;
+  const T a = l3 * delta;
+  T am1 = T(1);
+  for (int s = 1; s < m; ++s) am1 *= a;
+  const T am = am1 * a;
+  o.x = BM<T>::ex(am);
+  o.dx = T(m) * l3 * am1 * o.x;
+  o.x_l = T(m) * am1 * delta * o.x;
+  o.dx_l = T(m) * T(m) * am1 * (T(1) + am) * o.x;
+  return o;
+}
+
+// b(zeta) = (1 + (beta zeta)^n)^(-1/(2n)), b' = db/dzeta, b'' and the beta, n
+// derivatives of b and b'. zeta = 0 gives b = 1 and zero derivatives.
+template <class T> struct Bo {
+  T b, db, ddb, b_be, b_n, db_be, db_n;
+};
+template <class T>
+__device__ __forceinline__ Bo<T> bond_ad(T zeta, T be, T n) {
+  Bo<T> o;
+  if (!(zeta > T(0))) {
+    o.b = T(1);
+    o.db = o.ddb = o.b_be = o.b_n = o.db_be = o.db_n = T(0);
+    return o;
+  }
+  const T L = BM<T>::ln(be * zeta);
+  const T u = BM<T>::ex(n * L);
+  const T w = u / (T(1) + u);
+  const T l1u = BM<T>::ln1p(u);
+  const T iz = T(1) / zeta;
+  o.b = BM<T>::ex(-l1u / (T(2) * n));
+  o.db = -T(0.5) * o.b * w * iz;
+  o.ddb = -T(0.5) * (o.db * w + o.b * w * (n * (T(1) - w) - T(1)) * iz) * iz;
+  o.b_be = -o.b * w / (T(2) * be);
+  o.b_n = o.b * (l1u / (T(2) * n * n) - w * L / (T(2) * n));
+  const T w_be = n * w * (T(1) - w) / be;
+  const T w_n = w * (T(1) - w) * L;
+  o.db_be = -T(0.5) * (o.b_be * w + o.b * w_be) * iz;
+  o.db_n = -T(0.5) * (o.b_n * w + o.b * w_n) * iz;
+  return o;
+}
+
+// ------------------------------------------------------------------ accumulation
+// NS == 1: one record; gradients in registers, reduced per warp, per block.
+// Otherwise: per-block shared accumulators with shared-memory atomics.
+template <int NS> struct Acc;
+template <> struct Acc<1> {
+  double v[NP];
+  __device__ __forceinline__ void init(double*) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) v[q] = 0.0;
+  }
+  __device__ __forceinline__ void add(double*, int, int f, double x) { v[f] += x; }
+  __device__ __forceinline__ void flush(double* sh) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      double s = v[q];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if ((threadIdx.x & 31) == 0) atomicAdd(&sh[q], s);
+    }
+  }
+};
+template <> struct Acc<0> {
+  __device__ __forceinline__ void init(double*) {}
+  __device__ __forceinline__ void add(double* sh, int rec, int f, double x) {
+    if (x != 0.0) atomicAdd(&sh[rec * NP + f], x);
+  }
+  __device__ __forceinline__ void flush(double*) {}
+};
+
+template <class T>
+__device__ __forceinline__ T rec_val(const T* raw, int rec, int f) {
+  return raw[rec * NP + f];
+}
+
+// ------------------------------------------------------------------ the kernel
+template <class T, int NS>
+__global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ BwdArgs<T> a) {
+  constexpr int SNS = NS == 1 ? 1 : TERSOFF_MAX_SPECIES;
+  __shared__ T sraw[SNS * SNS * SNS * NP];
+  __shared__ T sfilt[SNS * SNS];
+  __shared__ double sgrad[SNS * SNS * SNS * NP];
+  const fwd::FwdArgs<T>& g = a.g;
+  const int ns = NS == 1 ? 1 : g.ns;
+  const int nrec = ns * ns * ns;
+  for (int q = threadIdx.x; q < nrec * NP; q += BLOCK) {
+    sraw[q] = a.raw[q];
+    sgrad[q] = 0.0;
+  }
+  if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = g.filt2[threadIdx.x];
+  __syncthreads();
+
+  Acc<NS == 1 ? 1 : 0> acc;
+  acc.init(sgrad);
+  const int i = blockIdx.x * BLOCK + threadIdx.x;
+  if (i < g.n) {
+    using P = typename SelfPos<T>::type;
+    const P pi = self_pos<T>(g, i);
+    const int ti = g.types[i];
+    const int c = min(g.cnt[i], g.cap);
+    const double gE = a.gE[a.atom_cell ? a.atom_cell[i] : 0];
+    const bool hasF = a.gF != nullptr;
+    double gfi0 = 0.0, gfi1 = 0.0, gfi2 = 0.0;
+    if (hasF) {
+      gfi0 = a.gF[3 * (size_t)i];
+      gfi1 = a.gF[3 * (size_t)i + 1];
+      gfi2 = a.gF[3 * (size_t)i + 2];
+    }
+    const T hE = T(0.5) * T(gE);
+    // bond j of the list: vector, length, unit vector, w and the rate of r
+    auto bond = [&](int s, T& ux, T& uy, T& uz, T& r, T& wx, T& wy, T& wz, T& rd, int& tj,
+                    bool& inside) {
+      T dx, dy, dz;
+      int j;
+      Bond<T>::vec(g, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, tj);
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      inside = r2 <= sfilt[ti * ns + tj];
+      r = BM<T>::sq(r2);
+      const T ir = T(1) / r;
+      ux = dx * ir;
+      uy = dy * ir;
+      uz = dz * ir;
+      wx = wy = wz = T(0);
+      if (hasF) {
+        wx = T(a.gF[3 * (size_t)j] - gfi0);
+        wy = T(a.gF[3 * (size_t)j + 1] - gfi1);
+        wz = T(a.gF[3 * (size_t)j + 2] - gfi2);
+      }
+      rd = ux * wx + uy * wy + uz * wz;
+    };
+    for (int sj = 0; sj < c; ++sj) {
+      T uxj, uyj, uzj, rj, wxj, wyj, wzj, rdj;
+      int tj;
+      bool inj;
+      bond(sj, uxj, uyj, uzj, rj, wxj, wyj, wzj, rdj, tj, inj);
+      if (!inj) continue;
+      const int p = NS == 1 ? 0 : (ti * ns + tj) * ns + tj;
+      const T Rp = rec_val(sraw, p, TERSOFF_P_R), Dp = rec_val(sraw, p, TERSOFF_P_D_CUT);
+      if (!(rj < Rp + Dp)) continue;
+      // first K loop: zeta_ij and its rate along w
+      T zeta = T(0), zd = T(0);
+      for (int sk = 0; sk < c; ++sk) {
+        if (sk == sj) continue;
+        T uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk;
+        int tk;
+        bool ink;
+        bond(sk, uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk, tk, ink);
+        if (!ink) continue;
+        const int q = NS == 1 ? 0 : (ti * ns + tj) * ns + tk;
+        const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
+        if (!(rk < Rq + Dq)) continue;
+        const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
+        const T csd = ((wxj - uxj * rdj) * uxk + (wyj - uyj * rdj) * uyk + (wzj - uzj * rdj) * uzk) / rj +
+                      ((wxk - uxk * rdk) * uxj + (wyk - uyk * rdk) * uyj + (wzk - uzk * rdk) * uzj) / rk;
+        const Cut<T> fk = cutoff_ad<T>(rk, Rq, Dq);
+        const Ang<T> an = angular_ad<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA),
+                                        rec_val(sraw, q, TERSOFF_P_C),
+                                        rec_val(sraw, q, TERSOFF_P_D),
+                                        rec_val(sraw, q, TERSOFF_P_H));
+        const Expo<T> ex = expo_ad<T>(rj - rk, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
+                                      (int)rec_val(sraw, q, TERSOFF_P_M));
+        zeta += fk.fc * an.g * ex.x;
+        zd += fk.dfc * rdk * an.g * ex.x + fk.fc * an.dg * csd * ex.x +
+              fk.fc * an.g * ex.dx * (rdj - rdk);
+      }
+      // pair level
+      const Cut<T> fj = cutoff_ad<T>(rj, Rp, Dp);
+      const T A = rec_val(sraw, p, TERSOFF_P_A), l1 = rec_val(sraw, p, TERSOFF_P_LAMBDA1);
+      const T B = rec_val(sraw, p, TERSOFF_P_B), l2 = rec_val(sraw, p, TERSOFF_P_LAMBDA2);
+      const T e1 = BM<T>::ex(-l1 * rj), e2 = BM<T>::ex(-l2 * rj);
+      const T Ae1 = A * e1, Be2 = B * e2;
+      const T Pv = fj.fc * Ae1;
+      const T Pd = (fj.dfc - l1 * fj.fc) * Ae1;
+      const T Qv = -fj.fc * Be2;
+      const T Qd = -(fj.dfc - l2 * fj.fc) * Be2;
+      const Bo<T> bo = bond_ad<T>(zeta, rec_val(sraw, p, TERSOFF_P_BETA),
+                                  rec_val(sraw, p, TERSOFF_P_N));
+      // L_j = gE/2 (P + b Q) - 1/2 (P' + b Q') rd_j - 1/2 Q b' zeta_rate
+      const T Pbar = hE;
+      const T Pdbar = -T(0.5) * rdj;
+      const T Qbar = hE * bo.b - T(0.5) * bo.db * zd;
+      const T Qdbar = -T(0.5) * bo.b * rdj;
+      const T bbar = hE * Qv - T(0.5) * Qd * rdj;
+      const T dbbar = -T(0.5) * Qv * zd;
+      acc.add(sgrad, p, TERSOFF_P_A, to_f64(Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
+      acc.add(sgrad, p, TERSOFF_P_LAMBDA1,
+              to_f64(Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
+      acc.add(sgrad, p, TERSOFF_P_B, to_f64(Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
+      acc.add(sgrad, p, TERSOFF_P_LAMBDA2,
+              to_f64(Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
+      acc.add(sgrad, p, TERSOFF_P_R,
+              to_f64((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
+                     (Qbar * fj.fc_R + Qdbar * (fj.dfc_R - l2 * fj.fc_R)) * Be2));
+      acc.add(sgrad, p, TERSOFF_P_D_CUT,
+              to_f64((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
+                     (Qbar * fj.fc_D + Qdbar * (fj.dfc_D - l2 * fj.fc_D)) * Be2));
+      acc.add(sgrad, p, TERSOFF_P_BETA, to_f64(bbar * bo.b_be + dbbar * bo.db_be));
+      acc.add(sgrad, p, TERSOFF_P_N, to_f64(bbar * bo.b_n + dbbar * bo.db_n));
+      const T zbar = bbar * bo.db + dbbar * bo.ddb;
+      const T zdbar = -T(0.5) * Qv * bo.db;
+      if (zbar == T(0) && zdbar == T(0)) continue;
+      // second K loop: recompute each three-body term, adjoints of its parameters
+      for (int sk = 0; sk < c; ++sk) {
+        if (sk == sj) continue;
+        T uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk;
+        int tk;
+        bool ink;
+        bond(sk, uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk, tk, ink);
+        if (!ink) continue;
+        const int q = NS == 1 ? 0 : (ti * ns + tj) * ns + tk;
+        const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
+        if (!(rk < Rq + Dq)) continue;
+        const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
+        const T csd = ((wxj - uxj * rdj) * uxk + (wyj - uyj * rdj) * uyk + (wzj - uzj * rdj) * uzk) / rj +
+                      ((wxk - uxk * rdk) * uxj + (wyk - uyk * rdk) * uyj + (wzk - uzk * rdk) * uzj) / rk;
+        const Cut<T> fk = cutoff_ad<T>(rk, Rq, Dq);
+        const Ang<T> an = angular_ad<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA),
+                                        rec_val(sraw, q, TERSOFF_P_C),
+                                        rec_val(sraw, q, TERSOFF_P_D),
+                                        rec_val(sraw, q, TERSOFF_P_H));
+        const T dl = rj - rk, dld = rdj - rdk;
+        const Expo<T> ex = expo_ad<T>(dl, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
+                                      (int)rec_val(sraw, q, TERSOFF_P_M));
+        // T = F3 G X ; T_rate = F3' rd_k G X + F3 G' cs_rate X + F3 G X' dl_rate
+        const T F3bar = zbar * an.g * ex.x + zdbar * (an.dg * csd * ex.x + an.g * ex.dx * dld);
+        const T F3dbar = zdbar * rdk * an.g * ex.x;
+        const T Gbar = zbar * fk.fc * ex.x + zdbar * (fk.dfc * rdk * ex.x + fk.fc * ex.dx * dld);
+        const T Gdbar = zdbar * fk.fc * csd * ex.x;
+        const T Xbar = zbar * fk.fc * an.g + zdbar * (fk.dfc * rdk * an.g + fk.fc * an.dg * csd);
+        const T Xdbar = zdbar * fk.fc * an.g * dld;
+        acc.add(sgrad, q, TERSOFF_P_R, to_f64(F3bar * fk.fc_R + F3dbar * fk.dfc_R));
+        acc.add(sgrad, q, TERSOFF_P_D_CUT, to_f64(F3bar * fk.fc_D + F3dbar * fk.dfc_D));
+        acc.add(sgrad, q, TERSOFF_P_GAMMA, to_f64(Gbar * an.g_ga + Gdbar * an.dg_ga));
+        acc.add(sgrad, q, TERSOFF_P_C, to_f64(Gbar * an.g_c + Gdbar * an.dg_c));
+        acc.add(sgrad, q, TERSOFF_P_D, to_f64(Gbar * an.g_d + Gdbar * an.dg_d));
+        acc.add(sgrad, q, TERSOFF_P_H, to_f64(Gbar * an.g_h + Gdbar * an.dg_h));
+        acc.add(sgrad, q, TERSOFF_P_LAMBDA3, to_f64(Xbar * ex.x_l + Xdbar * ex.dx_l));
+      }
+    }
+  }
+  acc.flush(sgrad);
+  __syncthreads();
+  for (int q = threadIdx.x; q < nrec * NP; q += BLOCK)
+    if (sgrad[q] != 0.0) atomicAdd(&a.grad[q], sgrad[q]);
+}
+
+// grad_x = -gE F (in place: f holds F on entry)
+__global__ void k_scale_forces(double* __restrict__ f, const double* __restrict__ gE, int n3) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n3) f[t] = -gE[0] * f[t];
+}
+
+template <class T> const T* filt_ptr(Ctx* c);
+template <> inline const float* filt_ptr<float>(Ctx* c) { return c->d_filt32; }
+template <> inline const double* filt_ptr<double>(Ctx* c) { return c->d_filt64; }
+
+template <class T>
+int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* grad,
+             cudaStream_t s) {
+  BwdArgs<T> a;
+  fwd::FwdArgs<T>& g = a.g;
+  memset(&g, 0, sizeof(g));
+  g.n = c->n;
+  g.cap = c->cap;
+  g.ns = c->ns;
+  g.nbr = c->d_nbr;
+  g.cnt = c->d_cnt;
+  g.types = c->d_types;
+  g.pos32 = c->d_pos32;
+  g.posq = c->d_posq;
+  g.pos64 = c->d_pos64;
+  g.filt2 = filt_ptr<T>(c);
+  const double scale = ldexp(1.0, c->grid.fix_shift);
+  for (int q = 0; q < 3; ++q) {
+    g.h[q] = (T)c->grid.h[q];
+    g.hq[q] = (int)llrint(c->grid.h[q] * scale);
+  }
+  g.qinv = ldexpf(1.0f, -c->grid.fix_shift);
+  a.raw = raw;
+  a.gE = gE;
+  a.atom_cell = nullptr;
+  a.gF = gF;
+  a.grad = grad;
+  const int grid = (c->n + BLOCK - 1) / BLOCK;
+  if (grid > 0) {
+    if (c->ns == 1)
+      k_tersoff_bwd<T, 1><<<grid, BLOCK, 0, s>>>(a);
+    else
+      k_tersoff_bwd<T, 0><<<grid, BLOCK, 0, s>>>(a);
+    c->launches++;
+  }
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+}  // namespace bwd
+
+int launch_backward(Ctx* c, const double* gE, const double* gF, double* grad, cudaStream_t s) {
+  if (c->precision == TERSOFF_MIXED) return bwd::launch_t<float>(c, c->d_raw32, gE, gF, grad, s);
+  return bwd::launch_t<double>(c, c->d_raw64, gE, gF, grad, s);
+}
+
+int launch_scale_forces(Ctx* c, double* f, const double* gE, cudaStream_t s) {
+  const int n3 = 3 * c->n;
+  if (n3 == 0) return TERSOFF_OK;
+  bwd::k_scale_forces<<<(n3 + 255) / 256, 256, 0, s>>>(f, gE, n3);
+  c->launches++;
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+}  // namespace tgb
