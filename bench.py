@@ -36,6 +36,8 @@ UNIT = "atom-steps/s"
 MD_PER_STEP = 10
 DT = 0.001
 R_LIST = 4.0
+RC_SI = 3.0  # largest f_C outer cutoff of the Tersoff 1989 Si / C tables (R + D)
+NPARAM_TABLE_SI = 14
 PEAK_FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 PEAK_FP64_TFLOPS_NOMINAL = 1.25
 
@@ -68,6 +70,13 @@ def force_traffic():
 def workload_name():
     return ("si-diamond-40x40x40-512000-atoms-1000K-dt1fs-rlist4.0-rebuild10-"
             "10-md-steps-per-step")
+
+
+def base_config(n, world):
+    return {"workload": workload_name(), "atoms_per_gpu": n, "md_steps_per_step": MD_PER_STEP,
+            "dt_ps": DT, "neighbor_rebuild_every": MD_PER_STEP, "r_list_A": R_LIST,
+            "l2": "flushed before each timed step (512 MiB write, outside the timed events)",
+            "parallelism": f"replicas x{world}"}
 
 
 def dist_info():
@@ -364,18 +373,9 @@ def run_ours(args):
         "dtype": "f32",
         "accumulate_dtype": "f64",
         "data": "synthetic",
-        "config": {
-            "workload": workload_name(),
-            "atoms_per_gpu": n,
-            "md_steps_per_step": MD_PER_STEP,
-            "dt_ps": DT,
-            "neighbor_rebuild_every": MD_PER_STEP,
-            "r_list_A": R_LIST,
-            "l2": "flushed before each timed step (512 MiB write, outside the timed events)",
-            "parallelism": f"replicas x{world}",
-            "scatter": best,
-            "scatter_trial_ms_per_step": {k: v / max(3, args.steps // 5) for k, v in trial.items()},
-        },
+        "config": dict(base_config(n, world), scatter=best,
+                       scatter_trial_ms_per_step={k: v / max(3, args.steps // 5)
+                                                  for k, v in trial.items()}),
         "force_error": {
             "reference": "FP64 GPU path (itself within 1e-10 of the FP64 CPU oracle in tests)",
             "force_rms_rel": force_rms_rel,
@@ -432,6 +432,12 @@ def run_ours(args):
         "clocks": clocks,
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
     }
+    if rank == 0 and not args.no_extra:
+        out["backward"] = time_backward(T, ctxm, xdm, ctx64, xd64, flush)
+    ctxm.close()
+    ctx64.close()
+    if rank == 0 and not args.no_extra:
+        out["single_evaluations"] = single_evaluations(T, W, dev, flush, cpu=not args.no_cpu_baseline)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x, v, t, box, names, table)
     if rank == 0:
@@ -439,6 +445,109 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _event_time(fn, reps, flush, stream):
+    """Mean device time (ms) of fn() over reps calls, L2 flushed before each."""
+    import torch
+    tot = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    return tot / reps
+
+
+def time_backward(T, ctxm, xdm, ctx64, xd64, flush, reps=10):
+    """tersoff_backward (parameter VJP of energy and forces) on the MD system,
+    both paths, against one force evaluation of the same path."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {"what": "tersoff_backward: d/dtheta [gE E + sum gF . F] for all table entries, "
+                   "random gF; forward = tersoff_compute (energy, forces, virial)",
+           "atoms": int(xdm.shape[0])}
+    for name, ctx, xd in (("mixed", ctxm, xdm), ("fp64", ctx64, xd64)):
+        n = xd.shape[0]
+        rng = np.random.Generator(np.random.Philox(7))
+        gE = torch.tensor([1.0], dtype=torch.float64, device=xd.device)
+        gF = torch.tensor(rng.normal(0.0, 1.0, size=(n, 3)), dtype=torch.float64,
+                          device=xd.device)
+        grad = torch.empty(NPARAM_TABLE_SI, dtype=torch.float64, device=xd.device)
+        e = torch.empty(1, dtype=torch.float64, device=xd.device)
+        f = torch.empty_like(xd)
+        w = torch.empty(6, dtype=torch.float64, device=xd.device)
+        for _ in range(2):
+            ctx.backward(xd, gE, gF, None, grad)
+            ctx.compute(xd, e, f, w)
+        torch.cuda.synchronize()
+        bw = _event_time(lambda: ctx.backward(xd, gE, gF, None, grad), reps, flush, stream)
+        fw = _event_time(lambda: ctx.compute(xd, e, f, w), reps, flush, stream)
+        out[name] = {"backward_ms": bw, "forward_ms": fw, "backward_over_forward": bw / fw,
+                     "backward_atoms_per_s": n / (bw * 1e-3)}
+    return out
+
+
+def single_evaluations(T, W, dev, flush, cpu=True, reps=20):
+    """The single-evaluation workloads: Si 8x8x8 cells (4,096 atoms) in FP64, and
+    SiC zincblende 64x64x64 cells (2,097,152 atoms) in the mixed path with its
+    error against the FP64 oracle (host cores)."""
+    import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {}
+    cases = [("si-diamond-8x8x8-4096-atoms-fp64", W.config_si_small(), T.FP64, RC_SI + 1.0),
+             ("sic-zincblende-64x64x64-2097152-atoms-mixed", W.config_sic(), T.MIXED, RC_SI + 1.0)]
+    for name, (x, t, box, names), prec, r_list in cases:
+        table = T.mix_tersoff89(*W.element_records(names))
+        ctx = T.Context(prec)
+        ctx.params(table)
+        xd = torch.tensor(x, dtype=torch.float64, device=dev)
+        td = torch.tensor(t, dtype=torch.int32, device=dev)
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        f = torch.empty_like(xd)
+        w = torch.empty(6, dtype=torch.float64, device=dev)
+        ctx.neighbor_build(xd, td, box, r_list)
+        ctx.compute(xd, e, f, w)
+        torch.cuda.synchronize()
+        build_ms = _event_time(lambda: ctx.neighbor_build(xd, td, box, r_list), 5, flush, stream)
+        eval_ms = _event_time(lambda: ctx.compute(xd, e, f, w), reps, flush, stream)
+        n = x.shape[0]
+        row = {"atoms": n, "precision": "fp64" if prec == T.FP64 else "mixed",
+               "r_list_A": r_list, "eval_ms": eval_ms, "atom_evals_per_s": n / (eval_ms * 1e-3),
+               "neighbor_build_ms": build_ms}
+        if prec == T.MIXED:
+            ctx.set_precision(T.FP64)
+            ctx.compute(xd, e, f, w)
+            ctx.set_precision(T.MIXED)
+            f64 = f.cpu().numpy()
+            ctx.compute(xd, e, f, w)
+            fm = f.cpu().numpy()
+            row["force_rms_rel_vs_fp64_gpu"] = float(np.sqrt(((fm - f64) ** 2).mean()) /
+                                                     np.sqrt((f64 ** 2).mean()))
+        if cpu:
+            import oracle
+            cores = os.cpu_count() or 1
+            t0 = time.perf_counter()
+            nl = oracle.neighbors(x, box, RC_SI)
+            er, fr, wr = oracle.compute(x, t, box, table, nl, nthreads=cores)
+            row["oracle_seconds"] = time.perf_counter() - t0
+            ctx.compute(xd, e, f, w)
+            torch.cuda.synchronize()
+            fg = f.cpu().numpy()
+            row["vs_fp64_oracle"] = {
+                "energy_rel": abs(e.item() - er) / abs(er),
+                "force_rms_rel": float(np.sqrt(((fg - fr) ** 2).mean()) / np.sqrt((fr ** 2).mean())),
+                "virial_max_rel": float(np.abs(w.cpu().numpy() - wr).max() / np.abs(wr).max())}
+        ctx.close()
+        del xd, td, f
+        out[name] = row
+    return out
 
 
 def cpu_baseline(x, v, t, box, names, table, nsteps=20):
@@ -464,13 +573,17 @@ def cpu_baseline(x, v, t, box, names, table, nsteps=20):
 
 
 def run_reference(args):
+    """The oracle on the host cores (there is no reference implementation to
+    install): each step is oracle velocity-Verlet MD of MD_PER_STEP steps on a
+    64,000-atom sample of the benchmark system (Si diamond 20x20x20 cells, same
+    recipe), including the oracle's own list build and first force evaluation,
+    so that the default run ends within minutes."""
     world, rank, local = dist_info()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
     import oracle
     import workloads as W
-    x, v, t, box, names = W.config_si_md()
+    x, v, t, box, names = W.config_si_md(ncell=20)
     table = oracle.mix_tersoff89(*W.element_records(names))
     mass = [W.MASS_AMU[s] for s in names]
     cores = os.cpu_count() or 1
@@ -486,6 +599,9 @@ def run_reference(args):
     total = sum(times)
     units = x.shape[0] * MD_PER_STEP * args.steps
     value = units / total
+    sample = (f"each step: oracle md_run of {MD_PER_STEP} VV steps on a {x.shape[0]}-atom sample "
+              f"(Si diamond 20x20x20 cells, same recipe) including its list build and first "
+              f"force evaluation, {cores} OpenMP threads")
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -500,12 +616,9 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_name(), "atoms_per_gpu": x.shape[0],
-                   "md_steps_per_step": MD_PER_STEP, "parallelism": "host cores"},
+        "config": base_config(512000, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"each step: oracle md_run of {MD_PER_STEP} VV steps on the "
-                                   f"full system including its list build and first force "
-                                   f"evaluation, {cores} OpenMP threads"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -544,6 +657,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the single-evaluation workloads and the backward timing")
     ap.add_argument("--only", choices=["force", "md"], default=None,
                     help="profiling case: K force evaluations (or K MD rebuild periods) of "
                          "the benchmark workload, nothing printed")
