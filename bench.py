@@ -629,20 +629,24 @@ def run_profile_case(args):
     import torch
     import workloads as W
     import paper_1607_02904_gb300 as T
-    x, v, t, box, names = W.config_si_md()
+    if args.only == "force-sic":
+        x, t, box, names = W.config_sic()
+        v = None
+    else:
+        x, v, t, box, names = W.config_si_md()
     table = T.mix_tersoff89(*W.element_records(names))
     mass = [W.MASS_AMU[s] for s in names]
     ctx = T.Context(T.MIXED if args.precision == "mixed" else T.FP64)
     ctx.set_scatter(T.SCATTER_ATOMIC if args.scatter == "atomic" else T.SCATTER_GATHER)
     ctx.params(table)
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
-    vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+    vd = torch.tensor(v, dtype=torch.float64, device="cuda") if v is not None else None
     td = torch.tensor(t, dtype=torch.int32, device="cuda")
     ctx.neighbor_build(xd, td, box, R_LIST)
     fd = torch.zeros_like(xd)
     e = torch.zeros(1, dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
-        if args.only == "force":
+        if args.only in ("force", "force-sic"):
             ctx.compute(xd, e, fd)
         else:
             ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
@@ -659,9 +663,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the single-evaluation workloads and the backward timing")
-    ap.add_argument("--only", choices=["force", "md"], default=None,
+    ap.add_argument("--only", choices=["force", "md", "force-sic"], default=None,
                     help="profiling case: K force evaluations (or K MD rebuild periods) of "
-                         "the benchmark workload, nothing printed")
+                         "the benchmark workload, or K force evaluations of the 2.1M-atom "
+                         "SiC workload; nothing printed")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--scatter", choices=["gather", "atomic"], default="gather")
     args = ap.parse_args()

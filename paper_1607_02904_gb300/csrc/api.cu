@@ -213,7 +213,6 @@ int build_list(Ctx* c, const double* x, cudaStream_t s) {
     c->max_cnt = c->h_flags[FLAG_OVERFLOW];
     c->max_short = c->h_flags[FLAG_SHORT_MAX];
     for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[flag_bucket(b)];
-    c->nwide = c->h_flags[FLAG_WIDE];
     if (c->max_cnt <= c->cap) {
       c->have_list = true;
       c->steps_since_build = 0;
@@ -769,7 +768,6 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     c->max_cnt = c->h_flags[tgb::FLAG_OVERFLOW];
     c->max_short = c->h_flags[tgb::FLAG_SHORT_MAX];
     for (int b = 0; b < 3; ++b) c->nbucket[b] = c->h_flags[tgb::flag_bucket(b)];
-    c->nwide = c->h_flags[tgb::FLAG_WIDE];
     return TERSOFF_OK;
   }
   // a build inside the sequence overflowed (or met non-finite positions):

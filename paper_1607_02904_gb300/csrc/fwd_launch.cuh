@@ -29,18 +29,18 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
   c->launches++;
 }
 
-// Launches per short-list size bucket (built with the list). Bucket 0 (at
-// most 4 stored entries) runs with register capacity 4. Bucket 1 (5 to 8) runs
-// with capacity 8, on a side stream next to the main launch, when many atoms
-// (over 5%) have more than 4 neighbours inside the filter radii themselves
-// (e.g. SiC). Otherwise its extra entries lie mostly in the list margin (e.g.
-// hot Si, where second neighbours drift into the margin) and it is appended to
-// the capacity-4 launch, whose atoms keep the entries inside the cutoffs at
-// each step. Bucket 2 and atoms with too many entries take the general path.
+// Launches per bucket (built with the list: the number of list entries inside
+// the filter radii themselves, without the margin). Bucket 0 (at most 4) runs
+// with register capacity 4. Bucket 1 (5 to 8) runs with capacity 8, on a side
+// stream next to the main launch, when it holds over 5% of the atoms (e.g.
+// SiC, where Si-Si second neighbours straddle the cutoff); otherwise it is
+// appended to the capacity-4 launch. Every launch masks the stored short list
+// (radius plus margin) by the cutoffs at each step; atoms with more entries
+// inside than the capacity, and bucket 2, take the general path.
 template <class T, int NS>
 void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
   const int full = (c->n + BLOCK - 1) / BLOCK;
-  const bool split1 = c->nbucket[1] > 0 && (long long)c->nwide * 20 > (long long)c->n;
+  const bool split1 = (long long)c->nbucket[1] * 20 > (long long)c->n;
   const bool fork = split1 && c->side != nullptr;
   cudaStream_t s2 = s;
   if (fork) {

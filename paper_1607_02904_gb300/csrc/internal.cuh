@@ -127,7 +127,7 @@ struct Ctx {
   int4* d_qref = nullptr;         // n: fixed-point offsets at the last build
   uint32_t* d_short = nullptr;    // zs_cap * n, slot-major short list
   int* d_zcnt = nullptr;          // n
-  int* d_bucket = nullptr;        // 3 x n: atom indices per short-list size bucket
+  int* d_bucket = nullptr;        // 3 x n: atom indices per bucket (entries inside the cutoffs)
   uint8_t* d_rev = nullptr;       // zs_cap x n: slot of j in the short list of its p-th neighbour
   void* d_contrib = nullptr;      // zs_cap x n force contributions (float4 or dpos4)
   void* d_own = nullptr;          // n: force of each atom's own terms on itself
@@ -136,7 +136,6 @@ struct Ctx {
   int contrib_prec = -1;
   bool scatter_atomic = false;    // forces by FP64 atomics instead of slots + gather
   int nbucket[3] = {0, 0, 0};     // bucket sizes at the last build
-  int nwide = 0;                  // FLAG_WIDE at the last build
   int zs_cap = 0;
   double margin = 0.0;            // short-list radius margin beyond the cutoffs
   double* d_trow = nullptr;       // MD thermo accumulation rows (ACC_LEN doubles per step)
@@ -208,10 +207,9 @@ enum : int {
   FLAG_OVERFLOW = 0 * FLAG_STRIDE,      // largest neighbour count of the build
   FLAG_SHORT_MAX = 1 * FLAG_STRIDE,     // largest short-list count of the build
   FLAG_DMAX = 2 * FLAG_STRIDE,          // running max squared displacement since the build (float bits)
-  FLAG_BUCKET = 3 * FLAG_STRIDE,        // 3 words: atoms per short-list size bucket (<= 4, <= 8, more)
+  FLAG_BUCKET = 3 * FLAG_STRIDE,        // 3 words: atoms per bucket (<= 4, <= 8, more list
+                                        // entries inside the filter radii)
   FLAG_REV_MISS = 6 * FLAG_STRIDE,      // a short-list entry has no reverse entry
-  FLAG_WIDE = 7 * FLAG_STRIDE,          // atoms with more than 4 list entries inside the
-                                        // filter radii themselves (no margin)
   FLAG_BUILD_WORDS = 8 * FLAG_STRIDE,
   FLAG_NONFINITE = 8 * FLAG_STRIDE,     // non-finite position seen by a build
   FLAG_FALLBACK = 9 * FLAG_STRIDE,      // atoms handled by the general path

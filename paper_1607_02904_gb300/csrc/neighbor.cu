@@ -268,11 +268,10 @@ __global__ void __launch_bounds__(128) k_neigh(
     zcnt[i] = z;
   }
   // block-level aggregation: one atomic per block and word
-  __shared__ int s_max[2], s_ovf, s_wide, s_cnt[3], s_base[3], s_wcnt[4][3];
+  __shared__ int s_max[2], s_ovf, s_cnt[3], s_base[3], s_wcnt[4][3];
   if (threadIdx.x == 0) {
     s_max[0] = s_max[1] = 0;
     s_ovf = 0;
-    s_wide = 0;
     s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
   }
   __syncthreads();
@@ -283,16 +282,16 @@ __global__ void __launch_bounds__(128) k_neigh(
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const bool ovf = __any_sync(0xffffffffu, active && count > cap);
-  const int wide = __popc(__ballot_sync(0xffffffffu, active && zw > 4));
-  // bucket by short-list size (<= 4, <= 8, more)
-  const int b = z <= 4 ? 0 : (z <= 8 ? 1 : 2);
+  // bucket by the entries inside the filter radii themselves (<= 4, <= 8,
+  // more): the force launch of a bucket keeps that many in registers and masks
+  // the stored short list (radius plus margin) by the cutoffs at each step
+  const int b = zw <= 4 ? 0 : (zw <= 8 ? 1 : 2);
   unsigned msk[3];
   for (int q = 0; q < 3; ++q) msk[q] = __ballot_sync(0xffffffffu, active && b == q);
   if (lane == 0) {
     atomicMax(&s_max[0], mc);
     atomicMax(&s_max[1], mz);
     if (ovf) s_ovf = 1;
-    if (wide) atomicAdd(&s_wide, wide);
     for (int q = 0; q < 3; ++q) s_wcnt[wid][q] = __popc(msk[q]);
   }
   __syncthreads();
@@ -300,7 +299,6 @@ __global__ void __launch_bounds__(128) k_neigh(
     if (s_max[0] > 0) atomicMax(&flags[FLAG_OVERFLOW], s_max[0]);
     if (s_max[1] > 0) atomicMax(&flags[FLAG_SHORT_MAX], s_max[1]);
     if (s_ovf) atomicOr(&flags[FLAG_OVF_ANY], 1);
-    if (s_wide) atomicAdd(&flags[FLAG_WIDE], s_wide);
     for (int q = 0; q < 3; ++q) {
       int tot = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_wcnt[w][q];

@@ -354,9 +354,13 @@ __device__ __forceinline__ int rec_off(int ns, int ti, int tj, int tk) {
 
 // slots: forces go to the per-slot contributions of the list (the short list),
 // otherwise to the fallback buffer through FP64 atomics.
+// use_mask: bit s of mask marks the entries s < 64 inside the filter radius
+// (the others cannot be in any term and are skipped before their bond vector
+// is formed).
 template <class T, int NS, bool LAM3>
 __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec, int i, int ti,
-                                          const uint32_t* list, int c, bool slots, T& ei,
+                                          const uint32_t* list, int c, bool slots,
+                                          bool use_mask, unsigned long long mask, T& ei,
                                           T* w) {
   using P = typename SelfPos<T>::type;
   const int ns = NS > 0 ? NS : a.ns;
@@ -365,6 +369,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
   if (slots)
     for (int q = 0; q < c; ++q) store_slot<T>(a, a.contrib, (size_t)q * a.n + i, T(0), T(0), T(0));
   for (int sj = 0; sj < c; ++sj) {
+    if (use_mask && !((mask >> sj) & 1ull)) continue;
     T dxj, dyj, dzj;
     int j, tj;
     Bond<T>::vec(a, pi, list[(size_t)sj * a.n + i], dxj, dyj, dzj, j, tj);
@@ -376,7 +381,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
     const T uxj = dxj * rinj, uyj = dyj * rinj, uzj = dzj * rinj;
     T zeta = 0;
     for (int sk = 0; sk < c; ++sk) {
-      if (sk == sj) continue;
+      if (sk == sj || (use_mask && !((mask >> sk) & 1ull))) continue;
       T dxk, dyk, dzk;
       int k, tk;
       Bond<T>::vec(a, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
@@ -394,7 +399,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
     ei += V;
     T Fjx = -dVdr * uxj, Fjy = -dVdr * uyj, Fjz = -dVdr * uzj;
     for (int sk = 0; sk < c; ++sk) {
-      if (sk == sj) continue;
+      if (sk == sj || (use_mask && !((mask >> sk) & 1ull))) continue;
       T dxk, dyk, dzk;
       int k, tk;
       Bond<T>::vec(a, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
@@ -560,6 +565,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
     int c;
     bool general;
     bool filtered = false;  // the register slots come from a cutoff mask over list
+    bool have_mask = false; // mask covers every entry of list (at most 64)
     int z_list = 0;         // stored short-list length (slots mode bookkeeping)
     if (use_short) {
       z_list = a.zcnt[i];
@@ -594,6 +600,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
           }
         z = __popcll(mask);
         general = !fits || z > ZC;
+        have_mask = fits;
       }
     } else {
       // filter the skin list into a bit mask (Sec. IV-D)
@@ -620,13 +627,14 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
       }
       z = __popcll(mask);
       general = !fits || z > ZC;
+      have_mask = fits;
     }
     if (!slots && !a.atomic_mode) clear_slots<T>(a, i);
     if (general) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
       if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
-      general_atom<T, NS, LAM3>(a, srec, i, ti, list, c, slots && list == a.shortl, eatom_i,
-                                w);
+      general_atom<T, NS, LAM3>(a, srec, i, ti, list, c, slots && list == a.shortl, have_mask,
+                                mask, eatom_i, w);
     } else {
       using P = typename SelfPos<T>::type;
       const P pi = self_pos<T>(a, i);
