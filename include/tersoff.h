@@ -183,12 +183,20 @@ int tersoff_compute_noalloc(tersoff_ctx* ctx, const double* x, int n, double* en
 int tersoff_compute_peratom(tersoff_ctx* ctx, const double* x, int n, double* eatom,
                             void* stream);
 
+/* rebuild_every value of the MD calls: rebuild the neighbour list when some
+ * atom has moved more than half the skin (r_list minus the largest cutoff)
+ * since the last build, the validity limit of the skin list (Sec. III). The
+ * check runs on the device after every step; inside a CUDA graph the rebuild
+ * is a conditional node, so no host synchronisation is needed. */
+#define TERSOFF_REBUILD_ON_SKIN (-1)
+
 /* Velocity-Verlet NVE steps in metal units (x in A, v in A/ps, dt in ps,
  * forces in eV/A). Requires a prior tersoff_neighbor_build on these atoms and
  * forces f holding F(x) (for example from tersoff_compute). Each step:
  *   v += dt/2 f/m;  x += dt v;  rebuild the list when the number of steps
- *   since the last build reaches rebuild_every (0 = never);  f = F(x);
- *   v += dt/2 f/m.
+ *   since the last build reaches rebuild_every (0 = never; or, with
+ *   TERSOFF_REBUILD_ON_SKIN, when an atom has moved more than half the skin);
+ *   f = F(x);  v += dt/2 f/m.
  * mass: HOST array of n_species masses (amu). x, v, f (device, N x 3) are
  * updated in place; positions are not wrapped into the box. thermo (device,
  * nsteps x 3, may be NULL) receives potential, kinetic and total energy (eV)
@@ -205,6 +213,10 @@ int tersoff_md_step(tersoff_ctx* ctx, double* x, double* v, double* f, int n,
 int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int n,
                          const double* mass, double dt, int nsteps, int rebuild_every,
                          double* thermo, void* stream);
+
+/* Number of neighbour rebuilds during the last tersoff_md_step call on this
+ * context (host output). */
+int tersoff_md_rebuilds(const tersoff_ctx* ctx, int* count);
 
 /* Force scatter. TERSOFF_SCATTER_GATHER (default): every atom stores the
  * forces its own terms put on each short-list neighbour in per-neighbour

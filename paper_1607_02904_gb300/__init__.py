@@ -15,6 +15,7 @@ from ._lib import (  # noqa: F401
     SCATTER_ATOMIC,
     NPARAM,
     NOALLOC_MAX_ATOMS,
+    REBUILD_ON_SKIN,
     load,
     library_path,
     declared_symbols,

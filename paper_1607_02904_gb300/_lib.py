@@ -26,6 +26,7 @@ SCATTER_GATHER = 0
 SCATTER_ATOMIC = 1
 NPARAM = 14
 NOALLOC_MAX_ATOMS = 65536
+REBUILD_ON_SKIN = -1
 
 _lib = None
 
@@ -49,6 +50,7 @@ _SIG = {
     "tersoff_md_step": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_md_step_host": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_launch_count": ([_P, _P], _I),
+    "tersoff_md_rebuilds": ([_P, _P], _I),
     "tersoff_set_timing": ([_P, _I], _I),
     "tersoff_set_graphs": ([_P, _I], _I),
     "tersoff_set_scatter": ([_P, _I], _I),
@@ -223,6 +225,12 @@ class Context:
         cnt = ctypes.c_longlong()
         self._check(self.lib.tersoff_timing(self.h, int(kind), ctypes.byref(ms), ctypes.byref(cnt)))
         return ms.value, cnt.value
+
+    def md_rebuilds(self):
+        """Neighbour rebuilds during the last md_step call."""
+        c = _I()
+        self._check(self.lib.tersoff_md_rebuilds(self.h, ctypes.byref(c)))
+        return c.value
 
     def launch_count(self):
         c = ctypes.c_longlong()

@@ -275,6 +275,8 @@ int tersoff_create(tersoff_ctx** out, int precision) {
   cudaMemset(c->d_acc, 0, sizeof(double) * tgb::ACC_LEN);
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     c->cap_stream = nullptr;
+  if (cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess)
+    c->body_stream = nullptr;
   int prio_lo = 0, prio_hi = 0;
   cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
   if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
@@ -306,6 +308,7 @@ int tersoff_destroy(tersoff_ctx* p) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->body_stream) cudaStreamDestroy(c->body_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   delete p;
@@ -611,15 +614,67 @@ int tersoff_compute_noalloc(tersoff_ctx* p, const double* x, int n, double* ener
   return tgb::launch_noalloc_out(c, scr, n, forces, energy, virial, s);
 }
 
+// Rebuild threshold of the displacement trigger: (skin / 2)^2, the skin being
+// the list radius beyond the largest cutoff.
+static float skin_lim2(const Ctx* c) {
+  const double skin = c->r_list - c->rmax_cut;
+  return (float)(0.25 * (skin > 0.0 ? skin * skin : 0.0));
+}
+
+// Adds to the graph being captured on cs a neighbour rebuild that runs only if
+// the largest displacement since the last build exceeds half the skin: a
+// one-thread kernel sets the condition of an IF node whose body (captured on
+// the context's body stream) holds the build. Returns the body's kernel count
+// in *body_kernels.
+static int enqueue_conditional_build(Ctx* c, const double* x, cudaStream_t cs,
+                                     long long* body_kernels) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  TGB_CUDA(c, cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive || !g || !c->body_stream)
+    return tgb::fail(c, TERSOFF_E_STATE, "conditional rebuild outside a graph capture");
+  cudaGraphConditionalHandle h;
+  TGB_CUDA(c, cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+  int st = tgb::launch_decide_rebuild(c, skin_lim2(c), h, cs);
+  if (st) return st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  TGB_CUDA(c, cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
+  // the node parameters are a C struct (zeroed storage, as the API requires)
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams& prm = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h;
+  prm.conditional.type = cudaGraphCondTypeIf;
+  prm.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  TGB_CUDA(c, cudaGraphAddNode(&node, g, deps, nullptr, nd, &prm));
+  cudaGraph_t body = prm.conditional.phGraph_out[0];
+  TGB_CUDA(c, cudaStreamBeginCaptureToGraph(c->body_stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+  const long long l0 = c->launches;
+  st = tgb::build_list_async(c, x, c->body_stream);
+  *body_kernels = c->launches - l0;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->body_stream, &captured);
+  if (st) return st;
+  TGB_CUDA(c, ce);
+  TGB_CUDA(c, cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                                  cudaStreamSetCaptureDependencies));
+  return TERSOFF_OK;
+}
+
 // Enqueues nsteps velocity-Verlet steps. sync_builds: rebuild with a host
 // check (eager); otherwise without host synchronisation (graph capture).
 static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
                       int nsteps, int rebuild_every, double* rows, double* thermo,
                       bool sync_builds, cudaStream_t s) {
   int st = TERSOFF_OK;
+  const bool on_skin = rebuild_every == TERSOFF_REBUILD_ON_SKIN;
   if (rows) TGB_CUDA(c, cudaMemsetAsync(rows, 0, sizeof(double) * tgb::ACC_LEN * (size_t)nsteps, s));
   for (int step = 0; step < nsteps; ++step) {
-    c->steps_since_build++;
+    if (!on_skin) c->steps_since_build++;
     const bool rebuild = rebuild_every > 0 && c->steps_since_build >= rebuild_every;
     // opening half kick (merged with the previous step's closing one), drift
     double* ke_row =
@@ -638,6 +693,24 @@ static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
       }
       if (st) return st;
       c->steps_since_build = 0;
+      c->last_rebuilds++;
+    } else if (on_skin) {
+      tgb::TimedRegion tr(c, 1, s);
+      if (sync_builds) {
+        // host check of the displacement tracked by the step just enqueued
+        if ((st = tgb::read_flags(c, s))) return st;
+        float d2;
+        std::memcpy(&d2, &c->h_flags[tgb::FLAG_DMAX], sizeof(float));
+        if (d2 > skin_lim2(c)) {
+          if ((st = tgb::build_list(c, x, s))) return st;
+          c->last_rebuilds++;
+        }
+      } else {
+        long long bk = 0;
+        if ((st = enqueue_conditional_build(c, x, s, &bk))) return st;
+        c->graph.body_kernels = bk;
+        c->launches -= bk;  // counted per rebuild that runs
+      }
     }
     if ((st = tgb::launch_forward(c, c->d_extra, acc, nullptr, s))) return st;
   }
@@ -656,9 +729,12 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   int st = tgb::check_ctx(c);
   if (st) return st;
   if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
-  if (n != c->n || (n > 0 && (!x || !v || !f)) || !mass || nsteps < 0 || rebuild_every < 0 ||
-      !(dt > 0.0) || !std::isfinite(dt))
+  if (n != c->n || (n > 0 && (!x || !v || !f)) || !mass || nsteps < 0 ||
+      (rebuild_every < 0 && rebuild_every != TERSOFF_REBUILD_ON_SKIN) || !(dt > 0.0) ||
+      !std::isfinite(dt))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad MD arguments");
+  c->last_rebuilds = 0;
+  const bool on_skin = rebuild_every == TERSOFF_REBUILD_ON_SKIN;
   for (int t = 0; t < c->ns; ++t)
     if (!(mass[t] > 0.0)) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "masses must be positive");
   if (n == 0 || nsteps == 0) return TERSOFF_OK;
@@ -704,7 +780,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   TGB_CUDA(c, cudaMemcpyAsync(c->d_snap, x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   TGB_CUDA(c, cudaMemcpyAsync(c->d_snap + m, v, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   TGB_CUDA(c, cudaMemcpyAsync(c->d_snap + 2 * m, f, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-  const int ssb0 = c->steps_since_build;
+  const int ssb0 = on_skin ? -1 : c->steps_since_build;
   auto& G = c->graph;
   const bool same = G.exec && G.gen == c->gen && G.x == x && G.v == v && G.f == f &&
                     G.thermo == thermo && G.dt == dt && G.nsteps == nsteps &&
@@ -735,7 +811,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     if (graph) cudaGraphDestroy(graph);
     if (st) {
       tgb::drop_graph(c);
-      c->steps_since_build = ssb0;
+      if (!on_skin) c->steps_since_build = ssb0;
       return st;
     }
     G.x = x;
@@ -752,17 +828,31 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     G.gen = c->gen;
     G.kernels = c->launches - l0;
     c->launches = l0;
-  } else {
-    // host bookkeeping of the replayed sequence
+    c->last_rebuilds = 0;  // nothing ran yet
+  } else if (!on_skin) {
+    // host bookkeeping of the replayed sequence (the capture did the same)
     for (int step = 0; step < nsteps; ++step) {
       c->steps_since_build++;
       if (rebuild_every > 0 && c->steps_since_build >= rebuild_every) c->steps_since_build = 0;
     }
   }
+  if (!on_skin) {
+    // rebuild steps of the fixed period in this call
+    int ssb = ssb0;
+    for (int step = 0; step < nsteps; ++step)
+      if (rebuild_every > 0 && ++ssb >= rebuild_every) {
+        ssb = 0;
+        c->last_rebuilds++;
+      }
+  }
   c->launches += G.kernels;
   TGB_CUDA(c, cudaGraphLaunch(G.exec, s));
   if ((st = tgb::read_flags(c, s))) return st;
   if (c->timing) tgb::fold_graph_timers(c);
+  if (on_skin) {
+    c->last_rebuilds = c->h_flags[tgb::FLAG_NREBUILD];
+    c->launches += (long long)c->last_rebuilds * G.body_kernels;
+  }
   const bool bad = c->h_flags[tgb::FLAG_OVF_ANY] || c->h_flags[tgb::FLAG_NONFINITE];
   if (!bad) {
     c->max_cnt = c->h_flags[tgb::FLAG_OVERFLOW];
@@ -776,13 +866,14 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   TGB_CUDA(c, cudaMemcpyAsync(v, c->d_snap + m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   TGB_CUDA(c, cudaMemcpyAsync(f, c->d_snap + 2 * m, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   if (c->h_flags[tgb::FLAG_NONFINITE]) {
-    c->steps_since_build = ssb0;
+    if (!on_skin) c->steps_since_build = ssb0;
     TGB_CUDA(c, cudaStreamSynchronize(s));
     return tgb::fail(c, TERSOFF_E_NONFINITE, "non-finite position during MD (state restored)");
   }
   c->cap = c->cap + c->cap / 2 + 4;
   c->gen++;
   if ((st = tgb::build_list(c, x, s))) return st;
+  c->last_rebuilds = 0;
   st = enqueue_md(c, x, v, f, dt, nsteps, rebuild_every, rows, thermo, true, s);
   if (st) return st;
   TGB_CUDA(c, cudaStreamSynchronize(s));
@@ -827,6 +918,12 @@ int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
     TGB_CUDA(c, cudaMemcpyAsync(thermo, c->d_thermo, sizeof(double) * 3 * nsteps,
                                 cudaMemcpyDeviceToHost, s));
   TGB_CUDA(c, cudaStreamSynchronize(s));
+  return TERSOFF_OK;
+}
+
+int tersoff_md_rebuilds(const tersoff_ctx* p, int* count) {
+  if (!p || !count) return TERSOFF_E_INVALID_ARG;
+  *count = p->impl.last_rebuilds;
   return TERSOFF_OK;
 }
 

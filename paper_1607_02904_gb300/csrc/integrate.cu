@@ -212,6 +212,14 @@ __global__ void k_gather(GatherArgs ga, double* __restrict__ f) {
   f[3 * (size_t)i + 2] = F[2];
 }
 
+// one thread: rebuild when the running max squared displacement (float bits,
+// non-negative) exceeds lim2
+__global__ void k_decide_rebuild(int* flags, float lim2, cudaGraphConditionalHandle h) {
+  const bool go = __int_as_float(flags[FLAG_DMAX]) > lim2;
+  if (go) flags[FLAG_NREBUILD] += 1;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // rows: ACC_LEN doubles per step (energy, virial[6], kinetic in mass units)
 __global__ void k_thermo_rows(const double* rows, int nsteps, double mvv2e, double* out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -273,6 +281,13 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
 int launch_gather(Ctx* c, double* f, cudaStream_t s) {
   if (c->n == 0) return TERSOFF_OK;
   k_gather<<<(c->n + 255) / 256, 256, 0, s>>>(make_gather(c), f);
+  c->launches++;
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+int launch_decide_rebuild(Ctx* c, float lim2, cudaGraphConditionalHandle h, cudaStream_t s) {
+  k_decide_rebuild<<<1, 1, 0, s>>>(c->d_flags, lim2, h);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

@@ -94,6 +94,7 @@ struct Ctx {
   std::vector<float> h_rec32;
   cudaStream_t side = nullptr;    // side stream for small force launches
   cudaStream_t cap_stream = nullptr;  // stream used to capture MD graphs
+  cudaStream_t body_stream = nullptr; // captures the body of a conditional rebuild
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* d_filt64 = nullptr;     // (ti,tj) filter radius^2
   float* d_filt32 = nullptr;
@@ -149,6 +150,7 @@ struct Ctx {
   double* d_coef = nullptr;       // MD: dt/2 F->a / m per species, then masses
   Coef coef{};                    // the same, passed to the kernels by value
   int steps_since_build = 0;
+  int last_rebuilds = 0;          // neighbour rebuilds during the last MD call
   double* d_fbuf = nullptr;       // scratch forces (n x 3) for calls without output
   double* d_stage = nullptr;      // host-call staging: x, v, f (3 x n x 3)
   double* d_thermo = nullptr;     // host-call staging thermo
@@ -181,7 +183,8 @@ struct Ctx {
     int nsteps = 0, rebuild_every = 0, ssb0 = 0, precision = 0;
     bool timing = false;
     long long gen = -1;
-    long long kernels = 0;  // kernel launches inside the graph
+    long long kernels = 0;  // kernel launches inside the graph, conditional bodies excluded
+    long long body_kernels = 0;  // kernel launches of one conditional rebuild
   } graph;
   double* d_snap = nullptr;  // x, v, f at the start of a graph launch (rollback)
   size_t snap_alloc = 0;
@@ -215,6 +218,7 @@ enum : int {
   FLAG_FALLBACK = 9 * FLAG_STRIDE,      // atoms handled by the general path
   FLAG_OVF_ANY = 10 * FLAG_STRIDE,      // some build exceeded the list capacity
   FLAG_EXTRA = 11 * FLAG_STRIDE,        // last force evaluation scattered through atomics
+  FLAG_NREBUILD = 12 * FLAG_STRIDE,     // displacement-triggered rebuilds in this MD call
   FLAG_EXTRA_STICKY = 13 * FLAG_STRIDE, // some evaluation since the call began did
   FLAG_COUNT = 16 * FLAG_STRIDE
 };
@@ -269,6 +273,9 @@ int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick,
 // closing half kick of the last step with gathered forces, which are also
 // written to f; ke_row (optional) as above
 int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t s);
+// Sets the condition of a graph IF node: 1 when the largest squared
+// displacement since the last build exceeds lim2 (and counts it), else 0.
+int launch_decide_rebuild(Ctx* c, float lim2, cudaGraphConditionalHandle h, cudaStream_t s);
 // thermo (nsteps x 3: potential, kinetic [eV], total) from the accumulator rows
 int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, double* thermo,
                        cudaStream_t s);
