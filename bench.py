@@ -438,6 +438,9 @@ def run_ours(args):
     ctx64.close()
     if rank == 0 and not args.no_extra:
         out["single_evaluations"] = single_evaluations(T, W, dev, flush, cpu=not args.no_cpu_baseline)
+        del flush
+        torch.cuda.empty_cache()
+        out["large_md"] = large_md(T, W, dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x, v, t, box, names, table)
     if rank == 0:
@@ -490,6 +493,58 @@ def time_backward(T, ctxm, xdm, ctx64, xd64, flush, reps=10):
         fw = _event_time(lambda: ctx.compute(xd, e, f, w), reps, flush, stream)
         out[name] = {"backward_ms": bw, "forward_ms": fw, "backward_over_forward": bw / fw,
                      "backward_atoms_per_s": n / (bw * 1e-3)}
+    return out
+
+
+def large_md(T, W, dev, steps_mixed=1000, steps_fp64=100, chunk=100):
+    """Si diamond 160x160x80 cells (16,384,000 atoms) at 1000 K: NVE velocity
+    Verlet, dt 1 fs, r_list 4.0 A (skin 1.0), rebuilds triggered by the
+    displacement (half the skin), all steps of a call in one CUDA graph. Reports
+    atom-steps/s per path and the total-energy drift per atom per ns (least-squares
+    slope of E_tot / N over the run)."""
+    import numpy as np
+    import torch
+    x, v, t, box, names = W.config_si_large()
+    n = x.shape[0]
+    table = T.mix_tersoff89(*W.element_records(names))
+    mass = [W.MASS_AMU[s] for s in names]
+    stream = torch.cuda.current_stream()
+    out = {"workload": "si-diamond-160x160x80-16384000-atoms-1000K-dt1fs-rlist4.0-"
+                       "rebuild-on-half-skin", "atoms": n}
+    for name, prec, steps in (("mixed", T.MIXED, steps_mixed), ("fp64", T.FP64, steps_fp64)):
+        ctx = T.Context(prec)
+        ctx.params(table)
+        xd = torch.tensor(x, dtype=torch.float64, device=dev)
+        vd = torch.tensor(v, dtype=torch.float64, device=dev)
+        td = torch.tensor(t, dtype=torch.int32, device=dev)
+        ctx.neighbor_build(xd, td, box, R_LIST)
+        fd = torch.zeros_like(xd)
+        ctx.compute(xd, None, fd)
+        th = torch.zeros((chunk, 3), dtype=torch.float64, device=dev)
+        # one untimed call captures the graph
+        ctx.md_step(xd, vd, fd, mass, DT, chunk, -1, th)
+        torch.cuda.synchronize()
+        ms, etot, rebuilds = 0.0, [], 0
+        for _ in range(steps // chunk):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.md_step(xd, vd, fd, mass, DT, chunk, -1, th)
+            b.record(stream)
+            b.synchronize()
+            ms += a.elapsed_time(b)
+            rebuilds += ctx.md_rebuilds()
+            etot.extend(th[:, 2].cpu().numpy().tolist())
+        e = np.asarray(etot) / n
+        tt = np.arange(e.size) * DT * 1e-3  # ns
+        slope = float(np.polyfit(tt, e, 1)[0])
+        out[name] = {"steps": steps, "ms": ms, "atom_steps_per_s": n * steps / (ms * 1e-3),
+                     "rebuilds": rebuilds, "etot_drift_eV_per_atom_per_ns": slope,
+                     "etot_first_last_eV_per_atom": [float(e[0]), float(e[-1])]}
+        ctx.close()
+        del xd, vd, td, fd, th
+        torch.cuda.empty_cache()
+    out["mixed_over_fp64"] = out["mixed"]["atom_steps_per_s"] / out["fp64"]["atom_steps_per_s"]
     return out
 
 
