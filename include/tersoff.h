@@ -106,6 +106,29 @@ int tersoff_params(tersoff_ctx* ctx, int n_species, const double* table);
 int tersoff_neighbor_build(tersoff_ctx* ctx, const double* x, const int* types, int n,
                            const double* box, double r_list, void* stream);
 
+/* Neighbour lists of a batch of n_systems independent periodic systems held
+ * in one context (for fitting over many configurations; the paper treats one
+ * system, Sec. II Eq. 4 applied to each). The atoms of system s are
+ * x[offsets[s] .. offsets[s+1]) (device, N x 3 in total; types device, N);
+ * sys_offsets: HOST, n_systems + 1 ints from 0 to n, non-decreasing; boxes:
+ * HOST, n_systems x 3 orthorhombic edges, each at least 2 r_list
+ * (TERSOFF_E_BOX_TOO_SMALL otherwise). Membership is the exact test of
+ * tersoff_neighbor_build within each system; list entries hold global atom
+ * indices (tersoff_neighbor_export works unchanged). Afterwards the context
+ * is in batch mode: use tersoff_compute_batched and tersoff_backward (with one
+ * gE per system); tersoff_compute and the MD calls return TERSOFF_E_STATE
+ * until the next tersoff_neighbor_build. Synchronises `stream`. */
+int tersoff_neighbor_build_batched(tersoff_ctx* ctx, const double* x, const int* types, int n,
+                                   const int* sys_offsets, const double* boxes, int n_systems,
+                                   double r_list, void* stream);
+
+/* Energy, forces and virial of every system of the batch in one launch over
+ * all atoms (Eq. 1, Eq. 5-7 per system). Outputs (device): energies[n_systems],
+ * forces[N x 3], virials[n_systems x 6] (component order as tersoff_compute);
+ * any may be NULL. Per-system sums are formed in a fixed order. */
+int tersoff_compute_batched(tersoff_ctx* ctx, const double* x, int n, double* energies,
+                            double* forces, double* virials, void* stream);
+
 /* Current per-atom capacity of the neighbour list and the largest count seen
  * in the last build (host outputs, either may be NULL). */
 int tersoff_neighbor_capacity(const tersoff_ctx* ctx, int* capacity, int* max_count);
@@ -142,7 +165,10 @@ int tersoff_compute(tersoff_ctx* ctx, const double* x, int n, double* energy,
  * force term, a Hessian-vector product) is not provided and returns
  * TERSOFF_E_INVALID_ARG. x: positions of the atoms of the last neighbour build
  * (as for tersoff_compute). Arithmetic follows the context's precision (mixed:
- * per-term float, gradient sums in double). */
+ * per-term float, gradient sums in double). In batch mode (see
+ * tersoff_neighbor_build_batched) gE holds one weight per system and E is the
+ * vector of system energies: grad_table = d/dtheta [sum_s gE_s E_s +
+ * sum_a gF_a . F_a] and grad_x = -gE_{s(a)} F_a. */
 int tersoff_backward(tersoff_ctx* ctx, const double* x, int n, const double* gE,
                      const double* gF, double* grad_x, double* grad_table, void* stream);
 

@@ -40,6 +40,8 @@ _SIG = {
     "tersoff_set_precision": ([_P, _I], _I),
     "tersoff_params": ([_P, _I, _P], _I),
     "tersoff_neighbor_build": ([_P, _P, _P, _I, _P, _D, _P], _I),
+    "tersoff_neighbor_build_batched": ([_P, _P, _P, _I, _P, _P, _I, _D, _P], _I),
+    "tersoff_compute_batched": ([_P, _P, _I, _P, _P, _P, _P], _I),
     "tersoff_neighbor_capacity": ([_P, _P, _P], _I),
     "tersoff_set_neighbor_capacity": ([_P, _I], _I),
     "tersoff_neighbor_export": ([_P, _P, _P, _I, _P], _I),
@@ -151,6 +153,22 @@ class Context:
         self._check(self.lib.tersoff_neighbor_build(self.h, _ptr(x), _ptr(types), self.n,
                                                     b.ctypes.data_as(_P), float(r_list),
                                                     _stream(stream)))
+
+    def neighbor_build_batched(self, x, types, offsets, boxes, r_list, stream=None):
+        """offsets: host ints (n_systems + 1); boxes: host (n_systems, 3)."""
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        bx = np.ascontiguousarray(boxes, dtype=np.float64)
+        self.n = int(x.shape[0])
+        self.n_sys = int(off.size - 1)
+        self._check(self.lib.tersoff_neighbor_build_batched(
+            self.h, _ptr(x), _ptr(types), self.n, off.ctypes.data_as(_P), bx.ctypes.data_as(_P),
+            self.n_sys, float(r_list), _stream(stream)))
+
+    def compute_batched(self, x, energies=None, forces=None, virials=None, stream=None):
+        self._check(self.lib.tersoff_compute_batched(self.h, _ptr(x), int(x.shape[0]),
+                                                     _ptr(energies), _ptr(forces), _ptr(virials),
+                                                     _stream(stream)))
 
     def neighbor_capacity(self):
         cap = _I()

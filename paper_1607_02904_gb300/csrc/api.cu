@@ -299,7 +299,8 @@ int tersoff_destroy(tersoff_ctx* p) {
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
                   c->d_bucket, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
-                  c->d_extra};
+                  c->d_extra, c->d_geo, c->d_sys, c->d_atom_sys, c->d_sys_off, c->d_vatom,
+                  c->d_eatom};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_flags) cudaFreeHost(c->h_flags);
@@ -467,6 +468,7 @@ int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, in
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "r_list is below the potential's cutoff");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = tgb::setup_grid(c, box, r_list))) return st;
+  c->n_sys = 0;
   c->n = n;
   c->r_list = r_list;
   c->margin = 0.6 * (r_list - c->rmax_cut);
@@ -478,6 +480,110 @@ int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, in
   // species range check on the device copy is folded into the build kernels'
   // parameter lookups; validate here on a host copy for clear errors
   if (n > 0) {
+    std::vector<int> ht(n);
+    TGB_CUDA(c, cudaMemcpyAsync(ht.data(), types, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+    TGB_CUDA(c, cudaStreamSynchronize(s));
+    for (int i = 0; i < n; ++i)
+      if (ht[i] < 0 || ht[i] >= c->ns)
+        return tgb::fail(c, TERSOFF_E_INVALID_ARG, "species index out of range");
+  }
+  return tgb::build_list(c, x, s);
+}
+
+int tersoff_neighbor_build_batched(tersoff_ctx* p, const double* x, const int* types, int n,
+                                   const int* sys_offsets, const double* boxes, int n_sys,
+                                   double r_list, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (c->ns == 0) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_params must come first");
+  if (n_sys < 1 || !sys_offsets || !boxes)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "need n_systems >= 1, offsets and boxes");
+  if (n < 0 || n > tgb::MAX_ATOMS || (n > 0 && (!x || !types)))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad atom arrays or count (max 2^26 atoms)");
+  if (!(r_list > 0.0) || !std::isfinite(r_list))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "r_list must be positive");
+  if (r_list < c->rmax_cut)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "r_list is below the potential's cutoff");
+  if (sys_offsets[0] != 0 || sys_offsets[n_sys] != n)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "offsets must run from 0 to n");
+  for (int q = 0; q < n_sys; ++q)
+    if (sys_offsets[q + 1] < sys_offsets[q])
+      return tgb::fail(c, TERSOFF_E_INVALID_ARG, "offsets must not decrease");
+  // one cell grid per system, cells numbered consecutively
+  std::vector<tgb::GridDev> geo(n_sys);
+  std::vector<tgb::SysShift> shifts(n_sys);
+  double hmax = 0.0;
+  long cells = 0;
+  for (int q = 0; q < n_sys; ++q) {
+    tgb::GridDev& g = geo[q];
+    g.cell_base = (int)cells;
+    long nq = 1;
+    for (int a = 0; a < 3; ++a) {
+      const double L = boxes[3 * (size_t)q + a];
+      if (!(L > 0.0) || !std::isfinite(L))
+        return tgb::fail(c, TERSOFF_E_INVALID_ARG, "box edges must be positive and finite");
+      if (L < 2.0 * r_list)
+        return tgb::fail(c, TERSOFF_E_BOX_TOO_SMALL,
+                         "a system's box edge is shorter than twice the neighbour-list radius");
+      int nc = (int)std::floor(L / r_list);
+      nc = nc < 2 ? 2 : (nc > 1024 ? 1024 : nc);
+      g.nc[a] = nc;
+      g.L[a] = L;
+      g.invL[a] = 1.0 / L;
+      g.h[a] = L / nc;
+      g.invh[a] = nc / L;
+      g.hf[a] = (float)g.h[a];
+      hmax = std::fmax(hmax, g.h[a]);
+      nq *= nc;
+    }
+    cells += nq;
+    if (cells > (1L << 30))
+      return tgb::fail(c, TERSOFF_E_INVALID_ARG, "too many list cells over the systems");
+  }
+  // the launch-wide grid carries only the fixed-point scale and hmax
+  tgb::Grid& G = c->grid;
+  for (int a = 0; a < 3; ++a) {
+    G.nc[a] = 1;
+    G.L[a] = G.h[a] = hmax;
+    G.invL[a] = G.invh[a] = 1.0 / hmax;
+  }
+  G.fix_shift = (int)std::floor(30.0 - std::log2(hmax + 8.0));
+  const double scale = std::ldexp(1.0, G.fix_shift);
+  for (int q = 0; q < n_sys; ++q)
+    for (int a = 0; a < 3; ++a) {
+      shifts[q].hq[a] = (int)std::llrint(geo[q].h[a] * scale);
+      shifts[q].hf[a] = (float)geo[q].h[a];
+      shifts[q].h[a] = geo[q].h[a];
+    }
+  std::vector<int> asys((size_t)n);
+  for (int q = 0; q < n_sys; ++q)
+    for (int i = sys_offsets[q]; i < sys_offsets[q + 1]; ++i) asys[i] = q;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = tgb::dev_alloc(c, &c->d_geo, (size_t)n_sys))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_sys, (size_t)n_sys))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_sys_off, (size_t)n_sys + 1))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_atom_sys, (size_t)n))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_eatom, (size_t)n))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_vatom, 6 * (size_t)n))) return st;
+  TGB_CUDA(c, cudaMemcpy(c->d_geo, geo.data(), sizeof(tgb::GridDev) * n_sys,
+                         cudaMemcpyHostToDevice));
+  TGB_CUDA(c, cudaMemcpy(c->d_sys, shifts.data(), sizeof(tgb::SysShift) * n_sys,
+                         cudaMemcpyHostToDevice));
+  TGB_CUDA(c, cudaMemcpy(c->d_sys_off, sys_offsets, sizeof(int) * (n_sys + 1),
+                         cudaMemcpyHostToDevice));
+  if (n > 0)
+    TGB_CUDA(c, cudaMemcpy(c->d_atom_sys, asys.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+  c->n_sys = n_sys;
+  c->ncell_batch = cells;
+  c->n = n;
+  c->r_list = r_list;
+  c->margin = 0.6 * (r_list - c->rmax_cut);
+  c->have_list = false;
+  c->gen++;
+  if ((st = tgb::ensure_atoms(c, n))) return st;
+  if (n > 0) {
+    TGB_CUDA(c, cudaMemcpyAsync(c->d_types, types, sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
     std::vector<int> ht(n);
     TGB_CUDA(c, cudaMemcpyAsync(ht.data(), types, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
     TGB_CUDA(c, cudaStreamSynchronize(s));
@@ -519,11 +625,27 @@ int tersoff_neighbor_export(tersoff_ctx* p, int* cnt, int* nbr, int cap, void* s
   return TERSOFF_OK;
 }
 
+// forces of a batch of systems into f, per-system energy and virial (either
+// may be NULL)
+static int batch_impl(Ctx* c, const double* x, double* f, double* energies, double* virials,
+                      cudaStream_t s) {
+  int st;
+  if ((st = tgb::ensure_nbr(c))) return st;
+  if ((st = tgb::launch_pack_positions(c, x, false, s))) return st;
+  TGB_CUDA(c, cudaMemsetAsync(c->d_acc, 0, sizeof(double) * tgb::ACC_LEN, s));
+  TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_EXTRA_STICKY, 0, sizeof(int), s));
+  if ((st = tgb::launch_forward_batch(c, c->d_extra, s))) return st;
+  if ((st = tgb::launch_gather(c, f, s))) return st;
+  return tgb::launch_system_sums(c, energies, virials, s);
+}
+
 static int compute_impl(Ctx* c, const double* x, int n, double* energy, double* forces,
                         double* virial, double* eatom, cudaStream_t s) {
   int st = tgb::check_ctx(c);
   if (st) return st;
   if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (c->n_sys > 0)
+    return tgb::fail(c, TERSOFF_E_STATE, "the context holds a batch: use tersoff_compute_batched");
   if (n != c->n || (n > 0 && !x))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
   double* f = forces ? forces : c->d_fbuf;
@@ -540,6 +662,18 @@ static int compute_impl(Ctx* c, const double* x, int n, double* energy, double* 
                                   sizeof(double) * tgb::ACC_STRIDE, sizeof(double), 6,
                                   cudaMemcpyDeviceToDevice, s));
   return TERSOFF_OK;
+}
+
+int tersoff_compute_batched(tersoff_ctx* p, const double* x, int n, double* energies,
+                            double* forces, double* virials, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list || c->n_sys == 0)
+    return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build_batched must come first");
+  if (n != c->n || (n > 0 && !x))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
+  return batch_impl(c, x, forces ? forces : c->d_fbuf, energies, virials, (cudaStream_t)stream);
 }
 
 int tersoff_compute(tersoff_ctx* p, const double* x, int n, double* energy, double* forces,
@@ -576,7 +710,11 @@ int tersoff_backward(tersoff_ctx* p, const double* x, int n, const double* gE, c
     if ((st = tgb::launch_backward(c, gE, gF, grad_table, s))) return st;
   }
   if (grad_x) {
-    if ((st = compute_impl(c, x, n, nullptr, grad_x, nullptr, nullptr, s))) return st;
+    if (c->n_sys > 0)
+      st = batch_impl(c, x, grad_x, nullptr, nullptr, s);
+    else
+      st = compute_impl(c, x, n, nullptr, grad_x, nullptr, nullptr, s);
+    if (st) return st;
     if ((st = tgb::launch_scale_forces(c, grad_x, gE, s))) return st;
   }
   return TERSOFF_OK;
@@ -595,6 +733,8 @@ int tersoff_compute_noalloc(tersoff_ctx* p, const double* x, int n, double* ener
   int st = tgb::check_ctx(c);
   if (st) return st;
   if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (c->n_sys > 0)
+    return tgb::fail(c, TERSOFF_E_STATE, "the context holds a batch: use tersoff_compute_batched");
   if (n != c->n || (n > 0 && !x))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
   double* scr = nullptr;
@@ -729,6 +869,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
   int st = tgb::check_ctx(c);
   if (st) return st;
   if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
+  if (c->n_sys > 0) return tgb::fail(c, TERSOFF_E_STATE, "MD runs on single-system contexts");
   if (n != c->n || (n > 0 && (!x || !v || !f)) || !mass || nsteps < 0 ||
       (rebuild_every < 0 && rebuild_every != TERSOFF_REBUILD_ON_SKIN) || !(dt > 0.0) ||
       !std::isfinite(dt))

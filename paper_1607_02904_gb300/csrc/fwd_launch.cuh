@@ -79,7 +79,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
 }
 
 template <class T>
-int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
+FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   FwdArgs<T> a;
   a.n = c->n;
   a.cap = c->cap;
@@ -110,10 +110,44 @@ int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
   a.acc = acc;
   a.eatom = eatom;
   a.flags = c->d_flags;
+  a.sys = c->d_sys;
+  a.atom_sys = c->d_atom_sys;
+  a.vatom = c->d_vatom;
+  a.order = c->d_bucket;
+  a.n_items = c->d_flags + flag_bucket(0);
+  a.order2 = a.order3 = nullptr;
+  a.n_items2 = a.n_items3 = nullptr;
+  a.identity = 1;
+  return a;
+}
+
+template <class T>
+int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
+  FwdArgs<T> a = make_args<T>(c, f, acc, eatom);
   switch (c->ns) {
     case 1: launch_buckets<T, 1>(c, a, s); break;
     case 2: launch_buckets<T, 2>(c, a, s); break;
     default: launch_buckets<T, 0>(c, a, s); break;
+  }
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+// Batch of systems: one launch over all atoms in index order with register
+// capacity 8 (the coordination of mixed packings varies widely), per-atom
+// energy and virial for the per-system sums.
+template <class T>
+int launch_batch(Ctx* c, double* f, cudaStream_t s) {
+  FwdArgs<T> a = make_args<T>(c, f, c->d_acc, c->d_eatom);
+  const int grid = (c->n + BLOCK - 1) / BLOCK;
+  if (grid > 0) {
+    if (c->has_lam3)
+      k_tersoff<T, 0, 8, 1, true><<<grid, BLOCK, 0, s>>>(a);
+    else if (c->sym_table)
+      k_tersoff<T, 0, 8, 2, true><<<grid, BLOCK, 0, s>>>(a);
+    else
+      k_tersoff<T, 0, 8, 0, true><<<grid, BLOCK, 0, s>>>(a);
+    c->launches++;
   }
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

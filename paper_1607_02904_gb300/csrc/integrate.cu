@@ -212,6 +212,37 @@ __global__ void k_gather(GatherArgs ga, double* __restrict__ f) {
   f[3 * (size_t)i + 2] = F[2];
 }
 
+// one block per system: sums of the per-atom energy and virial over the
+// system's atom range (fixed order: deterministic)
+__global__ void k_system_sums(const int* __restrict__ off, const double* __restrict__ eatom,
+                              const double* __restrict__ vatom, double* __restrict__ energy,
+                              double* __restrict__ virial) {
+  const int sys = blockIdx.x;
+  const int a0 = off[sys], a1 = off[sys + 1];
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+    v[0] += eatom[i];
+    for (int q = 0; q < 6; ++q) v[1 + q] += vatom[6 * (size_t)i + q];
+  }
+  __shared__ double part[7][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 7; ++q) {
+    double t = v[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) part[q][wid] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[threadIdx.x][w];
+    if (threadIdx.x == 0) {
+      if (energy) energy[sys] = t;
+    } else if (virial) {
+      virial[6 * (size_t)sys + threadIdx.x - 1] = t;
+    }
+  }
+}
+
 // one thread: rebuild when the running max squared displacement (float bits,
 // non-negative) exceeds lim2
 __global__ void k_decide_rebuild(int* flags, float lim2, cudaGraphConditionalHandle h) {
@@ -281,6 +312,14 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
 int launch_gather(Ctx* c, double* f, cudaStream_t s) {
   if (c->n == 0) return TERSOFF_OK;
   k_gather<<<(c->n + 255) / 256, 256, 0, s>>>(make_gather(c), f);
+  c->launches++;
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
+int launch_system_sums(Ctx* c, double* energy, double* virial, cudaStream_t s) {
+  if (c->n_sys <= 0) return TERSOFF_OK;
+  k_system_sums<<<c->n_sys, 256, 0, s>>>(c->d_sys_off, c->d_eatom, c->d_vatom, energy, virial);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

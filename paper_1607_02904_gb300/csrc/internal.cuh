@@ -76,6 +76,24 @@ struct Coef {
   float c2f[TERSOFF_MAX_SPECIES];
 };
 
+// Cell grid of one periodic system on the device (the launch-wide grid, or one
+// system of a batch whose cells are numbered from cell_base).
+struct GridDev {
+  int nc[3];
+  int cell_base;
+  double L[3], invL[3], h[3], invh[3];
+  float hf[3];
+};
+
+// Periodic shift units of one system of a batch: the edges of its list cells,
+// in fixed point (mixed path), float and double. A list entry's cell offset
+// code multiplies these.
+struct SysShift {
+  int hq[3];
+  float hf[3];
+  double h[3];
+};
+
 // ------------------------------------------------------------------ context
 struct Ctx {
   int precision = TERSOFF_FP64;
@@ -151,6 +169,16 @@ struct Ctx {
   Coef coef{};                    // the same, passed to the kernels by value
   int steps_since_build = 0;
   int last_rebuilds = 0;          // neighbour rebuilds during the last MD call
+
+  // batch of independent periodic systems (n_sys > 0; tersoff_neighbor_build_batched)
+  int n_sys = 0;
+  long ncell_batch = 0;           // cells of all systems' grids
+  GridDev* d_geo = nullptr;       // n_sys grids
+  SysShift* d_sys = nullptr;      // n_sys shift units
+  int* d_atom_sys = nullptr;      // n: system of each atom
+  int* d_sys_off = nullptr;       // n_sys + 1 atom offsets
+  double* d_vatom = nullptr;      // n x 6 per-atom virial
+  double* d_eatom = nullptr;      // n per-atom energy
   double* d_fbuf = nullptr;       // scratch forces (n x 3) for calls without output
   double* d_stage = nullptr;      // host-call staging: x, v, f (3 x n x 3)
   double* d_thermo = nullptr;     // host-call staging thermo
@@ -253,6 +281,13 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s);
 int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f32(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
+// Batch of systems: forces (slots or atomics into f, as launch_forward),
+// per-atom energy d_eatom and virial d_vatom.
+int launch_forward_batch(Ctx* c, double* f, cudaStream_t s);
+int launch_forward_batch_f32(Ctx* c, double* f, cudaStream_t s);
+// Per-system sums of d_eatom and d_vatom: energy[n_sys], virial[n_sys x 6]
+// (either may be NULL).
+int launch_system_sums(Ctx* c, double* energy, double* virial, cudaStream_t s);
 
 // Force gathering (integrate.cu): F_j = own_j + contributions of the terms of
 // j's short-list neighbours (+ the atomic fallback buffer when flagged), in

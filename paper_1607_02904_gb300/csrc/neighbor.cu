@@ -22,14 +22,9 @@ constexpr int SCAN_BLOCK = 1024;
 constexpr int SCAN_ITEMS = 4;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 
-struct GridDev {
-  int nc[3];
-  double L[3], invL[3], h[3], invh[3];
-  float hf[3];
-};
-
 GridDev to_dev(const Grid& g) {
   GridDev d;
+  d.cell_base = 0;
   for (int a = 0; a < 3; ++a) {
     d.nc[a] = g.nc[a];
     d.L[a] = g.L[a];
@@ -41,12 +36,28 @@ GridDev to_dev(const Grid& g) {
   return d;
 }
 
-__global__ void k_bin(int n, const double* __restrict__ x, GridDev g, double scale,
-                      int* __restrict__ cell_of, int* __restrict__ cell_count,
+// BATCH: every atom uses the grid of its system (geo[atom_sys[i]]), whose
+// cells are numbered from its cell_base; otherwise the launch-wide grid g1
+// (a kernel parameter, read in place).
+template <bool BATCH>
+__device__ __forceinline__ const GridDev& grid_of(const GridDev& g1,
+                                                  const GridDev* __restrict__ geo,
+                                                  const int* __restrict__ atom_sys, int i) {
+  if constexpr (BATCH)
+    return geo[atom_sys[i]];
+  else
+    return g1;
+}
+
+template <bool BATCH>
+__global__ void k_bin(int n, const double* __restrict__ x, const __grid_constant__ GridDev g1,
+                      const GridDev* __restrict__ geo, const int* __restrict__ atom_sys,
+                      double scale, int* __restrict__ cell_of, int* __restrict__ cell_count,
                       double* __restrict__ origin, double* __restrict__ qorg,
                       int* __restrict__ flags) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const GridDev& g = grid_of<BATCH>(g1, geo, atom_sys, i);
   int c3[3];
   bool finite = true;
   for (int a = 0; a < 3; ++a) {
@@ -66,7 +77,7 @@ __global__ void k_bin(int n, const double* __restrict__ x, GridDev g, double sca
     c3[a] = c;
   }
   if (!finite) atomicOr(&flags[FLAG_NONFINITE], 1);
-  int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+  int cell = g.cell_base + (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
   cell_of[i] = cell;
   atomicAdd(&cell_count[cell], 1);
 }
@@ -198,11 +209,15 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
   }
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-    const int* __restrict__ cell_atoms, GridDev g, double rc2, float lo2, float hi2, int cap,
-    uint32_t* __restrict__ nbr, int* __restrict__ cnt, Radii lim, Radii core, int ns,
+    const int* __restrict__ cell_atoms, const __grid_constant__ GridDev g1,
+    const GridDev* __restrict__ geo,
+    const int* __restrict__ atom_sys, double rc2, float lo2, float hi2, int cap,
+    uint32_t* __restrict__ nbr, int* __restrict__ cnt, const __grid_constant__ Radii lim,
+    const __grid_constant__ Radii core, int ns,
     uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
     int* __restrict__ flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -211,9 +226,10 @@ __global__ void __launch_bounds__(128) k_neigh(
   int z = 0;
   int zw = 0;  // entries inside the filter radii without the margin
   if (active) {
+    const GridDev& g = grid_of<BATCH>(g1, geo, atom_sys, i);
     const float4 pi = pos32[i];
     const int ti = __float_as_int(pi.w);
-    const int ci = cell_of[i];
+    const int ci = cell_of[i] - g.cell_base;
     const int cx = ci % g.nc[0];
     const int cy = (ci / g.nc[0]) % g.nc[1];
     const int cz = ci / (g.nc[0] * g.nc[1]);
@@ -229,7 +245,7 @@ __global__ void __launch_bounds__(128) k_neigh(
           int ax = cx + ox;
           ax += (ax < 0) ? g.nc[0] : 0;
           ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
-          const int c = (az * g.nc[1] + ay) * g.nc[0] + ax;
+          const int c = g.cell_base + (az * g.nc[1] + ay) * g.nc[0] + ax;
           const float sx = ox * g.hf[0], sy = oy * g.hf[1], sz = oz * g.hf[2];
           const uint32_t code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) |
                                 ((uint32_t)(oz + 1) << 30);
@@ -374,7 +390,8 @@ int grow(Ctx* c, T** p, size_t* have, size_t need) {
 int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const int n = c->n;
   const Grid& G = c->grid;
-  const long ncell = (long)G.nc[0] * G.nc[1] * G.nc[2];
+  const bool batch = c->n_sys > 0;
+  const long ncell = batch ? c->ncell_batch : (long)G.nc[0] * G.nc[1] * G.nc[2];
   // cell arrays
   if (c->cells_alloc < (size_t)ncell + 1) {
     cudaFree(c->d_cell_count);
@@ -395,8 +412,12 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const double scale = ldexp(1.0, G.fix_shift);
   TGB_CUDA(c, cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (ncell + 1), s));
   if (n > 0) {
-    k_bin<<<nb, B, 0, s>>>(n, x, g, scale, c->d_cell_of, c->d_cell_count, c->d_origin,
-                           c->d_qorg, c->d_flags);
+    if (batch)
+      k_bin<true><<<nb, B, 0, s>>>(n, x, g, c->d_geo, c->d_atom_sys, scale, c->d_cell_of,
+                                   c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags);
+    else
+      k_bin<false><<<nb, B, 0, s>>>(n, x, g, nullptr, nullptr, scale, c->d_cell_of,
+                                    c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags);
     c->launches++;
     int st = launch_pack_positions(c, x, true, s);
     if (st) return st;
@@ -431,10 +452,16 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
       core.r2[a * c->ns + b] = (float)(rf * rf);
     }
   if (n > 0) {
-    k_neigh<<<(n + 127) / 128, 128, 0, s>>>(n, x, c->d_pos32, c->d_cell_of, c->d_cell_start,
-                                            c->d_cell_atoms, g, rc2, lo2, hi2, c->cap, c->d_nbr,
-                                            c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
-                                            c->d_bucket, c->d_flags);
+    if (batch)
+      k_neigh<true><<<(n + 127) / 128, 128, 0, s>>>(
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_cell_atoms, g, c->d_geo,
+          c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
+          c->d_zcnt, c->d_bucket, c->d_flags);
+    else
+      k_neigh<false><<<(n + 127) / 128, 128, 0, s>>>(
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_cell_atoms, g, nullptr, nullptr,
+          rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
+          c->d_bucket, c->d_flags);
     k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
                                           c->d_flags);
     c->launches += 2;

@@ -218,7 +218,7 @@ __device__ __forceinline__ T rec_val(const T* raw, int rec, int f) {
 }
 
 // ------------------------------------------------------------------ the kernel
-template <class T, int NS>
+template <class T, int NS, bool BATCH>
 __global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ BwdArgs<T> a) {
   constexpr int SNS = NS == 1 ? 1 : TERSOFF_MAX_SPECIES;
   __shared__ T sraw[SNS * SNS * SNS * NP];
@@ -240,6 +240,8 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ B
   if (i < g.n) {
     using P = typename SelfPos<T>::type;
     const P pi = self_pos<T>(g, i);
+    fwd::Shift<T, BATCH> sh;
+    sh.load(g, i);
     const int ti = g.types[i];
     const int c = min(g.cnt[i], g.cap);
     const double gE = a.gE[a.atom_cell ? a.atom_cell[i] : 0];
@@ -256,7 +258,7 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ B
                     bool& inside) {
       T dx, dy, dz;
       int j;
-      Bond<T>::vec(g, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, tj);
+      Bond<T>::vec(g, sh, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, tj);
       const T r2 = dx * dx + dy * dy + dz * dz;
       inside = r2 <= sfilt[ti * ns + tj];
       r = BM<T>::sq(r2);
@@ -388,10 +390,11 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ B
     if (sgrad[q] != 0.0) atomicAdd(&a.grad[q], sgrad[q]);
 }
 
-// grad_x = -gE F (in place: f holds F on entry)
-__global__ void k_scale_forces(double* __restrict__ f, const double* __restrict__ gE, int n3) {
+// grad_x = -gE F (in place: f holds F on entry); gE of the atom's system
+__global__ void k_scale_forces(double* __restrict__ f, const double* __restrict__ gE,
+                               const int* __restrict__ atom_sys, int n3) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n3) f[t] = -gE[0] * f[t];
+  if (t < n3) f[t] = -gE[atom_sys ? atom_sys[t / 3] : 0] * f[t];
 }
 
 template <class T> const T* filt_ptr(Ctx* c);
@@ -420,17 +423,21 @@ int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* g
     g.hq[q] = (int)llrint(c->grid.h[q] * scale);
   }
   g.qinv = ldexpf(1.0f, -c->grid.fix_shift);
+  g.sys = c->d_sys;
+  g.atom_sys = c->d_atom_sys;
   a.raw = raw;
   a.gE = gE;
-  a.atom_cell = nullptr;
+  a.atom_cell = c->n_sys > 0 ? c->d_atom_sys : nullptr;
   a.gF = gF;
   a.grad = grad;
   const int grid = (c->n + BLOCK - 1) / BLOCK;
   if (grid > 0) {
-    if (c->ns == 1)
-      k_tersoff_bwd<T, 1><<<grid, BLOCK, 0, s>>>(a);
+    if (c->n_sys > 0)
+      k_tersoff_bwd<T, 0, true><<<grid, BLOCK, 0, s>>>(a);
+    else if (c->ns == 1)
+      k_tersoff_bwd<T, 1, false><<<grid, BLOCK, 0, s>>>(a);
     else
-      k_tersoff_bwd<T, 0><<<grid, BLOCK, 0, s>>>(a);
+      k_tersoff_bwd<T, 0, false><<<grid, BLOCK, 0, s>>>(a);
     c->launches++;
   }
   TGB_CUDA(c, cudaGetLastError());
@@ -447,7 +454,8 @@ int launch_backward(Ctx* c, const double* gE, const double* gF, double* grad, cu
 int launch_scale_forces(Ctx* c, double* f, const double* gE, cudaStream_t s) {
   const int n3 = 3 * c->n;
   if (n3 == 0) return TERSOFF_OK;
-  bwd::k_scale_forces<<<(n3 + 255) / 256, 256, 0, s>>>(f, gE, n3);
+  bwd::k_scale_forces<<<(n3 + 255) / 256, 256, 0, s>>>(f, gE, c->n_sys > 0 ? c->d_atom_sys : nullptr,
+                                                        n3);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

@@ -166,6 +166,10 @@ template <class T> struct FwdArgs {
   double* acc;           // energy, virial (6)
   double* eatom;         // optional per-atom energy
   int* flags;
+  // batches of independent systems (kernels instantiated with BATCH)
+  const SysShift* sys;   // per system: periodic shift units
+  const int* atom_sys;   // system of each atom
+  double* vatom;         // per-atom virial (6), summed per system afterwards
 };
 
 // position of atom j relative to its origin, in T, and its species
@@ -199,17 +203,41 @@ __device__ __forceinline__ void decode(uint32_t e, int& j, int& ox, int& oy, int
   oz = (int)(e >> 30) - 1;
 }
 
+// Periodic shift units of atom i: the launch-wide cell edges, or (batches of
+// systems) those of atom i's system, loaded once per atom.
+template <class T, bool BATCH> struct Shift {
+  __device__ __forceinline__ void load(const FwdArgs<T>&, int) {}
+  __device__ __forceinline__ int hq(const FwdArgs<T>& a, int q) const { return a.hq[q]; }
+  __device__ __forceinline__ T h(const FwdArgs<T>& a, int q) const { return a.h[q]; }
+};
+template <class T> struct Shift<T, true> {
+  int hq_[3];
+  T h_[3];
+  __device__ __forceinline__ void load(const FwdArgs<T>& a, int i) {
+    const SysShift& s = a.sys[a.atom_sys[i]];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      hq_[q] = s.hq[q];
+      h_[q] = (T)s.h[q];
+    }
+  }
+  __device__ __forceinline__ int hq(const FwdArgs<T>&, int q) const { return hq_[q]; }
+  __device__ __forceinline__ T h(const FwdArgs<T>&, int q) const { return h_[q]; }
+};
+
 // Accurate bond vector from i to entry e's image of j.
 template <class T> struct Bond;
 template <> struct Bond<float> {
-  static __device__ __forceinline__ void vec(const FwdArgs<float>& a, int4 qi, uint32_t e,
-                                             float& dx, float& dy, float& dz, int& j, int& tj) {
+  template <bool B>
+  static __device__ __forceinline__ void vec(const FwdArgs<float>& a, const Shift<float, B>& sh,
+                                             int4 qi, uint32_t e, float& dx, float& dy,
+                                             float& dz, int& j, int& tj) {
     int ox, oy, oz;
     decode(e, j, ox, oy, oz);
     int4 qj = __ldg(&a.posq[j]);
-    int ix = qj.x - qi.x + ox * a.hq[0];
-    int iy = qj.y - qi.y + oy * a.hq[1];
-    int iz = qj.z - qi.z + oz * a.hq[2];
+    int ix = qj.x - qi.x + ox * sh.hq(a, 0);
+    int iy = qj.y - qi.y + oy * sh.hq(a, 1);
+    int iz = qj.z - qi.z + oz * sh.hq(a, 2);
     dx = (float)ix * a.qinv;
     dy = (float)iy * a.qinv;
     dz = (float)iz * a.qinv;
@@ -217,15 +245,16 @@ template <> struct Bond<float> {
   }
 };
 template <> struct Bond<double> {
-  static __device__ __forceinline__ void vec(const FwdArgs<double>& a, dpos4 pi, uint32_t e,
-                                             double& dx, double& dy, double& dz, int& j,
-                                             int& tj) {
+  template <bool B>
+  static __device__ __forceinline__ void vec(const FwdArgs<double>& a, const Shift<double, B>& sh,
+                                             dpos4 pi, uint32_t e, double& dx, double& dy,
+                                             double& dz, int& j, int& tj) {
     int ox, oy, oz;
     decode(e, j, ox, oy, oz);
     dpos4 pj = a.pos64[j];
-    dx = (pj.x - pi.x) + ox * a.h[0];
-    dy = (pj.y - pi.y) + oy * a.h[1];
-    dz = (pj.z - pi.z) + oz * a.h[2];
+    dx = (pj.x - pi.x) + ox * sh.h(a, 0);
+    dy = (pj.y - pi.y) + oy * sh.h(a, 1);
+    dz = (pj.z - pi.z) + oz * sh.h(a, 2);
     tj = (int)pj.w;
   }
 };
@@ -357,8 +386,9 @@ __device__ __forceinline__ int rec_off(int ns, int ti, int tj, int tk) {
 // use_mask: bit s of mask marks the entries s < 64 inside the filter radius
 // (the others cannot be in any term and are skipped before their bond vector
 // is formed).
-template <class T, int NS, bool LAM3>
-__device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec, int i, int ti,
+template <class T, int NS, bool LAM3, bool BATCH>
+__device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T, BATCH>& sh,
+                                          const T* srec, int i, int ti,
                                           const uint32_t* list, int c, bool slots,
                                           bool use_mask, unsigned long long mask, T& ei,
                                           T* w) {
@@ -372,7 +402,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
     if (use_mask && !((mask >> sj) & 1ull)) continue;
     T dxj, dyj, dzj;
     int j, tj;
-    Bond<T>::vec(a, pi, list[(size_t)sj * a.n + i], dxj, dyj, dzj, j, tj);
+    Bond<T>::vec(a, sh, pi, list[(size_t)sj * a.n + i], dxj, dyj, dzj, j, tj);
     const T* p2 = srec + rec_off<NS>(ns, ti, tj, tj);
     const T r2j = dxj * dxj + dyj * dyj + dzj * dzj;
     const T rij = r2j * M<T>::rsqrt_nr(r2j);
@@ -384,7 +414,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
       if (sk == sj || (use_mask && !((mask >> sk) & 1ull))) continue;
       T dxk, dyk, dzk;
       int k, tk;
-      Bond<T>::vec(a, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
+      Bond<T>::vec(a, sh, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
       const T* p3 = srec + rec_off<NS>(ns, ti, tj, tk);
       const T r2k = dxk * dxk + dyk * dyk + dzk * dzk;
       const T rik = r2k * M<T>::rsqrt_nr(r2k);
@@ -402,7 +432,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const T* srec,
       if (sk == sj || (use_mask && !((mask >> sk) & 1ull))) continue;
       T dxk, dyk, dzk;
       int k, tk;
-      Bond<T>::vec(a, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
+      Bond<T>::vec(a, sh, pi, list[(size_t)sk * a.n + i], dxk, dyk, dzk, k, tk);
       const T* p3 = srec + rec_off<NS>(ns, ti, tj, tk);
       const T r2k = dxk * dxk + dyk * dyk + dzk * dzk;
       const T rik = r2k * M<T>::rsqrt_nr(r2k);
@@ -511,7 +541,7 @@ __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc
 }
 
 // ---------------------------------------------------------------- the kernel
-template <class T, int NS, int ZC, int MODE>
+template <class T, int NS, int ZC, int MODE, bool BATCH = false>
 __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
@@ -558,6 +588,10 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
                   : (item < n_first ? a.order[item]
                      : (item < n_second ? a.order2[item - n_first] : a.order3[item - n_second]));
     T eatom_i = T(0);
+    Shift<T, BATCH> sh;
+    sh.load(a, i);
+    if (BATCH)
+      for (int q = 0; q < 6; ++q) w[q] = T(0);
     int ti;
     int z;
     unsigned long long mask = 0ull;
@@ -592,9 +626,9 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
             T xj, yj, zj;
             int tj;
             Pos<T>::coarse(a, j, xj, yj, zj, tj);
-            const T dx = (xj - xi) + ox * a.h[0];
-            const T dy = (yj - yi) + oy * a.h[1];
-            const T dz = (zj - zi) + oz * a.h[2];
+            const T dx = (xj - xi) + ox * sh.h(a, 0);
+            const T dy = (yj - yi) + oy * sh.h(a, 1);
+            const T dz = (zj - zi) + oz * sh.h(a, 2);
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
           }
@@ -618,9 +652,9 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
           T xj, yj, zj;
           int tj;
           Pos<T>::coarse(a, j, xj, yj, zj, tj);
-          const T dx = (xj - xi) + ox * a.h[0];
-          const T dy = (yj - yi) + oy * a.h[1];
-          const T dz = (zj - zi) + oz * a.h[2];
+          const T dx = (xj - xi) + ox * sh.h(a, 0);
+          const T dy = (yj - yi) + oy * sh.h(a, 1);
+          const T dz = (zj - zi) + oz * sh.h(a, 2);
           const T r2 = dx * dx + dy * dy + dz * dz;
           if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
         }
@@ -633,8 +667,8 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
     if (general) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
       if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
-      general_atom<T, NS, LAM3>(a, srec, i, ti, list, c, slots && list == a.shortl, have_mask,
-                                mask, eatom_i, w);
+      general_atom<T, NS, LAM3, BATCH>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
+                                       have_mask, mask, eatom_i, w);
     } else {
       using P = typename SelfPos<T>::type;
       const P pi = self_pos<T>(a, i);
@@ -667,7 +701,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
           }
           T dx, dy, dz;
           int j, tj;
-          Bond<T>::vec(a, pi, e, dx, dy, dz, j, tj);
+          Bond<T>::vec(a, sh, pi, e, dx, dy, dz, j, tj);
           const T r2 = dx * dx + dy * dy + dz * dz;
           const T inv = M<T>::rsqrt_nr(r2);
           ri[q] = inv;
@@ -839,6 +873,8 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
     }
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     ei += eatom_i;
+    if (BATCH)
+      for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
   if (__syncthreads_or(any)) block_reduce_store<T>(ei, w, a.acc);
 }

@@ -85,70 +85,53 @@ def maxwell_velocities(types: np.ndarray, masses: np.ndarray, temp: float,
 
 
 def random_packing(n: int, c_frac: float, density_gcc: float, min_sep: float,
-                   rng: np.random.Generator, max_batches: int = 200000):
+                   rng: np.random.Generator, max_batches: int = 20000):
     """Random sequential insertion of ``n`` Si/C atoms in a periodic cube.
 
     Species: C with probability ``c_frac`` per atom (type 1), else Si (type 0).
     The cube's volume gives the mass density ``density_gcc``; every pair of
     atoms is at least ``min_sep`` apart (minimum image). Candidates are drawn
-    in batches and accepted in draw order against a cell grid. Returns
-    (x, types, box, ok); ``ok`` is False when the attempt budget ran out.
+    in batches; a candidate is accepted, in draw order, when no atom placed
+    before it (earlier batches: a periodic k-d tree query; its own batch: a
+    direct check) is closer than ``min_sep``. Returns (x, types, box, ok);
+    ``ok`` is False when the attempt budget ran out.
     """
+    from scipy.spatial import cKDTree
+
     types = (rng.random(n) < c_frac).astype(np.int32)
     masses = np.where(types == 1, MASS_AMU["C"], MASS_AMU["Si"])
     vol = masses.sum() * _AMU_G / density_gcc  # A^3
     L = vol ** (1.0 / 3.0)
-    nc = max(int(np.floor(L / min_sep)), 1)
-    h = L / nc
-    cap = 8
-    occ = np.full((nc, nc, nc, cap), -1, dtype=np.int64)
-    cnt = np.zeros((nc, nc, nc), dtype=np.int64)
     pos = np.zeros((n, 3), dtype=np.float64)
     placed = 0
     s2 = min_sep * min_sep
-    offs = np.array([[a, b, c] for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)])
-    batch = 256
+    batch = 1024
     for _ in range(max_batches):
         if placed == n:
             break
         cand = rng.random((batch, 3)) * L
-        cc = np.minimum((cand / h).astype(np.int64), nc - 1)
-        ok = np.ones(batch, dtype=bool)
         if placed:
-            nb = (cc[:, None, :] + offs[None, :, :]) % nc  # (B,27,3)
-            ids = occ[nb[..., 0], nb[..., 1], nb[..., 2]].reshape(batch, -1)  # (B,27*cap)
-            valid = ids >= 0
-            p = pos[np.where(valid, ids, 0)]
-            d = p - cand[:, None, :]
-            d -= L * np.rint(d / L)
-            r2 = (d * d).sum(axis=2)
-            ok = ~np.any(valid & (r2 < s2), axis=1)
-        for q in np.nonzero(ok)[0]:
+            tree = cKDTree(pos[:placed], boxsize=L)
+            dist, _ = tree.query(cand, k=1, distance_upper_bound=min_sep)
+            surv = np.nonzero(dist >= min_sep)[0]
+        else:
+            surv = np.arange(batch)
+        if surv.size == 0:
+            continue
+        cs = cand[surv]
+        d = cs[:, None, :] - cs[None, :, :]
+        d -= L * np.rint(d / L)
+        near = (d * d).sum(axis=2) < s2
+        np.fill_diagonal(near, False)
+        taken = np.zeros(surv.size, dtype=bool)
+        for k in range(surv.size):
             if placed == n:
                 break
-            c = cand[q]
-            # against atoms accepted earlier in this batch (and any other)
-            ci = cc[q]
-            clash = False
-            for o in offs:
-                cell = tuple((ci + o) % nc)
-                for s in range(cnt[cell]):
-                    d = pos[occ[cell][s]] - c
-                    d -= L * np.rint(d / L)
-                    if d @ d < s2:
-                        clash = True
-                        break
-                if clash:
-                    break
-            if clash:
+            if near[k, taken].any():
                 continue
-            cell = tuple(ci)
-            if cnt[cell] >= cap:
-                continue
-            occ[cell][cnt[cell]] = placed
-            cnt[cell] += 1
-            pos[placed] = c
+            pos[placed] = cs[k]
             placed += 1
+            taken[k] = True
     box = np.array([L, L, L], dtype=np.float64)
     return np.ascontiguousarray(pos[:placed]), types[:placed], box, placed == n
 
