@@ -21,4 +21,4 @@ from ._lib import (  # noqa: F401
     declared_symbols,
 )
 from .params import mix_tersoff89, FIELDS  # noqa: F401
-from .autograd import TersoffSystem, TersoffFunction, energy_forces  # noqa: F401
+from .autograd import TersoffSystem, TersoffBatch, TersoffFunction, energy_forces  # noqa: F401

@@ -23,7 +23,13 @@ class TersoffSystem:
 
     types: (N,) int species; box: 3 edges (A); r_list: cutoff plus skin (A).
     The list is rebuilt whenever a new table is uploaded (the filter radii
-    depend on the cutoffs) or ``rebuild(x)`` is called."""
+    depend on the cutoffs) or ``rebuild(x)`` is called. A table is uploaded
+    when it is a different tensor, or the same tensor modified in place, than
+    at the last call (its values are then compared on the host); an unchanged
+    table costs no device work, so forward and backward can be captured in a
+    CUDA graph."""
+
+    energies_shape = ()
 
     def __init__(self, types, box, r_list, precision=MIXED, device=None):
         self.device = torch.device(device if device is not None else "cuda")
@@ -33,11 +39,15 @@ class TersoffSystem:
         self.box = np.ascontiguousarray(box, dtype=np.float64)
         self.r_list = float(r_list)
         self._table = None
+        self._key = None
         self.version = 0
         self.ntable = 0
 
     def load(self, x, table):
-        """Upload ``table`` (if its values changed) and build the list at x."""
+        """Upload ``table`` (if it changed) and build the list at x."""
+        key = (table.data_ptr(), str(table.device), table._version, tuple(table.shape))
+        if key == self._key:
+            return
         t = table.detach().to("cpu", torch.float64).contiguous().numpy().ravel()
         if self._table is None or t.shape != self._table.shape or not np.array_equal(t, self._table):
             self.ctx.params(t)
@@ -45,9 +55,33 @@ class TersoffSystem:
             self.ntable = t.size
             self.version += 1
             self.rebuild(x)
+        self._key = key
 
     def rebuild(self, x):
         self.ctx.neighbor_build(x.detach().contiguous(), self.types, self.box, self.r_list)
+
+    def evaluate(self, x, e, f):
+        self.ctx.compute(x, e, f)
+
+
+class TersoffBatch(TersoffSystem):
+    """Independent periodic systems in one context: the atoms of system s are
+    rows offsets[s]:offsets[s+1] of x; boxes (n_systems, 3). Energies are per
+    system."""
+
+    def __init__(self, types, offsets, boxes, r_list, precision=MIXED, device=None):
+        super().__init__(types, np.zeros(3), r_list, precision, device)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+        self.boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 3)
+        self.n_systems = self.offsets.size - 1
+        self.energies_shape = (self.n_systems,)
+
+    def rebuild(self, x):
+        self.ctx.neighbor_build_batched(x.detach().contiguous(), self.types, self.offsets,
+                                        self.boxes, self.r_list)
+
+    def evaluate(self, x, e, f):
+        self.ctx.compute_batched(x, e, f)
 
 
 class TersoffFunction(torch.autograd.Function):
@@ -57,16 +91,17 @@ class TersoffFunction(torch.autograd.Function):
     def forward(fctx, x, table, system):
         xd = x.detach().contiguous()
         system.load(xd, table)
-        e = torch.empty(1, dtype=torch.float64, device=xd.device)
+        ne = int(np.prod(system.energies_shape)) if system.energies_shape else 1
+        e = torch.empty(ne, dtype=torch.float64, device=xd.device)
         f = torch.empty_like(xd)
-        system.ctx.compute(xd, e, f)
+        system.evaluate(xd, e, f)
         fctx.system = system
         fctx.version = system.version
         fctx.table_shape = table.shape
         fctx.table_device = table.device
         fctx.set_materialize_grads(False)
         fctx.save_for_backward(xd)
-        return e.reshape(()), f
+        return e.reshape(system.energies_shape), f
 
     @staticmethod
     def backward(fctx, gE, gF):
@@ -76,10 +111,11 @@ class TersoffFunction(torch.autograd.Function):
             raise RuntimeError("the system's parameter table changed after this forward call")
         need_x, need_t = fctx.needs_input_grad[0], fctx.needs_input_grad[1]
         dev = x.device
+        ne = int(np.prod(system.energies_shape)) if system.energies_shape else 1
         if gE is None:
-            ge = torch.zeros(1, dtype=torch.float64, device=dev)
+            ge = torch.zeros(ne, dtype=torch.float64, device=dev)
         else:
-            ge = gE.reshape(1).to(dev, torch.float64).contiguous()
+            ge = gE.reshape(ne).to(dev, torch.float64).contiguous()
         gf = None if gF is None else gF.to(dev, torch.float64).contiguous()
         if need_x and gf is not None:
             raise RuntimeError("the position derivative of the forces (a Hessian-vector "
@@ -95,9 +131,9 @@ class TersoffFunction(torch.autograd.Function):
 
 
 def energy_forces(system: TersoffSystem, x: torch.Tensor, table: torch.Tensor):
-    """Energy (0-dim) and forces (N, 3), differentiable in ``table`` (both) and
-    in ``x`` (energy only)."""
+    """Energy (0-dim; per system for a TersoffBatch) and forces (N, 3),
+    differentiable in ``table`` (both) and in ``x`` (energy only)."""
     return TersoffFunction.apply(x, table, system)
 
 
-__all__ = ["TersoffSystem", "TersoffFunction", "energy_forces", "NPARAM"]
+__all__ = ["TersoffSystem", "TersoffBatch", "TersoffFunction", "energy_forces", "NPARAM"]

@@ -232,3 +232,45 @@ def test_fitting_step_in_one_cuda_graph(T):
     torch.cuda.synchronize()
     assert torch.allclose(grad, eager, rtol=1e-9, atol=0)
     ctx.close()
+
+
+def test_autograd_batch_fitting_loss_eager_and_graph(T):
+    # loss = sum_s (E_s - E0_s)^2 + sum_a |F_a - F0_a|^2 through the autograd
+    # Function: the eager gradient (warm-up on a side stream, as whole-network
+    # CUDA-graph capture requires) against the oracle; forward and backward
+    # captured in one CUDA graph reproduce it
+    x, t, boxes = concat()
+    system = T.TersoffBatch(t, OFF, boxes, R_LIST, precision=0)
+    tab = torch.tensor(TABLE, dtype=torch.float64, device="cuda", requires_grad=True)
+    xd = dev(x)
+    rng = np.random.Generator(np.random.Philox(46))
+    e0 = dev(np.array([r[0] for r in REFS]) + rng.normal(0.0, 1.0, len(CELLS)))
+    f0 = dev(np.concatenate([r[1] for r in REFS]) + rng.normal(0.0, 0.1, (OFF[-1], 3)))
+
+    def loss_fn():
+        E, F = T.energy_forces(system, xd, tab)
+        return ((E - e0) ** 2).sum() + ((F - f0) ** 2).sum(), E, F
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            tab.grad = None
+            loss, E, F = loss_fn()
+            loss.backward()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    eager = tab.grad.clone()
+    gE = 2.0 * (E.detach().cpu().numpy() - e0.cpu().numpy())
+    gF = 2.0 * (F.detach().cpu().numpy() - f0.cpu().numpy())
+    assert _scaled_err(eager.cpu().numpy(), _vjp_ref(gE, gF)) <= 1e-10
+
+    tab.grad = None
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        static_loss = loss_fn()[0]
+        static_loss.backward()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.allclose(tab.grad, eager, rtol=1e-9, atol=0)
+    assert abs(static_loss.item() - loss.item()) <= 1e-9 * abs(loss.item())

@@ -136,29 +136,32 @@ def random_packing(n: int, c_frac: float, density_gcc: float, min_sep: float,
     return np.ascontiguousarray(pos[:placed]), types[:placed], box, placed == n
 
 
+def _batched_cell(args):
+    c, size, frac, density_gcc, min_sep, seed_k = args
+    k = 0
+    while True:
+        r = np.random.Generator(np.random.Philox([SEED_BASE + seed_k, c, k]))
+        x, t, box, ok = random_packing(int(size), float(frac), density_gcc, min_sep, r)
+        if ok:
+            return x, t, box
+        k += 1
+
+
 def batched_cells(n_cells: int = 256, nmin: int = 64, nmax: int = 4096,
-                  density_gcc: float = 2.3, min_sep: float = 1.8, seed_k: int = 4):
+                  density_gcc: float = 2.3, min_sep: float = 1.8, seed_k: int = 4,
+                  map_fn=map):
     """Independent periodic Si/C cells of uneven size for the batched workload.
 
     Atom counts ~ U{nmin..nmax}, C fraction ~ U(0,1) per cell; each cell is a
     random packing at ``density_gcc`` with minimum separation ``min_sep``. A
     cell whose packing runs out of attempts is drawn again from the next seed.
+    Every cell has its own generator, so ``map_fn`` may be a process pool's map.
     """
     rng = rng_for(seed_k)
     sizes = rng.integers(nmin, nmax + 1, size=n_cells)
     fracs = rng.random(n_cells)
-    cells = []
-    for c in range(n_cells):
-        k = 0
-        while True:
-            r = np.random.Generator(np.random.Philox([SEED_BASE + seed_k, c, k]))
-            x, t, box, ok = random_packing(int(sizes[c]), float(fracs[c]), density_gcc,
-                                           min_sep, r)
-            if ok:
-                break
-            k += 1
-        cells.append((x, t, box))
-    return cells
+    jobs = [(c, sizes[c], fracs[c], density_gcc, min_sep, seed_k) for c in range(n_cells)]
+    return list(map_fn(_batched_cell, jobs))
 
 
 # --------------------------------------------------------------------- named workloads
