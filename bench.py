@@ -72,6 +72,19 @@ def workload_name():
             "10-md-steps-per-step")
 
 
+def chosen_options(summary):
+    """The options of an autotuner summary ("chosen scatter=... split=...
+    waves=... block=... (...)") as a dict."""
+    head = summary.split("(")[0].replace("chosen", "").split()
+    return dict(kv.split("=") for kv in head)
+
+
+def apply_options(ctx, T, opt):
+    ctx.set_scatter(T.SCATTER_ATOMIC if opt["scatter"] == "atomic" else T.SCATTER_GATHER)
+    split = {"auto": -1, "off": 0, "on": 1}[opt["split"]]
+    ctx.set_launch(int(opt["waves"]), split, int(opt["block"]))
+
+
 def base_config(n, world):
     return {"workload": workload_name(), "atoms_per_gpu": n, "md_steps_per_step": MD_PER_STEP,
             "dt_ps": DT, "neighbor_rebuild_every": MD_PER_STEP, "r_list_A": R_LIST,
@@ -301,19 +314,12 @@ def run_ours(args):
                    FLOP_TRIPLET * ntrip)
     mufu_launch = MUFU_SHORT * nshort + MUFU_PAIR * npair + MUFU_TRIPLET * ntrip
 
-    # ---------------- scatter mode chosen by measurement (short trial of each)
-    trial = {}
-    for name, mode in (("gather", T.SCATTER_GATHER), ("atomic", T.SCATTER_ATOMIC)):
-        ctxm.set_scatter(mode)
-        trial[name] = timed(ctxm, xdm, vdm, fm, max(3, args.steps // 5), 2)[0]
-    best = min(trial, key=trial.get)
-    ctxm.set_scatter(T.SCATTER_GATHER if best == "gather" else T.SCATTER_ATOMIC)
-    trial64 = {}
-    for name, mode in (("gather", T.SCATTER_GATHER), ("atomic", T.SCATTER_ATOMIC)):
-        ctx64.set_scatter(mode)
-        trial64[name] = timed(ctx64, xd64, vd64, f64, 2, 1)[0]
-    best64 = min(trial64, key=trial64.get)
-    ctx64.set_scatter(T.SCATTER_GATHER if best64 == "gather" else T.SCATTER_ATOMIC)
+    # ---------------- launch options chosen by the library's autotuner (MD
+    # periods on copies of the state; the timed state is not advanced)
+    tune_m = ctxm.autotune(xdm, vdm, mass, DT, MD_PER_STEP)
+    tune_d = ctx64.autotune(xd64, vd64, mass, DT, MD_PER_STEP)
+    best = chosen_options(tune_m)
+    best64 = chosen_options(tune_d)
 
     # ---------------- timed: mixed (headline), then FP64; then instrumented
     # passes of the same length for the kernel durations
@@ -375,9 +381,8 @@ def run_ours(args):
         "dtype": "f32",
         "accumulate_dtype": "f64",
         "data": "synthetic",
-        "config": dict(base_config(n, world), scatter=best,
-                       scatter_trial_ms_per_step={k: v / max(3, args.steps // 5)
-                                                  for k, v in trial.items()}),
+        "config": dict(base_config(n, world), launch=best),
+        "autotune": {"mixed": tune_m, "fp64": tune_d},
         "force_error": {
             "reference": "FP64 GPU path (itself within 1e-10 of the FP64 CPU oracle in tests)",
             "force_rms_rel": force_rms_rel,
@@ -389,7 +394,7 @@ def run_ours(args):
             "unit": UNIT,
             "ms_per_step": tmax_d / args.steps,
             "dtype": "f64",
-            "scatter": best64,
+            "launch": best64,
             "force_kernel_ms": kern_ms_d,
             "force_kernel_tflops": flop_launch / (kern_ms_d * 1e-3) / 1e12,
             "force_kernel_frac_of_fp64_nominal": flop_launch / (kern_ms_d * 1e-3) / 1e12 /
@@ -443,7 +448,7 @@ def run_ours(args):
         out["batched_fit"] = batched_fit(T, W, dev, flush, cells, gen_s)
         del flush
         torch.cuda.empty_cache()
-        out["large_md"] = large_md(T, W, dev)
+        out["large_md"] = large_md(T, W, dev, best64)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x, v, t, box, names, table)
     if rank == 0:
@@ -539,6 +544,9 @@ def batched_fit(T, W, dev, flush, cells, gen_seconds, reps=20):
     ref.ctx.close()
     system = T.TersoffBatch(t, off, boxes, R_LIST, precision=T.MIXED)
     tab = torch.tensor(table, dtype=torch.float64, device=dev, requires_grad=True)
+    with torch.no_grad():
+        T.energy_forces(system, xd, tab)  # uploads the table, builds the lists
+    tune = system.ctx.autotune(xd)
 
     def step():
         E, F = T.energy_forces(system, xd, tab)
@@ -572,14 +580,14 @@ def batched_fit(T, W, dev, flush, cells, gen_seconds, reps=20):
                        "to all table entries; mixed path; one CUDA graph per step",
            "cells": len(cells), "atoms": int(n), "cell_generation_s": gen_seconds,
            "fit_step_ms": fit_ms, "atoms_per_s": n / (fit_ms * 1e-3),
-           "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+           "forward_ms": fwd_ms, "backward_ms": bwd_ms, "autotune": tune,
            "loss": float(static_loss.item()),
            "grad_norm": float(tab.grad.norm().item())}
     system.ctx.close()
     return out
 
 
-def large_md(T, W, dev, steps_mixed=1000, steps_fp64=100, chunk=100):
+def large_md(T, W, dev, opt64, steps_mixed=1000, steps_fp64=100, chunk=100):
     """Si diamond 160x160x80 cells (16,384,000 atoms) at 1000 K: NVE velocity
     Verlet, dt 1 fs, r_list 4.0 A (skin 1.0), rebuilds triggered by the
     displacement (half the skin), all steps of a call in one CUDA graph. Reports
@@ -601,6 +609,10 @@ def large_md(T, W, dev, steps_mixed=1000, steps_fp64=100, chunk=100):
         vd = torch.tensor(v, dtype=torch.float64, device=dev)
         td = torch.tensor(t, dtype=torch.int32, device=dev)
         ctx.neighbor_build(xd, td, box, R_LIST)
+        if prec == T.MIXED:
+            out["autotune_mixed"] = ctx.autotune(xd, vd, mass, DT, MD_PER_STEP)
+        else:
+            apply_options(ctx, T, opt64)
         fd = torch.zeros_like(xd)
         ctx.compute(xd, None, fd)
         th = torch.zeros((chunk, 3), dtype=torch.float64, device=dev)

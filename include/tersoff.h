@@ -240,6 +240,39 @@ int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int 
                          const double* mass, double dt, int nsteps, int rebuild_every,
                          double* thermo, void* stream);
 
+/* Autotuner (the paper has no counterpart; its launch choices are made for
+ * CPUs). Times the context's launch options on its current system and keeps
+ * the fastest:
+ *   - the force scatter (tersoff_set_scatter);
+ *   - the separate register-capacity-8 launch on a side stream
+ *     (automatic / never / whenever needed);
+ *   - the force kernel's grid: one thread per atom, or 1, 2 or 4 waves of
+ *     the blocks resident on all multiprocessors looping over the atoms;
+ *   - the block size of the pack, integrate and gather kernels (128/256/512).
+ * One option at a time, the others fixed at their best so far (coordinate
+ * descent); every trial is the median of 5 timed repetitions (CUDA events on
+ * `stream`) after 2 untimed ones.
+ * With v != NULL the repetition is one tersoff_md_step call of `steps` steps
+ * (list rebuilt after the last step) on internal copies of x and v (device,
+ * N x 3, not modified), mass (host) and dt as for tersoff_md_step; afterwards
+ * the neighbour list is rebuilt at x. With v == NULL the repetition is one
+ * force evaluation at x (tersoff_compute, or tersoff_compute_batched for a
+ * batch). Requires a neighbour build; synchronises `stream`; allocates
+ * scratch for the copies during the call. */
+int tersoff_autotune(tersoff_ctx* ctx, const double* x, const double* v, int n,
+                     const double* mass, double dt, int steps, void* stream);
+
+/* Sets the launch options that tersoff_autotune chooses: waves (0 = one
+ * thread per atom in the force kernel, else that many waves of resident
+ * blocks, at most 64), split (-1 automatic, 0 never, 1 whenever bucket 1 is
+ * non-empty) and block (pack / integrate / gather block size, a power of two
+ * in [64, 512]). Results do not depend on them beyond rounding order. */
+int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
+
+/* One-line text of the last tersoff_autotune: the chosen options and every
+ * trial's time (storage owned by the context). */
+const char* tersoff_autotune_summary(const tersoff_ctx* ctx);
+
 /* Number of neighbour rebuilds during the last tersoff_md_step call on this
  * context (host output). */
 int tersoff_md_rebuilds(const tersoff_ctx* ctx, int* count);

@@ -53,6 +53,9 @@ _SIG = {
     "tersoff_md_step_host": ([_P, _P, _P, _P, _I, _P, _D, _I, _I, _P, _P], _I),
     "tersoff_launch_count": ([_P, _P], _I),
     "tersoff_md_rebuilds": ([_P, _P], _I),
+    "tersoff_autotune": ([_P, _P, _P, _I, _P, _D, _I, _P], _I),
+    "tersoff_autotune_summary": ([_P], ctypes.c_char_p),
+    "tersoff_set_launch": ([_P, _I, _I, _I], _I),
     "tersoff_set_timing": ([_P, _I], _I),
     "tersoff_set_graphs": ([_P, _I], _I),
     "tersoff_set_scatter": ([_P, _I], _I),
@@ -243,6 +246,22 @@ class Context:
         cnt = ctypes.c_longlong()
         self._check(self.lib.tersoff_timing(self.h, int(kind), ctypes.byref(ms), ctypes.byref(cnt)))
         return ms.value, cnt.value
+
+    def autotune(self, x, v=None, mass=None, dt=0.001, steps=10, stream=None):
+        """Time the launch options on this system (MD steps on copies when v is
+        given, else force evaluations) and keep the fastest; returns the summary."""
+        import numpy as np
+        m = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
+        self._check(self.lib.tersoff_autotune(self.h, _ptr(x), _ptr(v), int(x.shape[0]),
+                                              None if m is None else m.ctypes.data_as(_P),
+                                              float(dt), int(steps), _stream(stream)))
+        return self.autotune_summary()
+
+    def set_launch(self, waves=0, split=-1, block=256):
+        self._check(self.lib.tersoff_set_launch(self.h, int(waves), int(split), int(block)))
+
+    def autotune_summary(self):
+        return self.lib.tersoff_autotune_summary(self.h).decode()
 
     def md_rebuilds(self):
         """Neighbour rebuilds during the last md_step call."""

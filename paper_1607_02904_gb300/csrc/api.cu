@@ -2,6 +2,7 @@
 // by the context, and the launch sequences of the compute and MD calls.
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 
 #include "internal.cuh"
@@ -273,6 +274,8 @@ int tersoff_create(tersoff_ctx** out, int precision) {
   }
   cudaMemset(c->d_flags, 0, sizeof(int) * tgb::FLAG_COUNT);
   cudaMemset(c->d_acc, 0, sizeof(double) * tgb::ACC_LEN);
+  if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+    c->n_sm = 0;
   if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     c->cap_stream = nullptr;
   if (cudaStreamCreateWithFlags(&c->body_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -1060,6 +1063,136 @@ int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
                                 cudaMemcpyDeviceToHost, s));
   TGB_CUDA(c, cudaStreamSynchronize(s));
   return TERSOFF_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+namespace {
+struct TuneOpt {
+  int atomic, split, waves, block;
+};
+
+void apply_opt(Ctx* c, const TuneOpt& o) {
+  c->scatter_atomic = o.atomic != 0;
+  c->opt_split = o.split;
+  c->opt_waves = o.waves;
+  c->opt_block = o.block;
+  c->gen++;  // captured MD graphs hold the old launch shapes
+}
+
+std::string opt_text(const TuneOpt& o) {
+  char b[128];
+  std::snprintf(b, sizeof(b), "scatter=%s split=%s waves=%d block=%d",
+                o.atomic ? "atomic" : "gather",
+                o.split < 0 ? "auto" : (o.split ? "on" : "off"), o.waves, o.block);
+  return b;
+}
+}  // namespace
+
+int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, const double* mass,
+                     double dt, int steps, void* stream) {
+  Ctx* c = C(p);
+  int st = tgb::check_ctx(c);
+  if (st) return st;
+  if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "a neighbour build must come first");
+  if (n != c->n || (n > 0 && !x)) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "bad positions");
+  const bool md = v != nullptr;
+  if (md && (c->n_sys > 0 || !mass || !(dt > 0.0) || steps < 1))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG,
+                     "MD tuning needs one system, masses, dt > 0 and steps >= 1");
+  if (n == 0) return TERSOFF_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool timing = c->timing;
+  c->timing = false;
+  const size_t m = 3 * (size_t)n;
+  double* work = nullptr;  // MD trials run on copies of x, v and F(x)
+  if (md) {
+    TGB_CUDA(c, cudaMalloc(&work, sizeof(double) * 3 * m));
+    TGB_CUDA(c, cudaMemcpyAsync(work, x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    TGB_CUDA(c, cudaMemcpyAsync(work + m, v, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TGB_CUDA(c, cudaEventCreate(&e0));
+  TGB_CUDA(c, cudaEventCreate(&e1));
+  auto trial = [&](const TuneOpt& o, double* ms_out) -> int {
+    apply_opt(c, o);
+    int r;
+    auto once = [&]() -> int {
+      if (md)
+        return md_impl(c, work, work + m, work + 2 * m, n, mass, dt, steps, steps, nullptr, s);
+      if (c->n_sys > 0) return batch_impl(c, x, c->d_fbuf, nullptr, nullptr, s);
+      return compute_impl(c, x, n, nullptr, c->d_fbuf, nullptr, nullptr, s);
+    };
+    if (md && (r = compute_impl(c, work, n, nullptr, work + 2 * m, nullptr, nullptr, s))) return r;
+    for (int w = 0; w < 2; ++w)
+      if ((r = once())) return r;
+    std::vector<float> t;
+    for (int q = 0; q < 5; ++q) {
+      TGB_CUDA(c, cudaEventRecord(e0, s));
+      if ((r = once())) return r;
+      TGB_CUDA(c, cudaEventRecord(e1, s));
+      TGB_CUDA(c, cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      TGB_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+      t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *ms_out = t[t.size() / 2];
+    return TERSOFF_OK;
+  };
+  TuneOpt best{c->scatter_atomic ? 1 : 0, c->opt_split, c->opt_waves, c->opt_block};
+  double best_ms = 0.0;
+  std::string log;
+  st = trial(best, &best_ms);
+  if (!st) {
+    log = opt_text(best) + ": " + std::to_string(best_ms) + " ms";
+    // coordinate descent: one option at a time, the others at their best
+    const std::vector<std::vector<int>> values = {
+        {0, 1}, {-1, 0, 1}, {0, 1, 2, 4}, {128, 256, 512}};
+    for (int k = 0; k < 4 && !st; ++k)
+      for (int val : values[k]) {
+        TuneOpt o = best;
+        int* field = k == 0 ? &o.atomic : k == 1 ? &o.split : k == 2 ? &o.waves : &o.block;
+        if (*field == val) continue;
+        if (k == 1 && c->n_sys > 0) continue;  // batches run one launch
+        *field = val;
+        double ms = 0.0;
+        if ((st = trial(o, &ms))) break;
+        log += "; " + opt_text(o) + ": " + std::to_string(ms) + " ms";
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = o;
+        }
+      }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (work) cudaFree(work);
+  apply_opt(c, best);
+  c->timing = timing;
+  if (st) return st;
+  // the MD trials rebuilt the list on the copies: rebuild it at x
+  if (md && (st = tgb::build_list(c, x, s))) return st;
+  c->tune_summary = "chosen " + opt_text(best) + " (" + std::to_string(best_ms) + " ms per " +
+                    (md ? std::to_string(steps) + " MD steps" : std::string("evaluation")) +
+                    "); trials: " + log;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_launch(tersoff_ctx* p, int waves, int split, int block) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (waves < 0 || waves > 64 || split < -1 || split > 1 ||
+      !(block == 64 || block == 128 || block == 256 || block == 512))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG,
+                     "waves in [0, 64], split in {-1, 0, 1}, block a power of two in [64, 512]");
+  TuneOpt o{c->scatter_atomic ? 1 : 0, split, waves, block};
+  apply_opt(c, o);
+  return TERSOFF_OK;
+}
+
+const char* tersoff_autotune_summary(const tersoff_ctx* p) {
+  if (!p) return "null context";
+  return p->impl.tune_summary.c_str();
 }
 
 int tersoff_md_rebuilds(const tersoff_ctx* p, int* count) {

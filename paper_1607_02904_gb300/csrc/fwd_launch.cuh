@@ -37,10 +37,21 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
 // appended to the capacity-4 launch. Every launch masks the stored short list
 // (radius plus margin) by the cutoffs at each step; atoms with more entries
 // inside than the capacity, and bucket 2, take the general path.
+// Grid of a force launch: one thread per item, or (launch option) a number of
+// waves of the blocks that fit on all SMs at once (resident blocks per SM from
+// the kernel's launch bounds), the kernel looping over the items.
+inline int force_grid(const Ctx* c, int zc) {
+  const int full = (c->n + BLOCK - 1) / BLOCK;
+  if (c->opt_waves <= 0 || c->n_sm <= 0) return full;
+  const int resident = c->n_sm * (zc <= 4 ? 8 : 4);
+  const int g = c->opt_waves * resident;
+  return g < full ? g : full;
+}
+
 template <class T, int NS>
 void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
-  const int full = (c->n + BLOCK - 1) / BLOCK;
-  const bool split1 = (long long)c->nbucket[1] * 20 > (long long)c->n;
+  const bool split1 = c->opt_split < 0 ? (long long)c->nbucket[1] * 20 > (long long)c->n
+                                       : (c->opt_split > 0 && c->nbucket[1] > 0);
   const bool fork = split1 && c->side != nullptr;
   cudaStream_t s2 = s;
   if (fork) {
@@ -55,7 +66,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
     b1.order2 = b1.order3 = nullptr;
     b1.n_items2 = b1.n_items3 = nullptr;
     b1.identity = 0;
-    launch_t<T, NS, 8>(c, b1, full, s2);
+    launch_t<T, NS, 8>(c, b1, force_grid(c, 8), s2);
   }
   // bucket 0, then bucket 1 (unless split off), then bucket 2 (general path)
   FwdArgs<T> b0 = a;
@@ -70,7 +81,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
   b0.identity = split1 ? 0 : 1;
   {
     TimedRegion tr(c, 0, s);
-    launch_t<T, NS, 4>(c, b0, full, s);
+    launch_t<T, NS, 4>(c, b0, force_grid(c, 4), s);
   }
   if (fork) {
     cudaEventRecord(c->ev_join, c->side);
@@ -139,7 +150,7 @@ int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
 template <class T>
 int launch_batch(Ctx* c, double* f, cudaStream_t s) {
   FwdArgs<T> a = make_args<T>(c, f, c->d_acc, c->d_eatom);
-  const int grid = (c->n + BLOCK - 1) / BLOCK;
+  const int grid = force_grid(c, 8);
   if (grid > 0) {
     if (c->has_lam3)
       k_tersoff<T, 0, 8, 1, true><<<grid, BLOCK, 0, s>>>(a);

@@ -285,7 +285,8 @@ PackArgs make_pack(Ctx* c, bool track, bool build = false) {
 
 int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s) {
   if (c->n == 0) return TERSOFF_OK;
-  k_pack<<<(c->n + 255) / 256, 256, 0, s>>>(make_pack(c, !build, build), x);
+  const int B = c->opt_block;
+  k_pack<<<(c->n + B - 1) / B, B, 0, s>>>(make_pack(c, !build, build), x);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;
@@ -293,7 +294,8 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s) {
 
 int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick, bool pack,
                    double* ke_row, double* acc_zero, cudaStream_t s) {
-  k_step<<<(c->n + 255) / 256, 256, 0, s>>>(make_pack(c, true), make_gather(c), kick == 2 ? 1 : 0,
+  const int B = c->opt_block;
+  k_step<<<(c->n + B - 1) / B, B, 0, s>>>(make_pack(c, true), make_gather(c), kick == 2 ? 1 : 0,
                                             x, v, f, c->coef, dt, kick, pack ? 1 : 0, ke_row,
                                             acc_zero);
   c->launches++;
@@ -302,7 +304,8 @@ int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick,
 }
 
 int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t s) {
-  k_final_kick<<<(c->n + 255) / 256, 256, 0, s>>>(make_gather(c), c->d_types, v, f, c->coef,
+  const int B = c->opt_block;
+  k_final_kick<<<(c->n + B - 1) / B, B, 0, s>>>(make_gather(c), c->d_types, v, f, c->coef,
                                                   ke_row);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
@@ -311,7 +314,8 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
 
 int launch_gather(Ctx* c, double* f, cudaStream_t s) {
   if (c->n == 0) return TERSOFF_OK;
-  k_gather<<<(c->n + 255) / 256, 256, 0, s>>>(make_gather(c), f);
+  const int B = c->opt_block;
+  k_gather<<<(c->n + B - 1) / B, B, 0, s>>>(make_gather(c), f);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

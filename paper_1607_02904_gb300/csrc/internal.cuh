@@ -170,6 +170,14 @@ struct Ctx {
   int steps_since_build = 0;
   int last_rebuilds = 0;          // neighbour rebuilds during the last MD call
 
+  // launch options (chosen by tersoff_autotune)
+  int opt_waves = 0;   // force kernel grid: 0 = one thread per item; k > 0 = k waves of the
+                       // blocks resident on all SMs (the kernel loops over items)
+  int opt_split = -1;  // capacity-8 side-stream launch: -1 automatic, 0 never, 1 when non-empty
+  int opt_block = 256; // block size of the per-atom pack / integrate / gather kernels
+  int n_sm = 0;        // multiprocessors of the device
+  std::string tune_summary;  // last tersoff_autotune: choice and trial times
+
   // batch of independent periodic systems (n_sys > 0; tersoff_neighbor_build_batched)
   int n_sys = 0;
   long ncell_batch = 0;           // cells of all systems' grids

@@ -1,0 +1,124 @@
+"""The autotuner and the launch options it chooses between.
+
+Every option value must give the same results as the default launch, to the
+parity tolerances against the oracle (FP64 1e-10 relative; mixed force RMS,
+energy and virial 1e-5); the tuner must leave the caller's arrays untouched,
+keep a valid list, and report its trials.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests import _systems as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RC = 3.0
+MASS = [W.MASS_AMU["Si"]]
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1607_02904_gb300 as T
+    T.load()
+    return T
+
+
+def dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def check(prec, got, ref):
+    e, f, w = got
+    er, fr, wr = ref
+    if prec == 0:
+        assert abs(e - er) <= 1e-10 * abs(er)
+        assert np.abs(f - fr).max() <= 1e-10 * np.abs(fr).max()
+        assert np.abs(w - wr).max() <= 1e-10 * np.abs(wr).max()
+    else:
+        assert np.sqrt(((f - fr) ** 2).mean()) / np.sqrt((fr ** 2).mean()) <= 1e-5
+        assert abs(e - er) <= 1e-5 * abs(er)
+        assert np.abs(w - wr).max() <= 1e-5 * np.abs(wr).max()
+
+
+# SiC: many atoms need register capacity 8 (bucket 1), so the split option matters
+X, TY, BOX = S.sic_cell(n=5, sigma=0.1, seed=90)
+TABLE = S.table_for(["Si", "C"], oracle.mix_tersoff89)
+REF = oracle.compute(X, TY, BOX, TABLE, oracle.neighbors(X, BOX, RC))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("waves,split,block", [(0, -1, 256), (1, -1, 256), (2, 0, 128),
+                                               (4, 1, 512), (1, 1, 64), (0, 0, 512)])
+def test_launch_options_keep_results(T, prec, waves, split, block):
+    ctx = T.Context(prec)
+    ctx.set_launch(waves, split, block)
+    ctx.params(TABLE)
+    xd = dev(X)
+    ctx.neighbor_build(xd, dev(TY, torch.int32), BOX, RC + 0.5)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(xd)
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(xd, e, f, w)
+    torch.cuda.synchronize()
+    check(prec, (e.item(), f.cpu().numpy(), w.cpu().numpy()), REF)
+    ctx.close()
+
+
+def test_set_launch_rejects_bad_values(T):
+    ctx = T.Context(1)
+    for bad in [(-1, -1, 256), (0, 2, 256), (0, -1, 1024), (0, -1, 96)]:
+        with pytest.raises(T.TersoffError):
+            ctx.set_launch(*bad)
+    ctx.close()
+
+
+def test_autotune_md_keeps_state_and_results(T):
+    x, t, box = W.diamond(5, 5, 5, 5.432)
+    rng = np.random.Generator(np.random.Philox(91))
+    x = W.jitter_gaussian(x, 0.05, rng)
+    v = W.maxwell_velocities(t, np.array(MASS), 1000.0, rng)
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    ctx = T.Context(0)
+    ctx.params(table)
+    xd, vd = dev(x), dev(v)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+    summary = ctx.autotune(xd, vd, MASS, 0.001, 10)
+    assert summary.startswith("chosen ") and summary.count("ms") >= 8
+    assert np.array_equal(xd.cpu().numpy(), x) and np.array_equal(vd.cpu().numpy(), v)
+    # the tuned context still runs MD equal to the oracle's
+    fd = torch.zeros_like(xd)
+    ctx.compute(xd, None, fd)
+    ctx.md_step(xd, vd, fd, MASS, 0.001, 20, 10)
+    torch.cuda.synchronize()
+    xo, vo, _, fo = oracle.md_run(x, v, t, box, table, MASS, 0.001, 20, RC + 1.0, 10)
+    assert np.abs(xd.cpu().numpy() - xo).max() < 1e-9
+    assert np.abs(fd.cpu().numpy() - fo).max() < 1e-8 * np.abs(fo).max()
+    ctx.close()
+
+
+def test_autotune_batch_compute(T):
+    cells = W.batched_cells(n_cells=4, nmin=64, nmax=400, seed_k=93)
+    off = np.cumsum([0] + [len(c[0]) for c in cells]).astype(np.int32)
+    x = np.concatenate([c[0] for c in cells])
+    t = np.concatenate([c[1] for c in cells]).astype(np.int32)
+    boxes = np.stack([c[2] for c in cells])
+    ctx = T.Context(1)
+    ctx.params(TABLE)
+    xd = dev(x)
+    ctx.neighbor_build_batched(xd, dev(t, torch.int32), off, boxes, RC + 0.5)
+    summary = ctx.autotune(xd)
+    assert summary.startswith("chosen ") and "split" in summary
+    e = torch.zeros(len(cells), dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(xd)
+    w = torch.zeros((len(cells), 6), dtype=torch.float64, device="cuda")
+    ctx.compute_batched(xd, e, f, w)
+    torch.cuda.synchronize()
+    for s, (xs, ts, bs) in enumerate(cells):
+        ref = oracle.compute(xs, ts, bs, TABLE, oracle.neighbors(xs, bs, RC))
+        check(1, (e[s].item(), f[off[s]:off[s + 1]].cpu().numpy(), w[s].cpu().numpy()), ref)
+    ctx.close()
