@@ -1,0 +1,92 @@
+"""The benchmark's multi-process logic on CPU ranks (gloo, world size 2): the
+reported time is the maximum over ranks and the work is the sum, and rank
+identity comes from the launcher's environment. Each GPU runs an independent
+replica of the workload (no collective on the data path), so these are the
+only cross-rank operations.
+"""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port),
+                       "RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank)})
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ws, r, local = bench.dist_info()
+        t, u = bench.aggregate(10.0 + 5.0 * rank, 1000.0 * (rank + 1), ws)
+        out[rank] = (ws, r, local, t, u)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_aggregate_max_time_sum_units_two_ranks():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    for rank in range(world):
+        ws, r, local, t, u = out[rank]
+        assert (ws, r, local) == (world, rank, rank)
+        assert t == 15.0  # slowest rank
+        assert u == 3000.0  # all ranks' atom-steps
+
+
+def test_single_rank_aggregate_is_identity():
+    import bench
+    assert bench.aggregate(12.5, 7.0, 1) == (12.5, 7.0)
+
+
+def test_partition_balances_and_covers():
+    import numpy as np
+    from paper_1607_02904_gb300 import shard
+    rng = np.random.Generator(np.random.Philox(7))
+    sizes = rng.integers(64, 4097, size=256)
+    for world in (1, 2, 3, 8):
+        parts = shard.partition(shard.system_cost(sizes), world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(sizes.size))
+        loads = [shard.system_cost(sizes[p]).sum() for p in parts]
+        # LPT bound: max load <= mean + largest item
+        assert max(loads) <= sum(loads) / world + shard.system_cost(sizes.max())
+
+
+def _grad_worker(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    from paper_1607_02904_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g = torch.arange(8, dtype=torch.float64) * (rank + 1)
+        loss = torch.tensor([10.0 * (rank + 1)], dtype=torch.float64)
+        shard.allreduce_sum(g, loss)
+        out[rank] = (g.tolist(), loss.item())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gradient_allreduce_two_ranks():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_grad_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    for rank in range(world):
+        g, loss = out[rank]
+        assert g == [3.0 * k for k in range(8)]
+        assert loss == 30.0
