@@ -39,7 +39,6 @@ using fwd::SelfPos;
 using fwd::self_pos;
 using fwd::to_f64;
 
-constexpr int BLOCK = 128;
 constexpr int NP = TERSOFF_NPARAM;
 
 template <class T> struct BwdArgs {
@@ -217,17 +216,181 @@ __device__ __forceinline__ T rec_val(const T* raw, int rec, int f) {
   return raw[rec * NP + f];
 }
 
+// ------------------------------------------------------------------ bonds
+// One neighbour k of the centre atom: unit vector u, length r, the rate of r
+// along w (rd = u . w), p = (w - u rd) / r (the rate of cos(theta_jk) is
+// p_j . u_k + p_k . u_j) and the species.
+template <class T> struct BondD {
+  T ux, uy, uz, r, rd, px, py, pz;
+  int t;
+};
+
+// Bonds inside the filter radius are cached per thread in dynamic shared
+// memory, slot-major with the thread index innermost (no bank conflicts):
+// ZB slots of 9 words. Atoms with more bonds inside recompute them from the
+// skin list in every loop.
+constexpr int ZB = 8;
+constexpr int SLOT_WORDS = 9;
+template <class T> struct BwdBlock;
+template <> struct BwdBlock<float> { static constexpr int size = 128; };
+template <> struct BwdBlock<double> { static constexpr int size = 64; };
+template <class T>
+constexpr size_t slot_bytes() { return (size_t)BwdBlock<T>::size * ZB * SLOT_WORDS * sizeof(T); }
+
+template <class T>
+__device__ __forceinline__ void put_slot(T* sh, int q, const BondD<T>& b) {
+  const int B = blockDim.x;
+  T* p = sh + (size_t)q * SLOT_WORDS * B + threadIdx.x;
+  p[0] = b.ux;
+  p[B] = b.uy;
+  p[2 * B] = b.uz;
+  p[3 * B] = b.r;
+  p[4 * B] = b.rd;
+  p[5 * B] = b.px;
+  p[6 * B] = b.py;
+  p[7 * B] = b.pz;
+  p[8 * B] = T(b.t);
+}
+template <class T>
+__device__ __forceinline__ void get_slot(const T* sh, int q, BondD<T>& b) {
+  const int B = blockDim.x;
+  const T* p = sh + (size_t)q * SLOT_WORDS * B + threadIdx.x;
+  b.ux = p[0];
+  b.uy = p[B];
+  b.uz = p[2 * B];
+  b.r = p[3 * B];
+  b.rd = p[4 * B];
+  b.px = p[5 * B];
+  b.py = p[6 * B];
+  b.pz = p[7 * B];
+  b.t = (int)p[8 * B];
+}
+
+// The adjoint of L_i over the neighbourhood given by get(q, bond) for
+// q < count (get returns false for a bond outside the filter radius), in
+// Algorithm 2's loop order.
+template <class T, int NS, class AccT, class Get>
+__device__ __forceinline__ void atom_adjoint(const T* sraw, int ns, int ti, T hE, int count,
+                                             Get get, AccT& acc, double* sgrad) {
+  for (int qj = 0; qj < count; ++qj) {
+    BondD<T> bj;
+    if (!get(qj, bj)) continue;
+    const int tj = bj.t;
+    const int p = NS == 1 ? 0 : (ti * ns + tj) * ns + tj;
+    const T Rp = rec_val(sraw, p, TERSOFF_P_R), Dp = rec_val(sraw, p, TERSOFF_P_D_CUT);
+    const T rj = bj.r, rdj = bj.rd;
+    if (!(rj < Rp + Dp)) continue;
+    // first K loop: zeta_ij and its rate along w
+    T zeta = T(0), zd = T(0);
+    for (int qk = 0; qk < count; ++qk) {
+      if (qk == qj) continue;
+      BondD<T> bk;
+      if (!get(qk, bk)) continue;
+      const int q = NS == 1 ? 0 : (ti * ns + tj) * ns + bk.t;
+      const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
+      const T rk = bk.r, rdk = bk.rd;
+      if (!(rk < Rq + Dq)) continue;
+      const T cs = bj.ux * bk.ux + bj.uy * bk.uy + bj.uz * bk.uz;
+      const T csd = (bj.px * bk.ux + bj.py * bk.uy + bj.pz * bk.uz) +
+                    (bk.px * bj.ux + bk.py * bj.uy + bk.pz * bj.uz);
+      const Cut<T> fk = cutoff_ad<T>(rk, Rq, Dq);
+      const Ang<T> an = angular_ad<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA),
+                                      rec_val(sraw, q, TERSOFF_P_C),
+                                      rec_val(sraw, q, TERSOFF_P_D),
+                                      rec_val(sraw, q, TERSOFF_P_H));
+      const Expo<T> ex = expo_ad<T>(rj - rk, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
+                                    (int)rec_val(sraw, q, TERSOFF_P_M));
+      zeta += fk.fc * an.g * ex.x;
+      zd += fk.dfc * rdk * an.g * ex.x + fk.fc * an.dg * csd * ex.x +
+            fk.fc * an.g * ex.dx * (rdj - rdk);
+    }
+    // pair level
+    const Cut<T> fj = cutoff_ad<T>(rj, Rp, Dp);
+    const T A = rec_val(sraw, p, TERSOFF_P_A), l1 = rec_val(sraw, p, TERSOFF_P_LAMBDA1);
+    const T B = rec_val(sraw, p, TERSOFF_P_B), l2 = rec_val(sraw, p, TERSOFF_P_LAMBDA2);
+    const T e1 = BM<T>::ex(-l1 * rj), e2 = BM<T>::ex(-l2 * rj);
+    const T Ae1 = A * e1, Be2 = B * e2;
+    const T Pv = fj.fc * Ae1;
+    const T Pd = (fj.dfc - l1 * fj.fc) * Ae1;
+    const T Qv = -fj.fc * Be2;
+    const T Qd = -(fj.dfc - l2 * fj.fc) * Be2;
+    const Bo<T> bo = bond_ad<T>(zeta, rec_val(sraw, p, TERSOFF_P_BETA),
+                                rec_val(sraw, p, TERSOFF_P_N));
+    // L_j = gE/2 (P + b Q) - 1/2 (P' + b Q') rd_j - 1/2 Q b' zeta_rate
+    const T Pbar = hE;
+    const T Pdbar = -T(0.5) * rdj;
+    const T Qbar = hE * bo.b - T(0.5) * bo.db * zd;
+    const T Qdbar = -T(0.5) * bo.b * rdj;
+    const T bbar = hE * Qv - T(0.5) * Qd * rdj;
+    const T dbbar = -T(0.5) * Qv * zd;
+    acc.add(sgrad, p, TERSOFF_P_A, to_f64(Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
+    acc.add(sgrad, p, TERSOFF_P_LAMBDA1,
+            to_f64(Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
+    acc.add(sgrad, p, TERSOFF_P_B, to_f64(Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
+    acc.add(sgrad, p, TERSOFF_P_LAMBDA2,
+            to_f64(Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
+    acc.add(sgrad, p, TERSOFF_P_R,
+            to_f64((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
+                   (Qbar * fj.fc_R + Qdbar * (fj.dfc_R - l2 * fj.fc_R)) * Be2));
+    acc.add(sgrad, p, TERSOFF_P_D_CUT,
+            to_f64((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
+                   (Qbar * fj.fc_D + Qdbar * (fj.dfc_D - l2 * fj.fc_D)) * Be2));
+    acc.add(sgrad, p, TERSOFF_P_BETA, to_f64(bbar * bo.b_be + dbbar * bo.db_be));
+    acc.add(sgrad, p, TERSOFF_P_N, to_f64(bbar * bo.b_n + dbbar * bo.db_n));
+    const T zbar = bbar * bo.db + dbbar * bo.ddb;
+    const T zdbar = -T(0.5) * Qv * bo.db;
+    if (zbar == T(0) && zdbar == T(0)) continue;
+    // second K loop: recompute each three-body term, adjoints of its parameters
+    for (int qk = 0; qk < count; ++qk) {
+      if (qk == qj) continue;
+      BondD<T> bk;
+      if (!get(qk, bk)) continue;
+      const int q = NS == 1 ? 0 : (ti * ns + tj) * ns + bk.t;
+      const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
+      const T rk = bk.r, rdk = bk.rd;
+      if (!(rk < Rq + Dq)) continue;
+      const T cs = bj.ux * bk.ux + bj.uy * bk.uy + bj.uz * bk.uz;
+      const T csd = (bj.px * bk.ux + bj.py * bk.uy + bj.pz * bk.uz) +
+                    (bk.px * bj.ux + bk.py * bj.uy + bk.pz * bj.uz);
+      const Cut<T> fk = cutoff_ad<T>(rk, Rq, Dq);
+      const Ang<T> an = angular_ad<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA),
+                                      rec_val(sraw, q, TERSOFF_P_C),
+                                      rec_val(sraw, q, TERSOFF_P_D),
+                                      rec_val(sraw, q, TERSOFF_P_H));
+      const T dl = rj - rk, dld = rdj - rdk;
+      const Expo<T> ex = expo_ad<T>(dl, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
+                                    (int)rec_val(sraw, q, TERSOFF_P_M));
+      // T = F3 G X ; T_rate = F3' rd_k G X + F3 G' cs_rate X + F3 G X' dl_rate
+      const T F3bar = zbar * an.g * ex.x + zdbar * (an.dg * csd * ex.x + an.g * ex.dx * dld);
+      const T F3dbar = zdbar * rdk * an.g * ex.x;
+      const T Gbar = zbar * fk.fc * ex.x + zdbar * (fk.dfc * rdk * ex.x + fk.fc * ex.dx * dld);
+      const T Gdbar = zdbar * fk.fc * csd * ex.x;
+      const T Xbar = zbar * fk.fc * an.g + zdbar * (fk.dfc * rdk * an.g + fk.fc * an.dg * csd);
+      const T Xdbar = zdbar * fk.fc * an.g * dld;
+      acc.add(sgrad, q, TERSOFF_P_R, to_f64(F3bar * fk.fc_R + F3dbar * fk.dfc_R));
+      acc.add(sgrad, q, TERSOFF_P_D_CUT, to_f64(F3bar * fk.fc_D + F3dbar * fk.dfc_D));
+      acc.add(sgrad, q, TERSOFF_P_GAMMA, to_f64(Gbar * an.g_ga + Gdbar * an.dg_ga));
+      acc.add(sgrad, q, TERSOFF_P_C, to_f64(Gbar * an.g_c + Gdbar * an.dg_c));
+      acc.add(sgrad, q, TERSOFF_P_D, to_f64(Gbar * an.g_d + Gdbar * an.dg_d));
+      acc.add(sgrad, q, TERSOFF_P_H, to_f64(Gbar * an.g_h + Gdbar * an.dg_h));
+      acc.add(sgrad, q, TERSOFF_P_LAMBDA3, to_f64(Xbar * ex.x_l + Xdbar * ex.dx_l));
+    }
+  }
+}
+
 // ------------------------------------------------------------------ the kernel
 template <class T, int NS, bool BATCH>
-__global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ BwdArgs<T> a) {
+__global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_constant__ BwdArgs<T> a) {
   constexpr int SNS = NS == 1 ? 1 : TERSOFF_MAX_SPECIES;
   __shared__ T sraw[SNS * SNS * SNS * NP];
   __shared__ T sfilt[SNS * SNS];
   __shared__ double sgrad[SNS * SNS * SNS * NP];
+  extern __shared__ __align__(16) unsigned char bwd_dyn[];
+  T* slots = reinterpret_cast<T*>(bwd_dyn);
   const fwd::FwdArgs<T>& g = a.g;
   const int ns = NS == 1 ? 1 : g.ns;
   const int nrec = ns * ns * ns;
-  for (int q = threadIdx.x; q < nrec * NP; q += BLOCK) {
+  for (int q = threadIdx.x; q < nrec * NP; q += blockDim.x) {
     sraw[q] = a.raw[q];
     sgrad[q] = 0.0;
   }
@@ -236,7 +399,7 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ B
 
   Acc<NS == 1 ? 1 : 0> acc;
   acc.init(sgrad);
-  const int i = blockIdx.x * BLOCK + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < g.n) {
     using P = typename SelfPos<T>::type;
     const P pi = self_pos<T>(g, i);
@@ -253,140 +416,52 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_bwd(const __grid_constant__ B
       gfi2 = a.gF[3 * (size_t)i + 2];
     }
     const T hE = T(0.5) * T(gE);
-    // bond j of the list: vector, length, unit vector, w and the rate of r
-    auto bond = [&](int s, T& ux, T& uy, T& uz, T& r, T& wx, T& wy, T& wz, T& rd, int& tj,
-                    bool& inside) {
+    // skin-list entry s: bond data; false when outside the filter radius
+    auto from_list = [&](int s, BondD<T>& b) -> bool {
       T dx, dy, dz;
       int j;
-      Bond<T>::vec(g, sh, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, tj);
+      Bond<T>::vec(g, sh, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, b.t);
       const T r2 = dx * dx + dy * dy + dz * dz;
-      inside = r2 <= sfilt[ti * ns + tj];
-      r = BM<T>::sq(r2);
-      const T ir = T(1) / r;
-      ux = dx * ir;
-      uy = dy * ir;
-      uz = dz * ir;
-      wx = wy = wz = T(0);
+      if (!(r2 <= sfilt[ti * ns + b.t])) return false;
+      b.r = BM<T>::sq(r2);
+      const T ir = T(1) / b.r;
+      b.ux = dx * ir;
+      b.uy = dy * ir;
+      b.uz = dz * ir;
+      T wx = T(0), wy = T(0), wz = T(0);
       if (hasF) {
         wx = T(a.gF[3 * (size_t)j] - gfi0);
         wy = T(a.gF[3 * (size_t)j + 1] - gfi1);
         wz = T(a.gF[3 * (size_t)j + 2] - gfi2);
       }
-      rd = ux * wx + uy * wy + uz * wz;
+      b.rd = b.ux * wx + b.uy * wy + b.uz * wz;
+      b.px = (wx - b.ux * b.rd) * ir;
+      b.py = (wy - b.uy * b.rd) * ir;
+      b.pz = (wz - b.uz * b.rd) * ir;
+      return true;
     };
-    for (int sj = 0; sj < c; ++sj) {
-      T uxj, uyj, uzj, rj, wxj, wyj, wzj, rdj;
-      int tj;
-      bool inj;
-      bond(sj, uxj, uyj, uzj, rj, wxj, wyj, wzj, rdj, tj, inj);
-      if (!inj) continue;
-      const int p = NS == 1 ? 0 : (ti * ns + tj) * ns + tj;
-      const T Rp = rec_val(sraw, p, TERSOFF_P_R), Dp = rec_val(sraw, p, TERSOFF_P_D_CUT);
-      if (!(rj < Rp + Dp)) continue;
-      // first K loop: zeta_ij and its rate along w
-      T zeta = T(0), zd = T(0);
-      for (int sk = 0; sk < c; ++sk) {
-        if (sk == sj) continue;
-        T uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk;
-        int tk;
-        bool ink;
-        bond(sk, uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk, tk, ink);
-        if (!ink) continue;
-        const int q = NS == 1 ? 0 : (ti * ns + tj) * ns + tk;
-        const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
-        if (!(rk < Rq + Dq)) continue;
-        const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
-        const T csd = ((wxj - uxj * rdj) * uxk + (wyj - uyj * rdj) * uyk + (wzj - uzj * rdj) * uzk) / rj +
-                      ((wxk - uxk * rdk) * uxj + (wyk - uyk * rdk) * uyj + (wzk - uzk * rdk) * uzj) / rk;
-        const Cut<T> fk = cutoff_ad<T>(rk, Rq, Dq);
-        const Ang<T> an = angular_ad<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA),
-                                        rec_val(sraw, q, TERSOFF_P_C),
-                                        rec_val(sraw, q, TERSOFF_P_D),
-                                        rec_val(sraw, q, TERSOFF_P_H));
-        const Expo<T> ex = expo_ad<T>(rj - rk, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
-                                      (int)rec_val(sraw, q, TERSOFF_P_M));
-        zeta += fk.fc * an.g * ex.x;
-        zd += fk.dfc * rdk * an.g * ex.x + fk.fc * an.dg * csd * ex.x +
-              fk.fc * an.g * ex.dx * (rdj - rdk);
-      }
-      // pair level
-      const Cut<T> fj = cutoff_ad<T>(rj, Rp, Dp);
-      const T A = rec_val(sraw, p, TERSOFF_P_A), l1 = rec_val(sraw, p, TERSOFF_P_LAMBDA1);
-      const T B = rec_val(sraw, p, TERSOFF_P_B), l2 = rec_val(sraw, p, TERSOFF_P_LAMBDA2);
-      const T e1 = BM<T>::ex(-l1 * rj), e2 = BM<T>::ex(-l2 * rj);
-      const T Ae1 = A * e1, Be2 = B * e2;
-      const T Pv = fj.fc * Ae1;
-      const T Pd = (fj.dfc - l1 * fj.fc) * Ae1;
-      const T Qv = -fj.fc * Be2;
-      const T Qd = -(fj.dfc - l2 * fj.fc) * Be2;
-      const Bo<T> bo = bond_ad<T>(zeta, rec_val(sraw, p, TERSOFF_P_BETA),
-                                  rec_val(sraw, p, TERSOFF_P_N));
-      // L_j = gE/2 (P + b Q) - 1/2 (P' + b Q') rd_j - 1/2 Q b' zeta_rate
-      const T Pbar = hE;
-      const T Pdbar = -T(0.5) * rdj;
-      const T Qbar = hE * bo.b - T(0.5) * bo.db * zd;
-      const T Qdbar = -T(0.5) * bo.b * rdj;
-      const T bbar = hE * Qv - T(0.5) * Qd * rdj;
-      const T dbbar = -T(0.5) * Qv * zd;
-      acc.add(sgrad, p, TERSOFF_P_A, to_f64(Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
-      acc.add(sgrad, p, TERSOFF_P_LAMBDA1,
-              to_f64(Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
-      acc.add(sgrad, p, TERSOFF_P_B, to_f64(Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
-      acc.add(sgrad, p, TERSOFF_P_LAMBDA2,
-              to_f64(Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
-      acc.add(sgrad, p, TERSOFF_P_R,
-              to_f64((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
-                     (Qbar * fj.fc_R + Qdbar * (fj.dfc_R - l2 * fj.fc_R)) * Be2));
-      acc.add(sgrad, p, TERSOFF_P_D_CUT,
-              to_f64((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
-                     (Qbar * fj.fc_D + Qdbar * (fj.dfc_D - l2 * fj.fc_D)) * Be2));
-      acc.add(sgrad, p, TERSOFF_P_BETA, to_f64(bbar * bo.b_be + dbbar * bo.db_be));
-      acc.add(sgrad, p, TERSOFF_P_N, to_f64(bbar * bo.b_n + dbbar * bo.db_n));
-      const T zbar = bbar * bo.db + dbbar * bo.ddb;
-      const T zdbar = -T(0.5) * Qv * bo.db;
-      if (zbar == T(0) && zdbar == T(0)) continue;
-      // second K loop: recompute each three-body term, adjoints of its parameters
-      for (int sk = 0; sk < c; ++sk) {
-        if (sk == sj) continue;
-        T uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk;
-        int tk;
-        bool ink;
-        bond(sk, uxk, uyk, uzk, rk, wxk, wyk, wzk, rdk, tk, ink);
-        if (!ink) continue;
-        const int q = NS == 1 ? 0 : (ti * ns + tj) * ns + tk;
-        const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
-        if (!(rk < Rq + Dq)) continue;
-        const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
-        const T csd = ((wxj - uxj * rdj) * uxk + (wyj - uyj * rdj) * uyk + (wzj - uzj * rdj) * uzk) / rj +
-                      ((wxk - uxk * rdk) * uxj + (wyk - uyk * rdk) * uyj + (wzk - uzk * rdk) * uzj) / rk;
-        const Cut<T> fk = cutoff_ad<T>(rk, Rq, Dq);
-        const Ang<T> an = angular_ad<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA),
-                                        rec_val(sraw, q, TERSOFF_P_C),
-                                        rec_val(sraw, q, TERSOFF_P_D),
-                                        rec_val(sraw, q, TERSOFF_P_H));
-        const T dl = rj - rk, dld = rdj - rdk;
-        const Expo<T> ex = expo_ad<T>(dl, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
-                                      (int)rec_val(sraw, q, TERSOFF_P_M));
-        // T = F3 G X ; T_rate = F3' rd_k G X + F3 G' cs_rate X + F3 G X' dl_rate
-        const T F3bar = zbar * an.g * ex.x + zdbar * (an.dg * csd * ex.x + an.g * ex.dx * dld);
-        const T F3dbar = zdbar * rdk * an.g * ex.x;
-        const T Gbar = zbar * fk.fc * ex.x + zdbar * (fk.dfc * rdk * ex.x + fk.fc * ex.dx * dld);
-        const T Gdbar = zdbar * fk.fc * csd * ex.x;
-        const T Xbar = zbar * fk.fc * an.g + zdbar * (fk.dfc * rdk * an.g + fk.fc * an.dg * csd);
-        const T Xdbar = zdbar * fk.fc * an.g * dld;
-        acc.add(sgrad, q, TERSOFF_P_R, to_f64(F3bar * fk.fc_R + F3dbar * fk.dfc_R));
-        acc.add(sgrad, q, TERSOFF_P_D_CUT, to_f64(F3bar * fk.fc_D + F3dbar * fk.dfc_D));
-        acc.add(sgrad, q, TERSOFF_P_GAMMA, to_f64(Gbar * an.g_ga + Gdbar * an.dg_ga));
-        acc.add(sgrad, q, TERSOFF_P_C, to_f64(Gbar * an.g_c + Gdbar * an.dg_c));
-        acc.add(sgrad, q, TERSOFF_P_D, to_f64(Gbar * an.g_d + Gdbar * an.dg_d));
-        acc.add(sgrad, q, TERSOFF_P_H, to_f64(Gbar * an.g_h + Gdbar * an.dg_h));
-        acc.add(sgrad, q, TERSOFF_P_LAMBDA3, to_f64(Xbar * ex.x_l + Xdbar * ex.dx_l));
-      }
+    // cache the bonds inside the filter radius when they fit
+    int z = 0;
+    for (int s = 0; s < c && z <= ZB; ++s) {
+      BondD<T> b;
+      if (!from_list(s, b)) continue;
+      if (z < ZB) put_slot<T>(slots, z, b);
+      ++z;
+    }
+    if (z <= ZB) {
+      atom_adjoint<T, NS>(sraw, ns, ti, hE, z,
+                          [&](int q, BondD<T>& b) -> bool {
+                            get_slot<T>(slots, q, b);
+                            return true;
+                          },
+                          acc, sgrad);
+    } else {
+      atom_adjoint<T, NS>(sraw, ns, ti, hE, c, from_list, acc, sgrad);
     }
   }
   acc.flush(sgrad);
   __syncthreads();
-  for (int q = threadIdx.x; q < nrec * NP; q += BLOCK)
+  for (int q = threadIdx.x; q < nrec * NP; q += blockDim.x)
     if (sgrad[q] != 0.0) atomicAdd(&a.grad[q], sgrad[q]);
 }
 
@@ -430,14 +505,16 @@ int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* g
   a.atom_cell = c->n_sys > 0 ? c->d_atom_sys : nullptr;
   a.gF = gF;
   a.grad = grad;
-  const int grid = (c->n + BLOCK - 1) / BLOCK;
+  constexpr int B = BwdBlock<T>::size;
+  constexpr size_t dyn = slot_bytes<T>();
+  const int grid = (c->n + B - 1) / B;
   if (grid > 0) {
-    if (c->n_sys > 0)
-      k_tersoff_bwd<T, 0, true><<<grid, BLOCK, 0, s>>>(a);
-    else if (c->ns == 1)
-      k_tersoff_bwd<T, 1, false><<<grid, BLOCK, 0, s>>>(a);
-    else
-      k_tersoff_bwd<T, 0, false><<<grid, BLOCK, 0, s>>>(a);
+    void (*k)(BwdArgs<T>) = c->n_sys > 0   ? k_tersoff_bwd<T, 0, true>
+                            : c->ns == 1 ? k_tersoff_bwd<T, 1, false>
+                                         : k_tersoff_bwd<T, 0, false>;
+    // static parameter tables plus the bond slots exceed the default 48 KB
+    TGB_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    k<<<grid, B, dyn, s>>>(a);
     c->launches++;
   }
   TGB_CUDA(c, cudaGetLastError());
