@@ -122,6 +122,7 @@ int ensure_atoms(Ctx* c, int n) {
   if ((st = dev_alloc(c, &c->d_posq, m))) return st;
   if ((st = dev_alloc(c, &c->d_pos64, m))) return st;
   if ((st = dev_alloc(c, &c->d_fbuf, 3 * m))) return st;
+  if ((st = dev_alloc(c, &c->d_gf32, 3 * m))) return st;
   if ((st = dev_alloc(c, &c->d_qorg, 3 * m))) return st;
   if ((st = dev_alloc(c, &c->d_qref, m))) return st;
   if ((st = dev_alloc(c, &c->d_zcnt, m))) return st;
@@ -303,7 +304,7 @@ int tersoff_destroy(tersoff_ctx* p) {
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
                   c->d_bucket, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
                   c->d_extra, c->d_geo, c->d_sys, c->d_atom_sys, c->d_sys_off, c->d_vatom,
-                  c->d_eatom};
+                  c->d_eatom, c->d_gf32};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->h_flags) cudaFreeHost(c->h_flags);

@@ -188,6 +188,7 @@ struct Ctx {
   double* d_vatom = nullptr;      // n x 6 per-atom virial
   double* d_eatom = nullptr;      // n per-atom energy
   double* d_fbuf = nullptr;       // scratch forces (n x 3) for calls without output
+  float* d_gf32 = nullptr;        // n x 3: force weights of the backward pass in float
   double* d_stage = nullptr;      // host-call staging: x, v, f (3 x n x 3)
   double* d_thermo = nullptr;     // host-call staging thermo
   size_t stage_alloc = 0;

@@ -46,8 +46,10 @@ template <class T> struct BwdArgs {
   const T* raw;           // ns^3 raw records (table layout)
   const double* gE;       // energy weight(s): gE[cell(i)]
   const int* atom_cell;   // optional: cell of each atom (NULL: one cell)
-  const double* gF;       // optional: N x 3 force weights
+  const T* gF;            // optional: N x 3 force weights, in T
   double* grad;           // ns^3 x NP, accumulated
+  const int* order;       // atoms by bucket (bonds inside the cutoffs: <= 4, <= 8, more) ...
+  const int* counts;      // ... and the three bucket sizes (device, FLAG_STRIDE apart)
 };
 
 // ------------------------------------------------------------------ math
@@ -184,17 +186,19 @@ __device__ __forceinline__ Bo<T> bond_ad(T zeta, T be, T n) {
 }
 
 // ------------------------------------------------------------------ accumulation
-// NS == 1: one record; gradients in registers, reduced per warp, per block.
+// NS == 1: one record; per-thread sums in double registers, reduced per warp.
+// NS == 2 (mixed path): the 4 records (ti, *, *) of the thread's centre
+// species in registers (T), reduced per warp once per centre species.
 // Otherwise: per-block shared accumulators with shared-memory atomics.
-template <int NS> struct Acc;
-template <> struct Acc<1> {
+template <int NS, class T> struct Acc;
+template <class T> struct Acc<1, T> {
   double v[NP];
-  __device__ __forceinline__ void init(double*) {
+  __device__ __forceinline__ void init() {
 #pragma unroll
     for (int q = 0; q < NP; ++q) v[q] = 0.0;
   }
-  __device__ __forceinline__ void add(double*, int, int f, double x) { v[f] += x; }
-  __device__ __forceinline__ void flush(double* sh) {
+  __device__ __forceinline__ void add(double*, int, int f, T x) { v[f] += to_f64(x); }
+  __device__ __forceinline__ void flush(double* sh, int) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       double s = v[q];
@@ -203,12 +207,42 @@ template <> struct Acc<1> {
     }
   }
 };
-template <> struct Acc<0> {
-  __device__ __forceinline__ void init(double*) {}
-  __device__ __forceinline__ void add(double* sh, int rec, int f, double x) {
-    if (x != 0.0) atomicAdd(&sh[rec * NP + f], x);
+template <class T> struct Acc<2, T> {
+  T v[4][NP];  // record (ti, tj, tk) at [2 tj + tk]; indices constant after unrolling
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < NP; ++q) v[r][q] = T(0);
   }
-  __device__ __forceinline__ void flush(double*) {}
+  __device__ __forceinline__ void add(double*, int rec, int f, T x) {
+    const int r = rec & 3;  // rec = 4 ti + 2 tj + tk
+    if (r == 0) v[0][f] += x;
+    else if (r == 1) v[1][f] += x;
+    else if (r == 2) v[2][f] += x;
+    else v[3][f] += x;
+  }
+  // all lanes; lanes without an atom hold zeros (ti 0)
+  __device__ __forceinline__ void flush(double* sh, int ti) {
+#pragma unroll
+    for (int tt = 0; tt < 2; ++tt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          double s = ti == tt ? to_f64(v[r][q]) : 0.0;
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&sh[(4 * tt + r) * NP + q], s);
+        }
+  }
+};
+template <class T> struct Acc<0, T> {
+  __device__ __forceinline__ void init() {}
+  __device__ __forceinline__ void add(double* sh, int rec, int f, T x) {
+    const double d = to_f64(x);
+    if (d != 0.0) atomicAdd(&sh[rec * NP + f], d);
+  }
+  __device__ __forceinline__ void flush(double*, int) {}
 };
 
 template <class T>
@@ -323,20 +357,16 @@ __device__ __forceinline__ void atom_adjoint(const T* sraw, int ns, int ti, T hE
     const T Qdbar = -T(0.5) * bo.b * rdj;
     const T bbar = hE * Qv - T(0.5) * Qd * rdj;
     const T dbbar = -T(0.5) * Qv * zd;
-    acc.add(sgrad, p, TERSOFF_P_A, to_f64(Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
-    acc.add(sgrad, p, TERSOFF_P_LAMBDA1,
-            to_f64(Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
-    acc.add(sgrad, p, TERSOFF_P_B, to_f64(Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
-    acc.add(sgrad, p, TERSOFF_P_LAMBDA2,
-            to_f64(Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
-    acc.add(sgrad, p, TERSOFF_P_R,
-            to_f64((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
+    acc.add(sgrad, p, TERSOFF_P_A, (Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
+    acc.add(sgrad, p, TERSOFF_P_LAMBDA1, (Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
+    acc.add(sgrad, p, TERSOFF_P_B, (Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
+    acc.add(sgrad, p, TERSOFF_P_LAMBDA2, (Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
+    acc.add(sgrad, p, TERSOFF_P_R, ((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
                    (Qbar * fj.fc_R + Qdbar * (fj.dfc_R - l2 * fj.fc_R)) * Be2));
-    acc.add(sgrad, p, TERSOFF_P_D_CUT,
-            to_f64((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
+    acc.add(sgrad, p, TERSOFF_P_D_CUT, ((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
                    (Qbar * fj.fc_D + Qdbar * (fj.dfc_D - l2 * fj.fc_D)) * Be2));
-    acc.add(sgrad, p, TERSOFF_P_BETA, to_f64(bbar * bo.b_be + dbbar * bo.db_be));
-    acc.add(sgrad, p, TERSOFF_P_N, to_f64(bbar * bo.b_n + dbbar * bo.db_n));
+    acc.add(sgrad, p, TERSOFF_P_BETA, (bbar * bo.b_be + dbbar * bo.db_be));
+    acc.add(sgrad, p, TERSOFF_P_N, (bbar * bo.b_n + dbbar * bo.db_n));
     const T zbar = bbar * bo.db + dbbar * bo.ddb;
     const T zdbar = -T(0.5) * Qv * bo.db;
     if (zbar == T(0) && zdbar == T(0)) continue;
@@ -367,13 +397,13 @@ __device__ __forceinline__ void atom_adjoint(const T* sraw, int ns, int ti, T hE
       const T Gdbar = zdbar * fk.fc * csd * ex.x;
       const T Xbar = zbar * fk.fc * an.g + zdbar * (fk.dfc * rdk * an.g + fk.fc * an.dg * csd);
       const T Xdbar = zdbar * fk.fc * an.g * dld;
-      acc.add(sgrad, q, TERSOFF_P_R, to_f64(F3bar * fk.fc_R + F3dbar * fk.dfc_R));
-      acc.add(sgrad, q, TERSOFF_P_D_CUT, to_f64(F3bar * fk.fc_D + F3dbar * fk.dfc_D));
-      acc.add(sgrad, q, TERSOFF_P_GAMMA, to_f64(Gbar * an.g_ga + Gdbar * an.dg_ga));
-      acc.add(sgrad, q, TERSOFF_P_C, to_f64(Gbar * an.g_c + Gdbar * an.dg_c));
-      acc.add(sgrad, q, TERSOFF_P_D, to_f64(Gbar * an.g_d + Gdbar * an.dg_d));
-      acc.add(sgrad, q, TERSOFF_P_H, to_f64(Gbar * an.g_h + Gdbar * an.dg_h));
-      acc.add(sgrad, q, TERSOFF_P_LAMBDA3, to_f64(Xbar * ex.x_l + Xdbar * ex.dx_l));
+      acc.add(sgrad, q, TERSOFF_P_R, (F3bar * fk.fc_R + F3dbar * fk.dfc_R));
+      acc.add(sgrad, q, TERSOFF_P_D_CUT, (F3bar * fk.fc_D + F3dbar * fk.dfc_D));
+      acc.add(sgrad, q, TERSOFF_P_GAMMA, (Gbar * an.g_ga + Gdbar * an.dg_ga));
+      acc.add(sgrad, q, TERSOFF_P_C, (Gbar * an.g_c + Gdbar * an.dg_c));
+      acc.add(sgrad, q, TERSOFF_P_D, (Gbar * an.g_d + Gdbar * an.dg_d));
+      acc.add(sgrad, q, TERSOFF_P_H, (Gbar * an.g_h + Gdbar * an.dg_h));
+      acc.add(sgrad, q, TERSOFF_P_LAMBDA3, (Xbar * ex.x_l + Xdbar * ex.dx_l));
     }
   }
 }
@@ -381,14 +411,14 @@ __device__ __forceinline__ void atom_adjoint(const T* sraw, int ns, int ti, T hE
 // ------------------------------------------------------------------ the kernel
 template <class T, int NS, bool BATCH>
 __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_constant__ BwdArgs<T> a) {
-  constexpr int SNS = NS == 1 ? 1 : TERSOFF_MAX_SPECIES;
+  constexpr int SNS = NS > 0 ? NS : TERSOFF_MAX_SPECIES;
   __shared__ T sraw[SNS * SNS * SNS * NP];
   __shared__ T sfilt[SNS * SNS];
   __shared__ double sgrad[SNS * SNS * SNS * NP];
   extern __shared__ __align__(16) unsigned char bwd_dyn[];
   T* slots = reinterpret_cast<T*>(bwd_dyn);
   const fwd::FwdArgs<T>& g = a.g;
-  const int ns = NS == 1 ? 1 : g.ns;
+  const int ns = NS > 0 ? NS : g.ns;
   const int nrec = ns * ns * ns;
   for (int q = threadIdx.x; q < nrec * NP; q += blockDim.x) {
     sraw[q] = a.raw[q];
@@ -397,19 +427,29 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
   if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = g.filt2[threadIdx.x];
   __syncthreads();
 
-  Acc<NS == 1 ? 1 : 0> acc;
-  acc.init(sgrad);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // atoms in bucket order: neighbouring lanes have similar neighbourhood sizes
+  __shared__ int nb[3];
+  if (threadIdx.x < 3) nb[threadIdx.x] = a.counts[threadIdx.x * FLAG_STRIDE];
+  __syncthreads();
+  Acc<NS, T> acc;
+  acc.init();
+  int ti = 0;
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n01 = nb[0] + nb[1];
+  const int i = item >= g.n ? g.n
+                : item < nb[0] ? a.order[item]
+                : item < n01   ? a.order[(size_t)g.n + item - nb[0]]
+                               : a.order[2 * (size_t)g.n + item - n01];
   if (i < g.n) {
     using P = typename SelfPos<T>::type;
     const P pi = self_pos<T>(g, i);
     fwd::Shift<T, BATCH> sh;
     sh.load(g, i);
-    const int ti = g.types[i];
+    ti = g.types[i];
     const int c = min(g.cnt[i], g.cap);
     const double gE = a.gE[a.atom_cell ? a.atom_cell[i] : 0];
     const bool hasF = a.gF != nullptr;
-    double gfi0 = 0.0, gfi1 = 0.0, gfi2 = 0.0;
+    T gfi0 = T(0), gfi1 = T(0), gfi2 = T(0);
     if (hasF) {
       gfi0 = a.gF[3 * (size_t)i];
       gfi1 = a.gF[3 * (size_t)i + 1];
@@ -430,9 +470,9 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
       b.uz = dz * ir;
       T wx = T(0), wy = T(0), wz = T(0);
       if (hasF) {
-        wx = T(a.gF[3 * (size_t)j] - gfi0);
-        wy = T(a.gF[3 * (size_t)j + 1] - gfi1);
-        wz = T(a.gF[3 * (size_t)j + 2] - gfi2);
+        wx = a.gF[3 * (size_t)j] - gfi0;
+        wy = a.gF[3 * (size_t)j + 1] - gfi1;
+        wz = a.gF[3 * (size_t)j + 2] - gfi2;
       }
       b.rd = b.ux * wx + b.uy * wy + b.uz * wz;
       b.px = (wx - b.ux * b.rd) * ir;
@@ -459,10 +499,15 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
       atom_adjoint<T, NS>(sraw, ns, ti, hE, c, from_list, acc, sgrad);
     }
   }
-  acc.flush(sgrad);
+  acc.flush(sgrad, ti);
   __syncthreads();
   for (int q = threadIdx.x; q < nrec * NP; q += blockDim.x)
     if (sgrad[q] != 0.0) atomicAdd(&a.grad[q], sgrad[q]);
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int m) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) out[t] = (float)in[t];
 }
 
 // grad_x = -gE F (in place: f holds F on entry); gE of the atom's system
@@ -475,6 +520,18 @@ __global__ void k_scale_forces(double* __restrict__ f, const double* __restrict_
 template <class T> const T* filt_ptr(Ctx* c);
 template <> inline const float* filt_ptr<float>(Ctx* c) { return c->d_filt32; }
 template <> inline const double* filt_ptr<double>(Ctx* c) { return c->d_filt64; }
+
+// force weights in T: the caller's doubles, or a float copy (mixed path)
+inline const double* weights_t(Ctx*, const double* gF, cudaStream_t, double*) { return gF; }
+inline const float* weights_t(Ctx* c, const double* gF, cudaStream_t s, float*) {
+  if (!gF) return nullptr;
+  const int m = 3 * c->n;
+  if (m > 0) {
+    k_to_float<<<(m + 255) / 256, 256, 0, s>>>(gF, c->d_gf32, m);
+    c->launches++;
+  }
+  return c->d_gf32;
+}
 
 template <class T>
 int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* grad,
@@ -503,14 +560,19 @@ int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* g
   a.raw = raw;
   a.gE = gE;
   a.atom_cell = c->n_sys > 0 ? c->d_atom_sys : nullptr;
-  a.gF = gF;
+  a.gF = weights_t(c, gF, s, (T*)nullptr);
+  a.order = c->d_bucket;
+  a.counts = c->d_flags + flag_bucket(0);
   a.grad = grad;
   constexpr int B = BwdBlock<T>::size;
   constexpr size_t dyn = slot_bytes<T>();
   const int grid = (c->n + B - 1) / B;
   if (grid > 0) {
-    void (*k)(BwdArgs<T>) = c->n_sys > 0   ? k_tersoff_bwd<T, 0, true>
+    // two species on the mixed path: register accumulators (NS = 2)
+    const bool two = c->ns == 2 && sizeof(T) == sizeof(float);
+    void (*k)(BwdArgs<T>) = c->n_sys > 0 ? (two ? k_tersoff_bwd<T, 2, true> : k_tersoff_bwd<T, 0, true>)
                             : c->ns == 1 ? k_tersoff_bwd<T, 1, false>
+                            : two        ? k_tersoff_bwd<T, 2, false>
                                          : k_tersoff_bwd<T, 0, false>;
     // static parameter tables plus the bond slots exceed the default 48 KB
     TGB_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
