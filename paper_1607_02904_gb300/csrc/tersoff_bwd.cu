@@ -261,15 +261,22 @@ template <class T> struct BondD {
 
 // Bonds inside the filter radius are cached per thread in dynamic shared
 // memory, slot-major with the thread index innermost (no bank conflicts):
-// ZB slots of 9 words. Atoms with more bonds inside recompute them from the
-// skin list in every loop.
-constexpr int ZB = 8;
+// slots of 9 words (12 slots in float, 8 in double). Atoms with more bonds
+// inside recompute them from the skin list in every loop.
 constexpr int SLOT_WORDS = 9;
 template <class T> struct BwdBlock;
-template <> struct BwdBlock<float> { static constexpr int size = 128; };
-template <> struct BwdBlock<double> { static constexpr int size = 64; };
+template <> struct BwdBlock<float> {
+  static constexpr int size = 128;
+  static constexpr int slots = 12;
+};
+template <> struct BwdBlock<double> {
+  static constexpr int size = 64;
+  static constexpr int slots = 8;
+};
 template <class T>
-constexpr size_t slot_bytes() { return (size_t)BwdBlock<T>::size * ZB * SLOT_WORDS * sizeof(T); }
+constexpr size_t slot_bytes() {
+  return (size_t)BwdBlock<T>::size * BwdBlock<T>::slots * SLOT_WORDS * sizeof(T);
+}
 
 template <class T>
 __device__ __forceinline__ void put_slot(T* sh, int q, const BondD<T>& b) {
@@ -481,6 +488,7 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
       return true;
     };
     // cache the bonds inside the filter radius when they fit
+    constexpr int ZB = BwdBlock<T>::slots;
     int z = 0;
     for (int s = 0; s < c && z <= ZB; ++s) {
       BondD<T> b;
