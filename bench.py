@@ -776,9 +776,28 @@ def run_reference(args):
 
 def run_profile_case(args):
     """The benchmark workload without timing, for profiler captures."""
+    import numpy as np
     import torch
     import workloads as W
     import paper_1607_02904_gb300 as T
+    if args.only == "backward-batch":
+        cells = W.batched_cells(n_cells=64)
+        off = np.cumsum([0] + [len(c[0]) for c in cells]).astype(np.int32)
+        x = np.concatenate([c[0] for c in cells])
+        t = np.concatenate([c[1] for c in cells]).astype(np.int32)
+        boxes = np.stack([c[2] for c in cells])
+        ctx = T.Context(T.MIXED if args.precision == "mixed" else T.FP64)
+        ctx.params(T.mix_tersoff89(*W.element_records(["Si", "C"])))
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        ctx.neighbor_build_batched(xd, torch.tensor(t, device="cuda"), off, boxes, R_LIST)
+        gE = torch.ones(len(cells), dtype=torch.float64, device="cuda")
+        gF = torch.ones_like(xd)
+        g = torch.empty(14 * 8, dtype=torch.float64, device="cuda")
+        for _ in range(args.steps):
+            ctx.backward(xd, gE, gF, None, g)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
     if args.only == "force-sic":
         x, t, box, names = W.config_sic()
         v = None
@@ -795,9 +814,14 @@ def run_profile_case(args):
     ctx.neighbor_build(xd, td, box, R_LIST)
     fd = torch.zeros_like(xd)
     e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gE = torch.ones(1, dtype=torch.float64, device="cuda")
+    gF = torch.ones_like(xd)
+    g = torch.empty(table.size, dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
         if args.only in ("force", "force-sic"):
             ctx.compute(xd, e, fd)
+        elif args.only == "backward":
+            ctx.backward(xd, gE, gF, None, g)
         else:
             ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
     torch.cuda.synchronize()
@@ -813,10 +837,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the single-evaluation workloads and the backward timing")
-    ap.add_argument("--only", choices=["force", "md", "force-sic"], default=None,
-                    help="profiling case: K force evaluations (or K MD rebuild periods) of "
-                         "the benchmark workload, or K force evaluations of the 2.1M-atom "
-                         "SiC workload; nothing printed")
+    ap.add_argument("--only", choices=["force", "md", "force-sic", "backward", "backward-batch"],
+                    default=None,
+                    help="profiling case: K force evaluations, K MD rebuild periods or K "
+                         "backward passes of the benchmark workload, K force evaluations of "
+                         "the 2.1M-atom SiC workload, or K backward passes of 64 packing "
+                         "cells; nothing printed")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--scatter", choices=["gather", "atomic"], default="gather")
     args = ap.parse_args()

@@ -186,24 +186,27 @@ __device__ __forceinline__ Bo<T> bond_ad(T zeta, T be, T n) {
 }
 
 // ------------------------------------------------------------------ accumulation
-// NS == 1: one record; per-thread sums in double registers, reduced per warp.
-// NS == 2 (mixed path): the 4 records (ti, *, *) of the thread's centre
-// species in registers (T), reduced per warp once per centre species.
-// Otherwise: per-block shared accumulators with shared-memory atomics.
+// Per-thread sums are kept in T (one atom's terms: a few dozen per field) and
+// summed over the warp in T; the warp totals go to the block and global sums
+// in double. On the mixed path this keeps the FP64 pipe out of the loops (a
+// depth-5 float tree adds ~3e-7 relative error to a warp's total).
+// NS == 1: one record. NS == 2 (mixed path): the 4 records (ti, *, *) of the
+// thread's centre species, summed once per centre species. Otherwise:
+// per-block shared accumulators with shared-memory atomics.
 template <int NS, class T> struct Acc;
 template <class T> struct Acc<1, T> {
-  double v[NP];
+  T v[NP];
   __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int q = 0; q < NP; ++q) v[q] = 0.0;
+    for (int q = 0; q < NP; ++q) v[q] = T(0);
   }
-  __device__ __forceinline__ void add(double*, int, int f, T x) { v[f] += to_f64(x); }
+  __device__ __forceinline__ void add(double*, int, int f, T x) { v[f] += x; }
   __device__ __forceinline__ void flush(double* sh, int) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      double s = v[q];
+      T s = v[q];
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if ((threadIdx.x & 31) == 0) atomicAdd(&sh[q], s);
+      if ((threadIdx.x & 31) == 0 && s != T(0)) atomicAdd(&sh[q], to_f64(s));
     }
   }
 };
@@ -230,9 +233,10 @@ template <class T> struct Acc<2, T> {
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
-          double s = ti == tt ? to_f64(v[r][q]) : 0.0;
+          T s = ti == tt ? v[r][q] : T(0);
           for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-          if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(&sh[(4 * tt + r) * NP + q], s);
+          if ((threadIdx.x & 31) == 0 && s != T(0))
+            atomicAdd(&sh[(4 * tt + r) * NP + q], to_f64(s));
         }
   }
 };
