@@ -823,11 +823,12 @@ static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
     // opening half kick (merged with the previous step's closing one), drift
     double* ke_row =
         (rows && step > 0) ? rows + tgb::ACC_LEN * (size_t)(step - 1) + 7 * tgb::ACC_STRIDE : nullptr;
-    double* acc = rows ? rows + tgb::ACC_LEN * (size_t)step : c->d_acc;
+    // energy and virial only when thermo rows are requested
+    double* acc = rows ? rows + tgb::ACC_LEN * (size_t)step : nullptr;
     {
       tgb::TimedRegion tr(c, 2, s);
       if ((st = tgb::launch_md_step(c, x, v, f, dt, step == 0 ? 1 : 2, !rebuild, ke_row,
-                                    rows ? nullptr : c->d_acc, s)))
+                                    nullptr, s)))
         return st;
     }
     if (rebuild) {

@@ -149,7 +149,8 @@ int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
 // energy and virial for the per-system sums.
 template <class T>
 int launch_batch(Ctx* c, double* f, cudaStream_t s) {
-  FwdArgs<T> a = make_args<T>(c, f, c->d_acc, c->d_eatom);
+  // energy and virial come from the per-atom stores: no block reduction
+  FwdArgs<T> a = make_args<T>(c, f, nullptr, c->d_eatom);
   const int grid = force_grid(c, 8);
   if (grid > 0) {
     if (c->has_lam3)

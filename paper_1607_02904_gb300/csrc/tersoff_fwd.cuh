@@ -163,7 +163,7 @@ template <class T> struct FwdArgs {
   void* own;             // per-atom force of its own terms (T4)
   int atomic_mode;       // scatter every force with FP64 atomics (no slots)
   double* f;             // fallback forces, accumulated atomically
-  double* acc;           // energy, virial (6)
+  double* acc;           // energy, virial (6); NULL: not needed (no reduction)
   double* eatom;         // optional per-atom energy
   int* flags;
   // batches of independent systems (kernels instantiated with BATCH)
@@ -876,7 +876,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (__syncthreads_or(any)) block_reduce_store<T>(ei, w, a.acc);
+  if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T>(ei, w, a.acc);
 }
 
 }  // namespace fwd
