@@ -15,6 +15,28 @@ template <class T> const T* filt_ptr(Ctx* c);
 template <> inline const float* filt_ptr<float>(Ctx* c) { return c->d_filt32; }
 template <> inline const double* filt_ptr<double>(Ctx* c) { return c->d_filt64; }
 
+// Atoms with more than 8 bonds inside the cutoffs (bucket 2), when they are
+// over 0.5% of the atoms (e.g. SiC): the slot-cached wide kernel, on the
+// launch's stream after the main launch. A grid of a few waves loops over the
+// bucket (its size lives on the device).
+template <class T, int NS>
+void launch_wide(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
+  FwdArgs<T> b2 = a;
+  b2.order = c->d_bucket + 2 * (size_t)c->n;
+  b2.n_items = c->d_flags + flag_bucket(2);
+  b2.order2 = b2.order3 = nullptr;
+  b2.n_items2 = b2.n_items3 = nullptr;
+  b2.identity = 0;
+  const size_t dyn = wide_slot_bytes(sizeof(T));
+  const int cap = (c->n_sm > 0 ? c->n_sm : 152) * 8;
+  const int need = (c->nbucket[2] + WIDE_BLOCK - 1) / WIDE_BLOCK + 1;
+  const int grid = need < cap ? need : cap;
+  void (*k)(FwdArgs<T>) = c->has_lam3 ? k_tersoff_wide<T, NS, true> : k_tersoff_wide<T, NS, false>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  k<<<grid, WIDE_BLOCK, dyn, s>>>(b2);
+  c->launches++;
+}
+
 // Grids are fixed by the atom count (the bucket sizes live on the device), so
 // the launches can be captured in a CUDA graph and replayed across builds.
 template <class T, int NS, int ZC>
@@ -69,19 +91,21 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
     launch_t<T, NS, 8>(c, b1, force_grid(c, 8), s2);
   }
   // bucket 0, then bucket 1 (unless split off), then bucket 2 (general path)
+  const bool wide = (long long)c->nbucket[2] * 200 > (long long)c->n;
   FwdArgs<T> b0 = a;
   b0.order = c->d_bucket;
   b0.n_items = c->d_flags + flag_bucket(0);
   b0.order2 = split1 ? nullptr : c->d_bucket + 1 * (size_t)c->n;
   b0.n_items2 = split1 ? nullptr : c->d_flags + flag_bucket(1);
-  b0.order3 = c->d_bucket + 2 * (size_t)c->n;
-  b0.n_items3 = c->d_flags + flag_bucket(2);
+  b0.order3 = wide ? nullptr : c->d_bucket + 2 * (size_t)c->n;
+  b0.n_items3 = wide ? nullptr : c->d_flags + flag_bucket(2);
   // all buckets in one launch: atoms in index order (spatial order, and no
   // indirection); atoms with longer lists take the masked or general path
-  b0.identity = split1 ? 0 : 1;
+  b0.identity = (split1 || wide) ? 0 : 1;
   {
     TimedRegion tr(c, 0, s);
     launch_t<T, NS, 4>(c, b0, force_grid(c, 4), s);
+    if (wide) launch_wide<T, NS>(c, a, s);
   }
   if (fork) {
     cudaEventRecord(c->ev_join, c->side);

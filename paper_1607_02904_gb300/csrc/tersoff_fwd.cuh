@@ -501,9 +501,9 @@ __device__ __forceinline__ void clear_slots(const FwdArgs<T>& a, int i) {
 // across the warp (halving exchanges: 4, 2, 1 values), then summed over the
 // remaining lanes; lanes 0, 4, ..., 28 end with the 8 warp totals. Warp totals
 // are summed in double over the block and added to acc with one atomic each.
-template <class T>
+template <class T, int NB = BLOCK>
 __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc) {
-  __shared__ double part[BLOCK / 32][8];
+  __shared__ double part[NB / 32][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   T v[8] = {ei, w[0], w[1], w[2], w[3], w[4], w[5], T(0)};
   const bool hi16 = lane & 16;
@@ -535,7 +535,7 @@ __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc
   __syncthreads();
   if (threadIdx.x < 7) {
     double s = 0.0;
-    for (int q = 0; q < BLOCK / 32; ++q) s += part[q][threadIdx.x];
+    for (int q = 0; q < NB / 32; ++q) s += part[q][threadIdx.x];
     atomicAdd(&acc[threadIdx.x * ACC_STRIDE], s);
   }
 }
@@ -877,6 +877,175 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
   if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T>(ei, w, a.acc);
+}
+
+// ---------------------------------------------------------------- wide kernel
+// Atoms with many bonds inside the cutoffs (bucket 2: more than 8). One thread
+// per atom; the bonds inside the filter radius are formed once into per-thread
+// slots in dynamic shared memory (unit vector, length, species, list slot, and
+// the force accumulated on that neighbour), and Algorithm 2's loops (zeta
+// over k, the pair terms, the three-body forces over k) run over the slots.
+// Atoms with more bonds than slots take the general path.
+constexpr int WIDE_BLOCK = 64;
+constexpr int WIDE_SLOTS = 16;
+constexpr int WIDE_WORDS = 9;  // ux uy uz r t s fx fy fz
+constexpr size_t wide_slot_bytes(size_t word) {
+  return (size_t)WIDE_BLOCK * WIDE_SLOTS * WIDE_WORDS * word;
+}
+
+template <class T, int NS, bool LAM3>
+__global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_constant__ FwdArgs<T> a) {
+  constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
+  constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
+  __shared__ T srec_s[SREC];
+  __shared__ T sfilt[SNS * SNS];
+  __shared__ int uni[3];
+  extern __shared__ __align__(16) unsigned char wide_dyn[];
+  T* sl = reinterpret_cast<T*>(wide_dyn);
+  const int ns = NS > 0 ? NS : a.ns;
+  if (NS != 1)
+    for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += WIDE_BLOCK) srec_s[q] = a.rec[q];
+  if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+  if (threadIdx.x == 0) {
+    uni[0] = *a.n_items;
+    uni[1] = a.flags[FLAG_REV_MISS];
+    uni[2] = a.flags[FLAG_DMAX];
+  }
+  __syncthreads();
+  const T* srec = NS == 1 ? a.prm1 : srec_s;
+  const int n_items = uni[0];
+  const bool use_short = __int_as_float(uni[2]) <= a.dlim2;
+  const bool slots = !a.atomic_mode && use_short && uni[1] == 0;
+  // slot q, word f of this thread (thread index innermost: no bank conflicts)
+  auto at = [&](int q, int f) -> T& {
+    return sl[((size_t)q * WIDE_WORDS + f) * WIDE_BLOCK + threadIdx.x];
+  };
+  T ei = 0;
+  T w[6] = {0, 0, 0, 0, 0, 0};
+  bool any = false;
+  for (int item = blockIdx.x * WIDE_BLOCK + threadIdx.x; item < n_items;
+       item += gridDim.x * WIDE_BLOCK) {
+    any = true;
+    const int i = a.order[item];
+    if (!slots && !a.atomic_mode) clear_slots<T>(a, i);
+    Shift<T, false> sh;
+    using P = typename SelfPos<T>::type;
+    const P pi = self_pos<T>(a, i);
+    const int ti = a.types[i];
+    const uint32_t* list = use_short ? a.shortl : a.nbr;
+    int c = use_short ? a.zcnt[i] : min(a.cnt[i], a.cap);
+    bool general = false;
+    if (use_short && c > a.zs_cap) {  // short list truncated: the skin list
+      list = a.nbr;
+      c = min(a.cnt[i], a.cap);
+      general = true;
+    }
+    // bonds inside the filter radius into the slots
+    int z = 0;
+    if (!general)
+      for (int s = 0; s < c && z <= WIDE_SLOTS; ++s) {
+        T dx, dy, dz;
+        int j, tj;
+        Bond<T>::vec(a, sh, pi, list[(size_t)s * a.n + i], dx, dy, dz, j, tj);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 <= sfilt[ti * ns + tj])) continue;
+        if (z < WIDE_SLOTS) {
+          const T r = r2 * M<T>::rsqrt_nr(r2);
+          const T ir = T(1) / r;
+          at(z, 0) = dx * ir;
+          at(z, 1) = dy * ir;
+          at(z, 2) = dz * ir;
+          at(z, 3) = r;
+          at(z, 4) = T(tj);
+          at(z, 5) = T(s);
+          at(z, 6) = at(z, 7) = at(z, 8) = T(0);
+        }
+        ++z;
+      }
+    T eatom_i = T(0);
+    if (general || z > WIDE_SLOTS) {
+      atomicAdd(&a.flags[FLAG_FALLBACK], 1);
+      if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
+      general_atom<T, NS, LAM3, false>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
+                                       false, 0ull, eatom_i, w);
+    } else {
+      for (int qj = 0; qj < z; ++qj) {
+        const T uxj = at(qj, 0), uyj = at(qj, 1), uzj = at(qj, 2), rij = at(qj, 3);
+        const int tj = (int)at(qj, 4);
+        const T* p2 = srec + rec_off<NS>(ns, ti, tj, tj);
+        if (!(rij < p2[K_ROUT2])) continue;
+        T zeta = 0;
+        for (int qk = 0; qk < z; ++qk) {
+          if (qk == qj) continue;
+          const T rik = at(qk, 3);
+          const T* p3 = srec + rec_off<NS>(ns, ti, tj, (int)at(qk, 4));
+          if (!(rik < p3[K_ROUT3])) continue;
+          const T cs = uxj * at(qk, 0) + uyj * at(qk, 1) + uzj * at(qk, 2);
+          T zt, A1, A2, A3;
+          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+          zeta += zt;
+        }
+        T V, dVdr, dzv;
+        pair<T>(p2, rij, zeta, V, dVdr, dzv);
+        eatom_i += V;
+        T Fjx = -dVdr * uxj, Fjy = -dVdr * uyj, Fjz = -dVdr * uzj;
+        const T rinj = T(1) / rij;
+        for (int qk = 0; qk < z; ++qk) {
+          if (qk == qj) continue;
+          const T rik = at(qk, 3);
+          const T* p3 = srec + rec_off<NS>(ns, ti, tj, (int)at(qk, 4));
+          if (!(rik < p3[K_ROUT3])) continue;
+          const T uxk = at(qk, 0), uyk = at(qk, 1), uzk = at(qk, 2);
+          const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
+          T zt, A1, A2, A3;
+          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+          const T rink = T(1) / rik;
+          Fjx -= dzv * (A1 * (uxk - cs * uxj) * rinj + A2 * uxj);
+          Fjy -= dzv * (A1 * (uyk - cs * uyj) * rinj + A2 * uyj);
+          Fjz -= dzv * (A1 * (uzk - cs * uzj) * rinj + A2 * uzj);
+          at(qk, 6) -= dzv * (A1 * (uxj - cs * uxk) * rink + (A3 - A2) * uxk);
+          at(qk, 7) -= dzv * (A1 * (uyj - cs * uyk) * rink + (A3 - A2) * uyk);
+          at(qk, 8) -= dzv * (A1 * (uzj - cs * uzk) * rink + (A3 - A2) * uzk);
+        }
+        at(qj, 6) += Fjx;
+        at(qj, 7) += Fjy;
+        at(qj, 8) += Fjz;
+      }
+      // forces, virial and the stores of the list's slots
+      if (slots)  // entries outside the cutoffs get zero; the kept ones are overwritten
+        for (int s = 0; s < c; ++s) store_slot<T>(a, a.contrib, (size_t)s * a.n + i, T(0), T(0), T(0));
+      T fix = 0, fiy = 0, fiz = 0;
+      for (int q = 0; q < z; ++q) {
+        const T fx = at(q, 6), fy = at(q, 7), fz = at(q, 8);
+        fix -= fx;
+        fiy -= fy;
+        fiz -= fz;
+        const T r = at(q, 3);
+        const T dx = at(q, 0) * r, dy = at(q, 1) * r, dz = at(q, 2) * r;
+        w[0] += dx * fx;
+        w[1] += dy * fy;
+        w[2] += dz * fz;
+        w[3] += dx * fy;
+        w[4] += dx * fz;
+        w[5] += dy * fz;
+        const int s = (int)at(q, 5);
+        if (slots) {
+          store_slot<T>(a, a.contrib, (size_t)s * a.n + i, fx, fy, fz);
+        } else {
+          int j, ox, oy, oz;
+          decode(list[(size_t)s * a.n + i], j, ox, oy, oz);
+          atomic_add3(a.f, j, to_f64(fx), to_f64(fy), to_f64(fz));
+        }
+      }
+      if (slots)
+        store_slot<T>(a, a.own, (size_t)i, fix, fiy, fiz);
+      else
+        atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+    }
+    if (a.eatom) a.eatom[i] = to_f64(eatom_i);
+    ei += eatom_i;
+  }
+  if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T, WIDE_BLOCK>(ei, w, a.acc);
 }
 
 }  // namespace fwd
