@@ -39,6 +39,11 @@ R_LIST = 4.0
 RC_SI = 3.0  # largest f_C outer cutoff of the Tersoff 1989 Si / C tables (R + D)
 NPARAM_TABLE_SI = 14
 PEAK_FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+PEAK_MUFU_TOPS_NOMINAL = 152 * 16 * 2.07e9 / 1e12  # SMs x special-function ops per clock x clock
+PEAK_ISSUE_WARP_INST = 152 * 4 * 2.07e9  # SMs x schedulers (one warp instruction each) x clock
+# warp instructions of one force launch on this workload (ncu smsp__inst_executed.sum, the same
+# capture as the traffic); like the traffic, valid only for the sources it was taken with
+FORCE_WARP_INST = 26_214_163
 PEAK_FP64_TFLOPS_NOMINAL = 1.25
 
 # Algorithmic FP32 operations of the mixed force kernel per unit of work
@@ -53,9 +58,24 @@ MUFU_SHORT, MUFU_PAIR, MUFU_TRIPLET = 1, 7, 1
 # workload, from an ncu capture (profiles/k_tersoff_si512k_mixed.md). Valid only
 # for the kernel sources it was taken with, identified by their SHA-256; once
 # those change the traffic is reported as null until it is measured again.
-FORCE_TRAFFIC_BYTES = 21_380_864 + 2_242_304
+FORCE_TRAFFIC_BYTES = 21_363_712 + 2_121_984
 FORCE_TRAFFIC_SOURCES = ("tersoff_fwd.cuh", "fwd_launch.cuh", "fwd_f32.cu")
-FORCE_TRAFFIC_SHA256 = "4734eccc43c444591a9968fa86d9ad354429e730d5537c445fdf9bf6e1fcae02"
+FORCE_TRAFFIC_SHA256 = "a644d2ed1cfab46e121363fcd85ad33b06c983f2b9aceb8ba880cdba46156a8b"
+
+
+def ceilings_us(flop, mufu, peaks, kern_ms):
+    """Lower bounds on one force launch (us) from each resource, beside the
+    measured time: FP32 arithmetic (the FLOP model), special-function
+    operations, DRAM traffic (ncu bytes over the measured copy bandwidth), and
+    instruction issue (ncu warp instructions over 4 per SM per clock)."""
+    out = {"fp32_flops": flop / (PEAK_FP32_TFLOPS_NOMINAL * 1e12) * 1e6,
+           "mufu": mufu / (PEAK_MUFU_TOPS_NOMINAL * 1e12) * 1e6,
+           "measured": kern_ms * 1e3}
+    tr = force_traffic()
+    if tr is not None and peaks.get("hbm_gbs"):
+        out["dram"] = tr / (peaks["hbm_gbs"] * 1e9) * 1e6
+        out["issue"] = FORCE_WARP_INST / PEAK_ISSUE_WARP_INST * 1e6
+    return out
 
 
 def force_traffic():
@@ -412,6 +432,7 @@ def run_ours(args):
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max clock",
             "traffic": force_traffic(),
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+            "ceilings_us": ceilings_us(flop_launch, mufu_launch, peaks, kern_ms),
             "flop_per_launch": flop_launch,
             "mufu_per_launch": mufu_launch,
             "work_per_launch": {"skin_entries": skin, "short_entries": nshort, "pairs": npair,
@@ -774,6 +795,59 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_accuracy(args):
+    """Long-run accuracy of the mixed path (the paper's accuracy experiment,
+    Sec. V-D): Si diamond 20x20x10 cells (32,000 atoms) at 1000 K, the same
+    initial state integrated by the FP64 and the mixed path for args.steps
+    velocity-Verlet steps (dt 1 fs, rebuilds on half the skin), total energy
+    recorded every step; reports the largest relative deviation of the mixed
+    path's total energy from the FP64 path's, and each path's drift."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_1607_02904_gb300 as T
+    names = ["Si"]
+    x, t, box = W.diamond(20, 20, 10, 5.432)
+    rng = W.rng_for(6)
+    x = W.jitter_gaussian(x, 0.05, rng)
+    v = W.maxwell_velocities(t, np.array([W.MASS_AMU["Si"]]), 1000.0, rng)
+    n = x.shape[0]
+    table = T.mix_tersoff89(*W.element_records(names))
+    mass = [W.MASS_AMU[s] for s in names]
+    chunk = 1000
+    out = {"metric": "total-energy deviation of the mixed path from the FP64 path",
+           "atoms": int(n), "steps": args.steps, "dt_ps": DT, "temperature_K": 1000.0,
+           "rebuild": "on half the skin (r_list 4.0 A)"}
+    series = {}
+    for name, prec in (("fp64", T.FP64), ("mixed", T.MIXED)):
+        ctx = T.Context(prec)
+        ctx.params(table)
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+        ctx.neighbor_build(xd, torch.tensor(t, dtype=torch.int32, device="cuda"), box, R_LIST)
+        fd = torch.zeros_like(xd)
+        ctx.compute(xd, None, fd)
+        th = torch.zeros((chunk, 3), dtype=torch.float64, device="cuda")
+        etot = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps // chunk):
+            ctx.md_step(xd, vd, fd, mass, DT, chunk, -1, th)
+            etot.append(th[:, 2].cpu().numpy().copy())
+        torch.cuda.synchronize()
+        series[name] = np.concatenate(etot)
+        out[name + "_seconds"] = time.perf_counter() - t0
+        ctx.close()
+    e64, em = series["fp64"], series["mixed"]
+    tt = np.arange(e64.size) * DT * 1e-3  # ns
+    out["max_rel_deviation"] = float(np.abs(em - e64).max() / np.abs(e64).max())
+    out["final_rel_deviation"] = float(abs(em[-1] - e64[-1]) / abs(e64[-1]))
+    out["paper_bound_rel"] = 2e-5
+    for name, e in (("fp64", e64), ("mixed", em)):
+        out[name + "_drift_eV_per_atom_per_ns"] = float(np.polyfit(tt, e / n, 1)[0])
+        out[name + "_etot_first_last_eV"] = [float(e[0]), float(e[-1])]
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_case(args):
     """The benchmark workload without timing, for profiler captures."""
     import numpy as np
@@ -844,10 +918,16 @@ def main():
                          "the 2.1M-atom SiC workload, or K backward passes of 64 packing "
                          "cells; nothing printed")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="long-run accuracy of the mixed path against the FP64 path "
+                         "(32,000 atoms, --steps MD steps; one JSON line)")
     ap.add_argument("--scatter", choices=["gather", "atomic"], default="gather")
     args = ap.parse_args()
     if args.only:
         run_profile_case(args)
+        return
+    if args.accuracy:
+        run_accuracy(args)
         return
     if args.warmup < 3:
         args.warmup = 3

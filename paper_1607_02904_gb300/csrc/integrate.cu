@@ -139,17 +139,23 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
       const float d0 = kf * sc[0] + kf * sc[3];
       const float d1 = kf * sc[1] + kf * sc[4];
       const float d2v = kf * sc[2] + kf * sc[5];
+      const bool extra = ga.flags[FLAG_EXTRA] | ga.flags[FLAG_EXTRA_STICKY];
       if (ke_row) {
         const float hf = cf.cf[t];
-        const double w0 = v0 + gather_f2d(hf * sc[0] + hf * sc[3]);
-        const double w1 = v1 + gather_f2d(hf * sc[1] + hf * sc[4]);
-        const double w2 = v2 + gather_f2d(hf * sc[2] + hf * sc[5]);
+        double w0 = v0 + gather_f2d(hf * sc[0] + hf * sc[3]);
+        double w1 = v1 + gather_f2d(hf * sc[1] + hf * sc[4]);
+        double w2 = v2 + gather_f2d(hf * sc[2] + hf * sc[5]);
+        if (extra) {  // forces scattered through the fallback buffer
+          w0 = fma(cu, F0, w0);
+          w1 = fma(cu, F1, w1);
+          w2 = fma(cu, F2, w2);
+        }
         ke = 0.5 * cf.m[t] * fma(w0, w0, fma(w1, w1, w2 * w2));
       }
       vn0 = v0 + gather_f2d(d0);
       vn1 = v1 + gather_f2d(d1);
       vn2 = v2 + gather_f2d(d2v);
-      if (ga.flags[FLAG_EXTRA] | ga.flags[FLAG_EXTRA_STICKY]) {
+      if (extra) {
         vn0 = fma(kcu, F0, vn0);
         vn1 = fma(kcu, F1, vn1);
         vn2 = fma(kcu, F2, vn2);

@@ -112,3 +112,31 @@ def test_fixed_period_rebuild_count(T):
     with pytest.raises(T.TersoffError):
         ctx.md_step(xd, vd, fd, MASS, 0.001, 5, -2)
     ctx.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False], ids=["graph", "eager"])
+def test_mixed_thermo_when_short_list_expires(T, graphs):
+    # 3000 K, skin 0.5 A and no rebuild for 25 steps: after ~15 steps atoms
+    # have moved beyond half the short-list margin (0.15 A) and the force
+    # kernel scatters through the fallback buffer, while the skin list stays
+    # valid (0.25 A). The mixed path's thermo must still follow the FP64 path.
+    x, v, t, box = hot_si(seed=63)
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    out = {}
+    for prec in (T.FP64, T.MIXED):
+        ctx = T.Context(prec)
+        ctx.set_graphs(graphs)
+        ctx.params(table)
+        xd, vd = dev(x), dev(v)
+        ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 0.5)
+        fd = torch.zeros_like(xd)
+        ctx.compute(xd, None, fd)
+        th = torch.zeros((25, 3), dtype=torch.float64, device="cuda")
+        ctx.md_step(xd, vd, fd, MASS, 0.001, 25, 0, th)
+        torch.cuda.synchronize()
+        out[prec] = th.cpu().numpy()
+        ctx.close()
+    d, m = out[T.FP64], out[T.MIXED]
+    scale = np.abs(d[:, 2]).max()
+    assert np.abs(m[:, 2] - d[:, 2]).max() <= 1e-6 * scale  # total energy
+    assert np.abs(m[:, 1] - d[:, 1]).max() <= 1e-5 * np.abs(d[:, 1]).max()  # kinetic

@@ -10,6 +10,7 @@ exactly four nearest neighbours per atom (Sec. VI). That input file is not
 available; the diamond lattices below take its shape and stand in for it.
 """
 from .synth import (  # noqa: F401
+    rng_for,
     ELEMENTS_TERSOFF89,
     CHI_SIC,
     MASS_AMU,
