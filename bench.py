@@ -848,6 +848,52 @@ def run_accuracy(args):
     print(json.dumps(out), flush=True)
 
 
+def run_ablations(args):
+    """The paper's design choices measured on the benchmark workload (mixed
+    path, default launch options): the stored short list (Sec. IV-D) and the
+    register-resident neighbourhood with pre-computed derivatives (Sec. IV-A),
+    each switched off alone and together. Reports ms per 10 MD steps and per
+    force evaluation; the forces are the same up to rounding order."""
+    import numpy as np
+    import torch
+    import workloads as W
+    import paper_1607_02904_gb300 as T
+    x, v, t, box, names = W.config_si_md()
+    table = T.mix_tersoff89(*W.element_records(names))
+    mass = [W.MASS_AMU[s] for s in names]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"metric": "ablations of the paper's design choices (mixed path)",
+           "workload": workload_name(), "md_ms_per_10_steps": {}, "force_eval_ms": {},
+           "force_rms_rel_vs_default": {}}
+    ref = None
+    for name, flags in (("default", 0), ("no_short_list", T.ABLATE_NO_SHORT),
+                        ("general_path", T.ABLATE_GENERAL),
+                        ("both", T.ABLATE_NO_SHORT | T.ABLATE_GENERAL)):
+        ctx = T.Context(T.MIXED)
+        ctx.set_ablation(flags)
+        ctx.params(table)
+        xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+        vd = torch.tensor(v, dtype=torch.float64, device="cuda")
+        ctx.neighbor_build(xd, torch.tensor(t, dtype=torch.int32, device="cuda"), box, R_LIST)
+        fd = torch.zeros_like(xd)
+        ctx.compute(xd, None, fd)
+        fr = fd.cpu().numpy()
+        if ref is None:
+            ref = fr
+        out["force_rms_rel_vs_default"][name] = float(np.sqrt(((fr - ref) ** 2).mean()) /
+                                                      np.sqrt((ref ** 2).mean()))
+        out["force_eval_ms"][name] = _event_time(lambda: ctx.compute(xd, None, fd), args.steps,
+                                                 flush, stream)
+        for _ in range(3):
+            ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
+        out["md_ms_per_10_steps"][name] = _event_time(
+            lambda: ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP), args.steps,
+            flush, stream)
+        ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_profile_case(args):
     """The benchmark workload without timing, for profiler captures."""
     import numpy as np
@@ -918,6 +964,8 @@ def main():
                          "the 2.1M-atom SiC workload, or K backward passes of 64 packing "
                          "cells; nothing printed")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--ablations", action="store_true",
+                    help="the paper's design choices switched off one at a time (one JSON line)")
     ap.add_argument("--accuracy", action="store_true",
                     help="long-run accuracy of the mixed path against the FP64 path "
                          "(32,000 atoms, --steps MD steps; one JSON line)")
@@ -928,6 +976,9 @@ def main():
         return
     if args.accuracy:
         run_accuracy(args)
+        return
+    if args.ablations:
+        run_ablations(args)
         return
     if args.warmup < 3:
         args.warmup = 3

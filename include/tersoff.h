@@ -269,6 +269,20 @@ int tersoff_autotune(tersoff_ctx* ctx, const double* x, const double* v, int n,
  * in [64, 512]). Results do not depend on them beyond rounding order. */
 int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
 
+/* Ablations of the paper's design choices, for measurement (results are
+ * unchanged up to rounding order; the default is 0):
+ *   TERSOFF_ABLATE_NO_SHORT   no stored short list: every force evaluation
+ *                             filters the full skin list by the cutoffs (the
+ *                             per-step filter of Sec. IV-D) and scatters forces
+ *                             with FP64 atomics (slots need the short list);
+ *   TERSOFF_ABLATE_GENERAL    every atom takes Algorithm 2's loops over its list
+ *                             with the three-body terms recomputed in the second K
+ *                             loop, instead of the register-resident neighbourhood
+ *                             with pre-computed derivatives (Sec. IV-A). */
+#define TERSOFF_ABLATE_NO_SHORT 1
+#define TERSOFF_ABLATE_GENERAL 2
+int tersoff_set_ablation(tersoff_ctx* ctx, int flags);
+
 /* One-line text of the last tersoff_autotune: the chosen options and every
  * trial's time (storage owned by the context). */
 const char* tersoff_autotune_summary(const tersoff_ctx* ctx);

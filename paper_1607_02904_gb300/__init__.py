@@ -16,6 +16,8 @@ from ._lib import (  # noqa: F401
     NPARAM,
     NOALLOC_MAX_ATOMS,
     REBUILD_ON_SKIN,
+    ABLATE_NO_SHORT,
+    ABLATE_GENERAL,
     load,
     library_path,
     declared_symbols,

@@ -27,6 +27,8 @@ SCATTER_ATOMIC = 1
 NPARAM = 14
 NOALLOC_MAX_ATOMS = 65536
 REBUILD_ON_SKIN = -1
+ABLATE_NO_SHORT = 1
+ABLATE_GENERAL = 2
 
 _lib = None
 
@@ -56,6 +58,7 @@ _SIG = {
     "tersoff_autotune": ([_P, _P, _P, _I, _P, _D, _I, _P], _I),
     "tersoff_autotune_summary": ([_P], ctypes.c_char_p),
     "tersoff_set_launch": ([_P, _I, _I, _I], _I),
+    "tersoff_set_ablation": ([_P, _I], _I),
     "tersoff_set_timing": ([_P, _I], _I),
     "tersoff_set_graphs": ([_P, _I], _I),
     "tersoff_set_scatter": ([_P, _I], _I),
@@ -259,6 +262,10 @@ class Context:
 
     def set_launch(self, waves=0, split=-1, block=256):
         self._check(self.lib.tersoff_set_launch(self.h, int(waves), int(split), int(block)))
+
+    def set_ablation(self, flags):
+        """ABLATE_NO_SHORT | ABLATE_GENERAL, for measuring the design choices."""
+        self._check(self.lib.tersoff_set_ablation(self.h, int(flags)))
 
     def autotune_summary(self):
         return self.lib.tersoff_autotune_summary(self.h).decode()

@@ -1192,6 +1192,15 @@ int tersoff_set_launch(tersoff_ctx* p, int waves, int split, int block) {
   return TERSOFF_OK;
 }
 
+int tersoff_set_ablation(tersoff_ctx* p, int flags) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (flags & ~3) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "ablation flags are bits 0 and 1");
+  c->ablate = flags;
+  c->gen++;  // captured MD graphs hold the old kernel arguments
+  return TERSOFF_OK;
+}
+
 const char* tersoff_autotune_summary(const tersoff_ctx* p) {
   if (!p) return "null context";
   return p->impl.tune_summary.c_str();

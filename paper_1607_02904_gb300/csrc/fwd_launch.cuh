@@ -137,7 +137,9 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   a.shortl = c->d_short;
   a.zcnt = c->d_zcnt;
   a.zs_cap = c->zs_cap;
-  a.dlim2 = (float)(0.25 * c->margin * c->margin);
+  // ablation ABLATE_NO_SHORT: the stored short list is never valid
+  a.dlim2 = (c->ablate & 1) ? -1.0f : (float)(0.25 * c->margin * c->margin);
+  a.all_general = (c->ablate & 2) ? 1 : 0;
   a.f = f;
   a.contrib = c->d_contrib;
   a.atomic_mode = c->scatter_atomic ? 1 : 0;

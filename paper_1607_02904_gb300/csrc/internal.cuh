@@ -176,6 +176,7 @@ struct Ctx {
   int opt_split = -1;  // capacity-8 side-stream launch: -1 automatic, 0 never, 1 when non-empty
   int opt_block = 256; // block size of the per-atom pack / integrate / gather kernels
   int n_sm = 0;        // multiprocessors of the device
+  int ablate = 0;      // tersoff_set_ablation flags
   std::string tune_summary;  // last tersoff_autotune: choice and trial times
 
   // batch of independent periodic systems (n_sys > 0; tersoff_neighbor_build_batched)

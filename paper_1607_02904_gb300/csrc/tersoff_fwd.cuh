@@ -158,6 +158,7 @@ template <class T> struct FwdArgs {
   const int* order3;
   const int* n_items3;
   int identity;          // process atoms 0..n-1 directly (no bucket order)
+  int all_general;       // ablation: every atom takes the general path (Algorithm 2 loops)
   float dlim2;           // short list valid while max squared displacement <= dlim2
   void* contrib;         // slot-major per-neighbour force contributions (T4)
   void* own;             // per-atom force of its own terms (T4)
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
       list = a.shortl;
       c = z_list;
       z = z_list;
-      general = z_list > a.zs_cap;
+      general = z_list > a.zs_cap || a.all_general;
       if (general) {  // short list truncated: use the skin list
         list = a.nbr;
         c = min(a.cnt[i], a.cap);
@@ -633,7 +634,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
             if (r2 <= sfilt[ti * ns + tj]) mask |= 1ull << s;
           }
         z = __popcll(mask);
-        general = !fits || z > ZC;
+        general = !fits || z > ZC || a.all_general;
         have_mask = fits;
       }
     } else {
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
         }
       }
       z = __popcll(mask);
-      general = !fits || z > ZC;
+      general = !fits || z > ZC || a.all_general;
       have_mask = fits;
     }
     if (!slots && !a.atomic_mode) clear_slots<T>(a, i);

@@ -122,3 +122,22 @@ def test_autotune_batch_compute(T):
         ref = oracle.compute(xs, ts, bs, TABLE, oracle.neighbors(xs, bs, RC))
         check(1, (e[s].item(), f[off[s]:off[s + 1]].cpu().numpy(), w[s].cpu().numpy()), ref)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_ablations_keep_results(T, prec, flags):
+    ctx = T.Context(prec)
+    ctx.set_ablation(flags)
+    ctx.params(TABLE)
+    xd = dev(X)
+    ctx.neighbor_build(xd, dev(TY, torch.int32), BOX, RC + 0.5)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(xd)
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(xd, e, f, w)
+    torch.cuda.synchronize()
+    check(prec, (e.item(), f.cpu().numpy(), w.cpu().numpy()), REF)
+    with pytest.raises(T.TersoffError):
+        ctx.set_ablation(4)
+    ctx.close()
