@@ -159,16 +159,16 @@ int tersoff_compute(tersoff_ctx* ctx, const double* x, int n, double* energy,
  * the derivative with respect to the forces; NULL means zero):
  *   grad_table (device, n_species^3 x TERSOFF_NPARAM doubles, table layout)
  *       = d/dtheta [ gE E + sum_a gF_a . F_a ]      (field m gets 0: integer)
- *   grad_x (device, N x 3) = gE dE/dx = -gE F.
+ *   grad_x (device, N x 3) = d/dx [ gE E + sum_a gF_a . F_a ]
+ *       = -gE F - H gF,   H the Hessian d^2E/dx^2 (a Hessian-vector product;
+ *       with gF == NULL only the -gE F term).
  * The three-body sums are recomputed, not stored by the forward call. Either
- * output may be NULL. grad_x with gF != NULL (the position derivative of the
- * force term, a Hessian-vector product) is not provided and returns
- * TERSOFF_E_INVALID_ARG. x: positions of the atoms of the last neighbour build
+ * output may be NULL. x: positions of the atoms of the last neighbour build
  * (as for tersoff_compute). Arithmetic follows the context's precision (mixed:
  * per-term float, gradient sums in double). In batch mode (see
  * tersoff_neighbor_build_batched) gE holds one weight per system and E is the
  * vector of system energies: grad_table = d/dtheta [sum_s gE_s E_s +
- * sum_a gF_a . F_a] and grad_x = -gE_{s(a)} F_a. */
+ * sum_a gF_a . F_a] and grad_x = -gE_{s(a)} F_a - (H gF)_a. */
 int tersoff_backward(tersoff_ctx* ctx, const double* x, int n, const double* gE,
                      const double* gF, double* grad_x, double* grad_table, void* stream);
 

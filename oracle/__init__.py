@@ -54,7 +54,7 @@ def _load():
         "oracle_compute": ([I, P, P, P, I, P, P, P, I, I, P, P, P, P], I),
         "oracle_energy_n3": ([I, P, P, P, I, P, P], I),
         "oracle_cs_param": ([I, P, P, P, I, P, P, P, I, I, D, P, P], I),
-        "oracle_cs_pos": ([I, P, P, P, I, P, P, P, I, I, I, D, P], I),
+        "oracle_cs_pos": ([I, P, P, P, I, P, P, P, I, I, I, D, P, P], I),
         "oracle_md_run": ([I, P, P, P, P, I, P, P, D, I, D, I, I, I, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -155,8 +155,8 @@ def cs_param(x, types, box, table, nl, p, h=1e-30):
     return float(de[0]), df
 
 
-def cs_pos(x, types, box, table, nl, a, c, h=1e-30):
-    """Complex-step dE/dx[a, c]."""
+def cs_pos(x, types, box, table, nl, a, c, h=1e-30, forces=False):
+    """Complex-step dE/dx[a, c] (and, with forces=True, dF/dx[a, c] as (n, 3))."""
     x = _f64(x)
     types = _i32(types)
     box = _f64(box)
@@ -164,10 +164,12 @@ def cs_pos(x, types, box, table, nl, a, c, h=1e-30):
     cnt, nbr = _i32(nl[0]), _i32(nl[1])
     ns = round((table.size // NPAR) ** (1.0 / 3.0))
     de = np.zeros(1)
+    df = np.zeros((x.shape[0], 3)) if forces else None
     st = _load().oracle_cs_pos(x.shape[0], _p(x), _p(types), _p(box), ns, _p(table), _p(cnt),
-                               _p(nbr), nbr.shape[1], int(a), int(c), float(h), _p(de))
+                               _p(nbr), nbr.shape[1], int(a), int(c), float(h), _p(de),
+                               _p(df) if forces else None)
     assert st == 0
-    return float(de[0])
+    return (float(de[0]), df) if forces else float(de[0])
 
 
 def md_run(x, v, types, box, table, mass_per_species, dt, nsteps, rlist, rebuild_every,

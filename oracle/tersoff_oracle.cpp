@@ -515,10 +515,12 @@ int oracle_cs_param(int n, const double* x, const int* types, const double* box,
   return 0;
 }
 
-// Complex-step derivative of E with respect to position component x[3*a + c].
+// Complex-step derivatives with respect to position component x[3*a + c]:
+// dE/dx_ac, and (dF optional, n x 3) dF/dx_ac, the column (a, c) of minus the
+// Hessian.
 int oracle_cs_pos(int n, const double* x, const int* types, const double* box, int ns,
                   const double* table, const int* cnt, const int* nbr, int cap, int a,
-                  int c, double h, double* dE) {
+                  int c, double h, double* dE, double* dF) {
   size_t nt = (size_t)ns * ns * ns * NPAR;
   std::vector<cd> xz(3 * (size_t)n), tz(nt), fz(3 * (size_t)n, cd(0.0));
   for (size_t q = 0; q < 3 * (size_t)n; ++q) xz[q] = cd(x[q], 0.0);
@@ -529,6 +531,8 @@ int oracle_cs_pos(int n, const double* x, const int* types, const double* box, i
   evaluate<cd>(n, xz.data(), types, box, ns, tz.data(), nl, 0, n, &E, fz.data(), W,
                (cd*)nullptr);
   *dE = E.imag() / h;
+  if (dF)
+    for (size_t q = 0; q < 3 * (size_t)n; ++q) dF[q] = fz[q].imag() / h;
   return 0;
 }
 

@@ -3,16 +3,17 @@
 ``energy_forces(system, x, table)`` returns (E, F) from the CUDA library's
 ``tersoff_compute``; its backward runs the library's adjoint kernel
 (``tersoff_backward``): the gradient of ``gE E + sum_a gF_a . F_a`` with respect
-to the parameter table, and ``dE/dx = -F`` for the positions. The position
-derivative of the forces (a Hessian-vector product) is not provided: a loss
-that uses the forces can be differentiated with respect to the table, not the
-positions. Everything here marshals arguments; the arithmetic runs in the
-library's kernels.
+to the parameter table and with respect to the positions (``-gE F`` plus the
+Hessian-vector product ``-H gF``), so a loss on energies and forces can be
+differentiated in both. The returned gradients are not themselves
+differentiable (no double backward). Everything here marshals arguments; the
+arithmetic runs in the library's kernels.
 """
 from __future__ import annotations
 
 import numpy as np
 import torch
+from torch.autograd.function import once_differentiable
 
 from ._lib import MIXED, NPARAM, Context
 
@@ -104,6 +105,7 @@ class TersoffFunction(torch.autograd.Function):
         return e.reshape(system.energies_shape), f
 
     @staticmethod
+    @once_differentiable
     def backward(fctx, gE, gF):
         (x,) = fctx.saved_tensors
         system = fctx.system
@@ -117,10 +119,6 @@ class TersoffFunction(torch.autograd.Function):
         else:
             ge = gE.reshape(ne).to(dev, torch.float64).contiguous()
         gf = None if gF is None else gF.to(dev, torch.float64).contiguous()
-        if need_x and gf is not None:
-            raise RuntimeError("the position derivative of the forces (a Hessian-vector "
-                               "product) is not provided; differentiate a force loss with "
-                               "respect to the table only")
         gx = torch.empty_like(x) if need_x else None
         gt = torch.empty(system.ntable, dtype=torch.float64, device=dev) if need_t else None
         if need_x or need_t:
@@ -132,7 +130,7 @@ class TersoffFunction(torch.autograd.Function):
 
 def energy_forces(system: TersoffSystem, x: torch.Tensor, table: torch.Tensor):
     """Energy (0-dim; per system for a TersoffBatch) and forces (N, 3),
-    differentiable in ``table`` (both) and in ``x`` (energy only)."""
+    differentiable in ``table`` and in ``x``."""
     return TersoffFunction.apply(x, table, system)
 
 

@@ -702,10 +702,6 @@ int tersoff_backward(tersoff_ctx* p, const double* x, int n, const double* gE, c
   if (n != c->n || (n > 0 && !x))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "atom count differs from the neighbour build");
   if (!gE) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "gE is null");
-  if (grad_x && gF)
-    return tgb::fail(c, TERSOFF_E_INVALID_ARG,
-                     "the position derivative of the force term (a Hessian-vector product) "
-                     "is not provided: grad_x requires gF == NULL");
   cudaStream_t s = (cudaStream_t)stream;
   if (grad_table) {
     const size_t nraw = (size_t)c->ns * c->ns * c->ns * TERSOFF_NPARAM;
@@ -720,6 +716,7 @@ int tersoff_backward(tersoff_ctx* p, const double* x, int n, const double* gE, c
       st = compute_impl(c, x, n, nullptr, grad_x, nullptr, nullptr, s);
     if (st) return st;
     if ((st = tgb::launch_scale_forces(c, grad_x, gE, s))) return st;
+    if (gF && (st = tgb::launch_hvp(c, gF, grad_x, s))) return st;
   }
   return TERSOFF_OK;
 }

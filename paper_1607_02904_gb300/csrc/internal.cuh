@@ -327,6 +327,8 @@ int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, dou
 // Parameter adjoint (tersoff_bwd.cu): adds d/dtheta [gE E + sum gF . F] to
 // grad (ns^3 x TERSOFF_NPARAM); positions must be packed. And f = -gE f.
 int launch_backward(Ctx* c, const double* gE, const double* gF, double* grad, cudaStream_t s);
+// adds the position derivative of sum_a gF_a . F_a to grad_x (positions packed)
+int launch_hvp(Ctx* c, const double* gF, double* grad_x, cudaStream_t s);
 int launch_scale_forces(Ctx* c, double* f, const double* gE, cudaStream_t s);
 // Fixed scratch of tersoff_compute_noalloc (noalloc.cu): the current device's
 // array and its length in doubles; and the copy of its results to the outputs.

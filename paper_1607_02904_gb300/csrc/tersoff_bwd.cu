@@ -517,6 +517,338 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
     if (sgrad[q] != 0.0) atomicAdd(&a.grad[q], sgrad[q]);
 }
 
+// ------------------------------------------------------------------ Hessian-vector product
+// The position derivative of the force term: d/dx [sum_a gF_a . F_a] =
+// -sum_i d/dx D_w E_i, D_w E_i the derivative of E_i along the bond
+// perturbations w_ij = gF_j - gF_i (as in the parameter adjoint). Per centre
+// atom, D_w E_i = sum_j [V_r(r_j, zeta_j) rd_j + V_zeta(r_j, zeta_j) zeta_rate_j]
+// is differentiated in reverse with respect to the bond geometry (lengths r,
+// unit vectors u, rates rd = u.w, and p = (w - u rd)/r, through which
+// cos(theta_jk) = u_j.u_k and its rate p_j.u_k + p_k.u_j depend on the bond
+// vectors), which needs the second derivatives of f_C, g, the exponential and
+// the pair functions; the bond-vector adjoints are scattered to the atoms.
+
+template <class T> struct D2 {
+  T f, d1, d2;
+};
+// f_C(r) and its first two r-derivatives
+template <class T>
+__device__ __forceinline__ D2<T> cutoff2(T r, T R, T D) {
+  D2<T> o;
+  if (r <= R - D) {
+    o.f = T(1);
+    o.d1 = o.d2 = T(0);
+    return o;
+  }
+  if (r >= R + D) {
+    o.f = o.d1 = o.d2 = T(0);
+    return o;
+  }
+  const T q = (r - R) / (T(2) * D);
+  T sn, cn;
+  BM<T>::scpi(q, &sn, &cn);
+  const T PI = T(3.14159265358979323846);
+  const T k = PI / (T(4) * D);
+  o.f = T(0.5) - T(0.5) * sn;
+  o.d1 = -k * cn;
+  o.d2 = k * PI / (T(2) * D) * sn;
+  return o;
+}
+// g(cos) and its first two cos-derivatives (t = h - cos, Den = d^2 + t^2)
+template <class T>
+__device__ __forceinline__ D2<T> angular2(T cs, T ga, T c, T d, T h) {
+  const T t = h - cs, t2 = t * t, d2 = d * d, den = d2 + t2, iden = T(1) / den, c2 = c * c;
+  D2<T> o;
+  o.f = ga + ga * c2 * t2 / (d2 * den);
+  o.d1 = -T(2) * ga * c2 * t * iden * iden;
+  o.d2 = T(2) * ga * c2 * (den - T(4) * t2) * iden * iden * iden;
+  return o;
+}
+// X(Delta) = exp((lambda3 Delta)^m) and its first two Delta-derivatives
+template <class T>
+__device__ __forceinline__ D2<T> expo2(T delta, T l3, int m) {
+  const T a = l3 * delta;
+  T am2 = T(1);  // a^(m-2), used for m >= 2
+  for (int s = 2; s < m; ++s) am2 *= a;
+  const T am1 = m >= 2 ? am2 * a : T(1);
+  D2<T> o;
+  o.f = BM<T>::ex(am1 * a);
+  o.d1 = T(m) * l3 * am1 * o.f;
+  o.d2 = (m >= 2 ? T(m) * T(m - 1) * l3 * l3 * am2 * o.f : T(0)) + T(m) * l3 * am1 * o.d1;
+  return o;
+}
+
+// Adjoints of one bond's (r, u, rd, p).
+template <class T> struct BondBar {
+  T r, ux, uy, uz, rd, px, py, pz;
+};
+template <class T>
+__device__ __forceinline__ BondBar<T> zero_bar() {
+  BondBar<T> o;
+  o.r = o.ux = o.uy = o.uz = o.rd = o.px = o.py = o.pz = T(0);
+  return o;
+}
+
+// The adjoint of the bond vector d from those of (r, u, rd, p), with
+// r = |d|, u = d / r, rd = u . w, p = (w - u rd) / r (w held fixed).
+template <class T>
+__device__ __forceinline__ void bond_vec_bar(const BondD<T>& b, BondBar<T> q, T& dx, T& dy, T& dz) {
+  const T ir = T(1) / b.r;
+  q.ux -= b.rd * ir * q.px;
+  q.uy -= b.rd * ir * q.py;
+  q.uz -= b.rd * ir * q.pz;
+  q.rd -= (b.ux * q.px + b.uy * q.py + b.uz * q.pz) * ir;
+  q.r -= (b.px * q.px + b.py * q.py + b.pz * q.pz) * ir;
+  // w = p r + u rd
+  q.ux += q.rd * (b.px * b.r + b.ux * b.rd);
+  q.uy += q.rd * (b.py * b.r + b.uy * b.rd);
+  q.uz += q.rd * (b.pz * b.r + b.uz * b.rd);
+  const T uu = q.ux * b.ux + q.uy * b.uy + q.uz * b.uz;
+  dx = (q.ux - uu * b.ux) * ir + q.r * b.ux;
+  dy = (q.uy - uu * b.uy) * ir + q.r * b.uy;
+  dz = (q.uz - uu * b.uz) * ir + q.r * b.uz;
+}
+
+// Reverse-mode derivative of D_w E_i with respect to the geometry of the
+// centre atom's bonds, in Algorithm 2's loop order: per bond j a first K loop
+// forms zeta_ij and its rate, the pair level seeds the adjoints, and a second
+// K loop adds the adjoints of every three-body term's inputs. get(q, bond, j)
+// returns bond q (false outside the filter radius); sink(q, bond, j, bar)
+// receives additive adjoint contributions for bond q.
+template <class T, class Get, class Sink>
+__device__ __forceinline__ void atom_hvp(const T* sraw, int ns, int ti, int count, Get get, Sink sink) {
+  for (int qj = 0; qj < count; ++qj) {
+    BondD<T> bj;
+    int jj;
+    if (!get(qj, bj, jj)) continue;
+    const int tj = bj.t;
+    const int p = (ti * ns + tj) * ns + tj;
+    const T Rp = rec_val(sraw, p, TERSOFF_P_R), Dp = rec_val(sraw, p, TERSOFF_P_D_CUT);
+    const T rj = bj.r, rdj = bj.rd;
+    if (!(rj < Rp + Dp)) continue;
+    // first K loop: zeta_ij and its rate
+    T zeta = T(0), zd = T(0);
+    for (int qk = 0; qk < count; ++qk) {
+      if (qk == qj) continue;
+      BondD<T> bk;
+      int jk;
+      if (!get(qk, bk, jk)) continue;
+      const int q = (ti * ns + tj) * ns + bk.t;
+      const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
+      if (!(bk.r < Rq + Dq)) continue;
+      const T cs = bj.ux * bk.ux + bj.uy * bk.uy + bj.uz * bk.uz;
+      const T csd = (bj.px * bk.ux + bj.py * bk.uy + bj.pz * bk.uz) +
+                    (bk.px * bj.ux + bk.py * bj.uy + bk.pz * bj.uz);
+      const D2<T> F3 = cutoff2<T>(bk.r, Rq, Dq);
+      const D2<T> G = angular2<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA), rec_val(sraw, q, TERSOFF_P_C),
+                                  rec_val(sraw, q, TERSOFF_P_D), rec_val(sraw, q, TERSOFF_P_H));
+      const D2<T> X = expo2<T>(rj - bk.r, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
+                               (int)rec_val(sraw, q, TERSOFF_P_M));
+      zeta += F3.f * G.f * X.f;
+      zd += F3.d1 * bk.rd * G.f * X.f + F3.f * G.d1 * csd * X.f + F3.f * G.f * X.d1 * (rdj - bk.rd);
+    }
+    // pair level: Phi_j = 1/2 (P' + b Q') rd_j + 1/2 Q b' zeta_rate
+    const D2<T> fc = cutoff2<T>(rj, Rp, Dp);
+    const T A = rec_val(sraw, p, TERSOFF_P_A), l1 = rec_val(sraw, p, TERSOFF_P_LAMBDA1);
+    const T B = rec_val(sraw, p, TERSOFF_P_B), l2 = rec_val(sraw, p, TERSOFF_P_LAMBDA2);
+    const T Ae = A * BM<T>::ex(-l1 * rj), Be = B * BM<T>::ex(-l2 * rj);
+    const T P1 = (fc.d1 - l1 * fc.f) * Ae;
+    const T P2 = (fc.d2 - T(2) * l1 * fc.d1 + l1 * l1 * fc.f) * Ae;
+    const T Q0 = -fc.f * Be;
+    const T Q1 = -(fc.d1 - l2 * fc.f) * Be;
+    const T Q2 = -(fc.d2 - T(2) * l2 * fc.d1 + l2 * l2 * fc.f) * Be;
+    const Bo<T> bo = bond_ad<T>(zeta, rec_val(sraw, p, TERSOFF_P_BETA), rec_val(sraw, p, TERSOFF_P_N));
+    BondBar<T> aj = zero_bar<T>();
+    aj.rd = T(0.5) * (P1 + bo.b * Q1);
+    aj.r = T(0.5) * (P2 + bo.b * Q2) * rdj + T(0.5) * Q1 * bo.db * zd;
+    const T zb = T(0.5) * Q1 * bo.db * rdj + T(0.5) * Q0 * bo.ddb * zd;  // d Phi_j / d zeta
+    const T zdb = T(0.5) * Q0 * bo.db;                                   // d Phi_j / d zeta_rate
+    if (zb != T(0) || zdb != T(0)) {
+      // second K loop: T = F3 G X, T_rate = F3' rd_k G X + F3 G' cs_rate X + F3 G X' (rd_j - rd_k)
+      for (int qk = 0; qk < count; ++qk) {
+        if (qk == qj) continue;
+        BondD<T> bk;
+        int jk;
+        if (!get(qk, bk, jk)) continue;
+        const int q = (ti * ns + tj) * ns + bk.t;
+        const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
+        const T rk = bk.r, rdk = bk.rd;
+        if (!(rk < Rq + Dq)) continue;
+        const T cs = bj.ux * bk.ux + bj.uy * bk.uy + bj.uz * bk.uz;
+        const T csd = (bj.px * bk.ux + bj.py * bk.uy + bj.pz * bk.uz) +
+                      (bk.px * bj.ux + bk.py * bj.uy + bk.pz * bj.uz);
+        const T dl = rdj - rdk;
+        const D2<T> F3 = cutoff2<T>(rk, Rq, Dq);
+        const D2<T> G = angular2<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA), rec_val(sraw, q, TERSOFF_P_C),
+                                    rec_val(sraw, q, TERSOFF_P_D), rec_val(sraw, q, TERSOFF_P_H));
+        const D2<T> X = expo2<T>(rj - rk, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
+                                 (int)rec_val(sraw, q, TERSOFF_P_M));
+        const T FG = F3.f * G.f;
+        BondBar<T> ak = zero_bar<T>();
+        ak.r = zb * (F3.d1 * G.f * X.f - FG * X.d1) +
+               zdb * (F3.d2 * rdk * G.f * X.f - F3.d1 * rdk * G.f * X.d1 + F3.d1 * G.d1 * csd * X.f -
+                      F3.f * G.d1 * csd * X.d1 + F3.d1 * G.f * X.d1 * dl - FG * X.d2 * dl);
+        ak.rd = zdb * (F3.d1 * G.f * X.f - FG * X.d1);
+        aj.r += zb * FG * X.d1 + zdb * (F3.d1 * rdk * G.f * X.d1 + F3.f * G.d1 * csd * X.d1 + FG * X.d2 * dl);
+        aj.rd += zdb * FG * X.d1;
+        const T cb = zb * F3.f * G.d1 * X.f +
+                     zdb * (F3.d1 * rdk * G.d1 * X.f + F3.f * G.d2 * csd * X.f + F3.f * G.d1 * X.d1 * dl);
+        const T cdb = zdb * F3.f * G.d1 * X.f;
+        // cos = u_j . u_k, cos_rate = p_j . u_k + p_k . u_j
+        aj.ux += cb * bk.ux + cdb * bk.px;
+        aj.uy += cb * bk.uy + cdb * bk.py;
+        aj.uz += cb * bk.uz + cdb * bk.pz;
+        aj.px += cdb * bk.ux;
+        aj.py += cdb * bk.uy;
+        aj.pz += cdb * bk.uz;
+        ak.ux = cb * bj.ux + cdb * bj.px;
+        ak.uy = cb * bj.uy + cdb * bj.py;
+        ak.uz = cb * bj.uz + cdb * bj.pz;
+        ak.px = cdb * bj.ux;
+        ak.py = cdb * bj.uy;
+        ak.pz = cdb * bj.uz;
+        sink(qk, bk, jk, ak);
+      }
+    }
+    sink(qj, bj, jj, aj);
+  }
+}
+
+// Per-thread bond slots of the Hessian-vector kernel in dynamic shared memory,
+// thread index innermost: the bond data (9 words, as in the parameter
+// adjoint), its adjoint accumulators (8 words) and the neighbour index.
+constexpr int HVP_BAR_WORDS = 8;
+constexpr int HVP_SLOTS = 12;
+template <class T> struct HvpBlock;
+template <> struct HvpBlock<float> { static constexpr int size = 64; };
+template <> struct HvpBlock<double> { static constexpr int size = 32; };
+template <class T>
+constexpr size_t hvp_bytes() {
+  return (size_t)HvpBlock<T>::size * HVP_SLOTS *
+         ((SLOT_WORDS + HVP_BAR_WORDS) * sizeof(T) + sizeof(int));
+}
+
+template <class T, bool BATCH>
+__global__ void __launch_bounds__(HvpBlock<T>::size) k_tersoff_hvp(const __grid_constant__ BwdArgs<T> a,
+                                                                  double* __restrict__ gx) {
+  constexpr int SNS = TERSOFF_MAX_SPECIES;
+  constexpr int ZB = HVP_SLOTS;
+  constexpr int BS = HvpBlock<T>::size;
+  __shared__ T sraw[SNS * SNS * SNS * NP];
+  __shared__ T sfilt[SNS * SNS];
+  extern __shared__ __align__(16) unsigned char hvp_dyn[];
+  T* geo = reinterpret_cast<T*>(hvp_dyn);
+  T* bar = geo + (size_t)ZB * SLOT_WORDS * BS;
+  int* sj = reinterpret_cast<int*>(bar + (size_t)ZB * HVP_BAR_WORDS * BS);
+  const fwd::FwdArgs<T>& g = a.g;
+  const int ns = g.ns;
+  for (int q = threadIdx.x; q < ns * ns * ns * NP; q += blockDim.x) sraw[q] = a.raw[q];
+  if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = g.filt2[threadIdx.x];
+  __shared__ int nb[3];
+  if (threadIdx.x < 3) nb[threadIdx.x] = a.counts[threadIdx.x * FLAG_STRIDE];
+  __syncthreads();
+  const int item = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n01 = nb[0] + nb[1];
+  const int i = item >= g.n ? g.n
+                : item < nb[0] ? a.order[item]
+                : item < n01   ? a.order[(size_t)g.n + item - nb[0]]
+                               : a.order[2 * (size_t)g.n + item - n01];
+  if (i >= g.n) return;
+  using P = typename SelfPos<T>::type;
+  const P pi = self_pos<T>(g, i);
+  fwd::Shift<T, BATCH> sh;
+  sh.load(g, i);
+  const int ti = g.types[i];
+  const int c = min(g.cnt[i], g.cap);
+  const T gfi0 = a.gF[3 * (size_t)i], gfi1 = a.gF[3 * (size_t)i + 1], gfi2 = a.gF[3 * (size_t)i + 2];
+  auto from_list = [&](int s, BondD<T>& b, int& j) -> bool {
+    T dx, dy, dz;
+    Bond<T>::vec(g, sh, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, b.t);
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 <= sfilt[ti * ns + b.t])) return false;
+    b.r = BM<T>::sq(r2);
+    const T ir = T(1) / b.r;
+    b.ux = dx * ir;
+    b.uy = dy * ir;
+    b.uz = dz * ir;
+    const T wx = a.gF[3 * (size_t)j] - gfi0, wy = a.gF[3 * (size_t)j + 1] - gfi1,
+            wz = a.gF[3 * (size_t)j + 2] - gfi2;
+    b.rd = b.ux * wx + b.uy * wy + b.uz * wz;
+    b.px = (wx - b.ux * b.rd) * ir;
+    b.py = (wy - b.uy * b.rd) * ir;
+    b.pz = (wz - b.uz * b.rd) * ir;
+    return true;
+  };
+  // the force term takes minus the derivative of D_w E_i: -bar(d) at atom j,
+  // +bar(d) at the centre
+  double gix = 0.0, giy = 0.0, giz = 0.0;
+  auto scatter = [&](const BondD<T>& b, int j, const BondBar<T>& q) {
+    T dx, dy, dz;
+    bond_vec_bar<T>(b, q, dx, dy, dz);
+    atomicAdd(gx + 3 * (size_t)j, -to_f64(dx));
+    atomicAdd(gx + 3 * (size_t)j + 1, -to_f64(dy));
+    atomicAdd(gx + 3 * (size_t)j + 2, -to_f64(dz));
+    gix += to_f64(dx);
+    giy += to_f64(dy);
+    giz += to_f64(dz);
+  };
+  int z = 0;
+  for (int s = 0; s < c && z <= ZB; ++s) {
+    BondD<T> b;
+    int j;
+    if (!from_list(s, b, j)) continue;
+    if (z < ZB) {
+      put_slot<T>(geo, z, b);
+      sj[z * BS + threadIdx.x] = j;
+      for (int f = 0; f < HVP_BAR_WORDS; ++f) bar[((size_t)z * HVP_BAR_WORDS + f) * BS + threadIdx.x] = T(0);
+    }
+    ++z;
+  }
+  if (z <= ZB) {
+    // adjoints accumulated per slot, one scatter per bond
+    atom_hvp<T>(sraw, ns, ti, z,
+                [&](int q, BondD<T>& b, int& j) -> bool {
+                  get_slot<T>(geo, q, b);
+                  j = sj[q * BS + threadIdx.x];
+                  return true;
+                },
+                [&](int q, const BondD<T>&, int, const BondBar<T>& v) {
+                  T* p = bar + (size_t)q * HVP_BAR_WORDS * BS + threadIdx.x;
+                  p[0] += v.r;
+                  p[BS] += v.ux;
+                  p[2 * BS] += v.uy;
+                  p[3 * BS] += v.uz;
+                  p[4 * BS] += v.rd;
+                  p[5 * BS] += v.px;
+                  p[6 * BS] += v.py;
+                  p[7 * BS] += v.pz;
+                });
+    for (int q = 0; q < z; ++q) {
+      BondD<T> b;
+      get_slot<T>(geo, q, b);
+      const T* p = bar + (size_t)q * HVP_BAR_WORDS * BS + threadIdx.x;
+      BondBar<T> v;
+      v.r = p[0];
+      v.ux = p[BS];
+      v.uy = p[2 * BS];
+      v.uz = p[3 * BS];
+      v.rd = p[4 * BS];
+      v.px = p[5 * BS];
+      v.py = p[6 * BS];
+      v.pz = p[7 * BS];
+      scatter(b, sj[q * BS + threadIdx.x], v);
+    }
+  } else {
+    // more bonds than slots: bonds recomputed from the list, every adjoint
+    // contribution scattered as it is formed (the map to bar(d) is linear)
+    atom_hvp<T>(sraw, ns, ti, c, from_list,
+                [&](int, const BondD<T>& b, int j, const BondBar<T>& v) { scatter(b, j, v); });
+  }
+  atomicAdd(gx + 3 * (size_t)i, gix);
+  atomicAdd(gx + 3 * (size_t)i + 1, giy);
+  atomicAdd(gx + 3 * (size_t)i + 2, giz);
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int m) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) out[t] = (float)in[t];
@@ -546,8 +878,8 @@ inline const float* weights_t(Ctx* c, const double* gF, cudaStream_t s, float*) 
 }
 
 template <class T>
-int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* grad,
-             cudaStream_t s) {
+BwdArgs<T> make_args(Ctx* c, const T* raw, const double* gE, const double* gF, double* grad,
+                     cudaStream_t s) {
   BwdArgs<T> a;
   fwd::FwdArgs<T>& g = a.g;
   memset(&g, 0, sizeof(g));
@@ -576,6 +908,13 @@ int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* g
   a.order = c->d_bucket;
   a.counts = c->d_flags + flag_bucket(0);
   a.grad = grad;
+  return a;
+}
+
+template <class T>
+int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* grad,
+             cudaStream_t s) {
+  const BwdArgs<T> a = make_args<T>(c, raw, gE, gF, grad, s);
   constexpr int B = BwdBlock<T>::size;
   constexpr size_t dyn = slot_bytes<T>();
   const int grid = (c->n + B - 1) / B;
@@ -595,7 +934,28 @@ int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* g
   return TERSOFF_OK;
 }
 
+template <class T>
+int launch_hvp_t(Ctx* c, const T* raw, const double* gF, double* gx, cudaStream_t s) {
+  const BwdArgs<T> a = make_args<T>(c, raw, nullptr, gF, nullptr, s);
+  constexpr int B = HvpBlock<T>::size;
+  constexpr size_t dyn = hvp_bytes<T>();
+  const int grid = (c->n + B - 1) / B;
+  if (grid > 0) {
+    void (*k)(BwdArgs<T>, double*) = c->n_sys > 0 ? k_tersoff_hvp<T, true> : k_tersoff_hvp<T, false>;
+    TGB_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    k<<<grid, B, dyn, s>>>(a, gx);
+    c->launches++;
+  }
+  TGB_CUDA(c, cudaGetLastError());
+  return TERSOFF_OK;
+}
+
 }  // namespace bwd
+
+int launch_hvp(Ctx* c, const double* gF, double* grad_x, cudaStream_t s) {
+  if (c->precision == TERSOFF_MIXED) return bwd::launch_hvp_t<float>(c, c->d_raw32, gF, grad_x, s);
+  return bwd::launch_hvp_t<double>(c, c->d_raw64, gF, grad_x, s);
+}
 
 int launch_backward(Ctx* c, const double* gE, const double* gF, double* grad, cudaStream_t s) {
   if (c->precision == TERSOFF_MIXED) return bwd::launch_t<float>(c, c->d_raw32, gE, gF, grad, s);

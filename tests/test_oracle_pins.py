@@ -328,3 +328,30 @@ def test_md_energy_conservation():
     etot = thermo[:, 2]
     ke = thermo[:, 1]
     assert np.ptp(etot) < 0.02 * np.ptp(ke)
+
+
+def test_force_derivative_complex_step_vs_fd():
+    # dF/dx by the complex step (a column of minus the Hessian) against central
+    # differences of the oracle's forces; and the Hessian's symmetry
+    table = sic_table()
+    x, t, box = S.packing_cell(n=48, seed=19)
+    nl = oracle.neighbors(x, box, RC)
+    cols = {}
+    for a, c in [(0, 0), (5, 2), (17, 1), (30, 0)]:
+        de, df = oracle.cs_pos(x, t, box, table, nl, a, c, forces=True)
+        h = 1e-5
+        xp, xm = x.copy(), x.copy()
+        xp[a, c] += h
+        xm[a, c] -= h
+        _, fp, _ = oracle.compute(x=xp, types=t, box=box, table=table, nl=nl)
+        _, fm, _ = oracle.compute(x=xm, types=t, box=box, table=table, nl=nl)
+        fd = (fp - fm) / (2 * h)
+        assert np.abs(df - fd).max() <= 1e-6 * np.abs(df).max()
+        _, f0, _ = oracle.compute(x, t, box, table, nl)
+        assert abs(de + f0[a, c]) <= 1e-10 * np.abs(f0).max()
+        cols[(a, c)] = df
+    # H = -dF/dx is symmetric: dF_b/dx_a = dF_a/dx_b
+    keys = list(cols)
+    for p in keys:
+        for q in keys:
+            assert abs(cols[p][q] - cols[q][p]) <= 1e-9 * np.abs(cols[p]).max()
