@@ -502,7 +502,9 @@ def time_backward(T, ctxm, xdm, ctx64, xd64, flush, reps=10):
     import torch
     stream = torch.cuda.current_stream()
     out = {"what": "tersoff_backward: d/dtheta [gE E + sum gF . F] for all table entries, "
-                   "random gF; forward = tersoff_compute (energy, forces, virial)",
+                   "random gF (backward_ms), and d/dx of the same loss = -gE F - H gF "
+                   "(position_grad_ms: forces plus the Hessian-vector product); "
+                   "forward = tersoff_compute (energy, forces, virial)",
            "atoms": int(xdm.shape[0])}
     for name, ctx, xd in (("mixed", ctxm, xdm), ("fp64", ctx64, xd64)):
         n = xd.shape[0]
@@ -514,13 +516,17 @@ def time_backward(T, ctxm, xdm, ctx64, xd64, flush, reps=10):
         e = torch.empty(1, dtype=torch.float64, device=xd.device)
         f = torch.empty_like(xd)
         w = torch.empty(6, dtype=torch.float64, device=xd.device)
+        gx = torch.empty_like(xd)
         for _ in range(2):
             ctx.backward(xd, gE, gF, None, grad)
+            ctx.backward(xd, gE, gF, gx, None)
             ctx.compute(xd, e, f, w)
         torch.cuda.synchronize()
         bw = _event_time(lambda: ctx.backward(xd, gE, gF, None, grad), reps, flush, stream)
+        px = _event_time(lambda: ctx.backward(xd, gE, gF, gx, None), reps, flush, stream)
         fw = _event_time(lambda: ctx.compute(xd, e, f, w), reps, flush, stream)
-        out[name] = {"backward_ms": bw, "forward_ms": fw, "backward_over_forward": bw / fw,
+        out[name] = {"backward_ms": bw, "position_grad_ms": px, "forward_ms": fw,
+                     "backward_over_forward": bw / fw, "position_grad_over_forward": px / fw,
                      "backward_atoms_per_s": n / (bw * 1e-3)}
     return out
 
@@ -942,6 +948,8 @@ def run_profile_case(args):
             ctx.compute(xd, e, fd)
         elif args.only == "backward":
             ctx.backward(xd, gE, gF, None, g)
+        elif args.only == "hvp":
+            ctx.backward(xd, gE, gF, fd, None)
         else:
             ctx.md_step(xd, vd, fd, mass, DT, MD_PER_STEP, MD_PER_STEP)
     torch.cuda.synchronize()
@@ -957,12 +965,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the single-evaluation workloads and the backward timing")
-    ap.add_argument("--only", choices=["force", "md", "force-sic", "backward", "backward-batch"],
+    ap.add_argument("--only", choices=["force", "md", "force-sic", "backward", "backward-batch", "hvp"],
                     default=None,
-                    help="profiling case: K force evaluations, K MD rebuild periods or K "
-                         "backward passes of the benchmark workload, K force evaluations of "
-                         "the 2.1M-atom SiC workload, or K backward passes of 64 packing "
-                         "cells; nothing printed")
+                    help="profiling case: K force evaluations, K MD rebuild periods, K "
+                         "parameter backward passes or K position gradients (hvp) of the "
+                         "benchmark workload, K force evaluations of the 2.1M-atom SiC "
+                         "workload, or K backward passes of 64 packing cells; nothing printed")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--ablations", action="store_true",
                     help="the paper's design choices switched off one at a time (one JSON line)")

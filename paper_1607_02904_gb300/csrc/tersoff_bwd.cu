@@ -609,13 +609,27 @@ __device__ __forceinline__ void bond_vec_bar(const BondD<T>& b, BondBar<T> q, T&
   dz = (q.uz - uu * b.uz) * ir + q.r * b.uz;
 }
 
+// The three-body factor of one (j, k) pair and what the Hessian-vector pass
+// needs of it: T = F3(r_k) G(cos) X(r_j - r_k) with first and second
+// derivatives. Tables with lambda3 = 0 everywhere (LAM3 false) have X = 1.
+template <class T, bool LAM3> struct Tri {
+  D2<T> F3, G, X;
+  __device__ __forceinline__ Tri(const T* sraw, int q, T rj, T rk, T cs) {
+    F3 = cutoff2<T>(rk, rec_val(sraw, q, TERSOFF_P_R), rec_val(sraw, q, TERSOFF_P_D_CUT));
+    G = angular2<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA), rec_val(sraw, q, TERSOFF_P_C),
+                    rec_val(sraw, q, TERSOFF_P_D), rec_val(sraw, q, TERSOFF_P_H));
+    if constexpr (LAM3)
+      X = expo2<T>(rj - rk, rec_val(sraw, q, TERSOFF_P_LAMBDA3), (int)rec_val(sraw, q, TERSOFF_P_M));
+  }
+};
+
 // Reverse-mode derivative of D_w E_i with respect to the geometry of the
 // centre atom's bonds, in Algorithm 2's loop order: per bond j a first K loop
 // forms zeta_ij and its rate, the pair level seeds the adjoints, and a second
 // K loop adds the adjoints of every three-body term's inputs. get(q, bond, j)
 // returns bond q (false outside the filter radius); sink(q, bond, j, bar)
 // receives additive adjoint contributions for bond q.
-template <class T, class Get, class Sink>
+template <class T, bool LAM3, class Get, class Sink>
 __device__ __forceinline__ void atom_hvp(const T* sraw, int ns, int ti, int count, Get get, Sink sink) {
   for (int qj = 0; qj < count; ++qj) {
     BondD<T> bj;
@@ -634,18 +648,20 @@ __device__ __forceinline__ void atom_hvp(const T* sraw, int ns, int ti, int coun
       int jk;
       if (!get(qk, bk, jk)) continue;
       const int q = (ti * ns + tj) * ns + bk.t;
-      const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
-      if (!(bk.r < Rq + Dq)) continue;
+      if (!(bk.r < rec_val(sraw, q, TERSOFF_P_R) + rec_val(sraw, q, TERSOFF_P_D_CUT))) continue;
       const T cs = bj.ux * bk.ux + bj.uy * bk.uy + bj.uz * bk.uz;
       const T csd = (bj.px * bk.ux + bj.py * bk.uy + bj.pz * bk.uz) +
                     (bk.px * bj.ux + bk.py * bj.uy + bk.pz * bj.uz);
-      const D2<T> F3 = cutoff2<T>(bk.r, Rq, Dq);
-      const D2<T> G = angular2<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA), rec_val(sraw, q, TERSOFF_P_C),
-                                  rec_val(sraw, q, TERSOFF_P_D), rec_val(sraw, q, TERSOFF_P_H));
-      const D2<T> X = expo2<T>(rj - bk.r, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
-                               (int)rec_val(sraw, q, TERSOFF_P_M));
-      zeta += F3.f * G.f * X.f;
-      zd += F3.d1 * bk.rd * G.f * X.f + F3.f * G.d1 * csd * X.f + F3.f * G.f * X.d1 * (rdj - bk.rd);
+      const Tri<T, LAM3> tr(sraw, q, rj, bk.r, cs);
+      const T FG = tr.F3.f * tr.G.f;
+      const T FGd = tr.F3.d1 * bk.rd * tr.G.f + tr.F3.f * tr.G.d1 * csd;
+      if constexpr (LAM3) {
+        zeta += FG * tr.X.f;
+        zd += FGd * tr.X.f + FG * tr.X.d1 * (rdj - bk.rd);
+      } else {
+        zeta += FG;
+        zd += FGd;
+      }
     }
     // pair level: Phi_j = 1/2 (P' + b Q') rd_j + 1/2 Q b' zeta_rate
     const D2<T> fc = cutoff2<T>(rj, Rp, Dp);
@@ -671,29 +687,33 @@ __device__ __forceinline__ void atom_hvp(const T* sraw, int ns, int ti, int coun
         int jk;
         if (!get(qk, bk, jk)) continue;
         const int q = (ti * ns + tj) * ns + bk.t;
-        const T Rq = rec_val(sraw, q, TERSOFF_P_R), Dq = rec_val(sraw, q, TERSOFF_P_D_CUT);
         const T rk = bk.r, rdk = bk.rd;
-        if (!(rk < Rq + Dq)) continue;
+        if (!(rk < rec_val(sraw, q, TERSOFF_P_R) + rec_val(sraw, q, TERSOFF_P_D_CUT))) continue;
         const T cs = bj.ux * bk.ux + bj.uy * bk.uy + bj.uz * bk.uz;
         const T csd = (bj.px * bk.ux + bj.py * bk.uy + bj.pz * bk.uz) +
                       (bk.px * bj.ux + bk.py * bj.uy + bk.pz * bj.uz);
-        const T dl = rdj - rdk;
-        const D2<T> F3 = cutoff2<T>(rk, Rq, Dq);
-        const D2<T> G = angular2<T>(cs, rec_val(sraw, q, TERSOFF_P_GAMMA), rec_val(sraw, q, TERSOFF_P_C),
-                                    rec_val(sraw, q, TERSOFF_P_D), rec_val(sraw, q, TERSOFF_P_H));
-        const D2<T> X = expo2<T>(rj - rk, rec_val(sraw, q, TERSOFF_P_LAMBDA3),
-                                 (int)rec_val(sraw, q, TERSOFF_P_M));
-        const T FG = F3.f * G.f;
-        BondBar<T> ak = zero_bar<T>();
-        ak.r = zb * (F3.d1 * G.f * X.f - FG * X.d1) +
-               zdb * (F3.d2 * rdk * G.f * X.f - F3.d1 * rdk * G.f * X.d1 + F3.d1 * G.d1 * csd * X.f -
-                      F3.f * G.d1 * csd * X.d1 + F3.d1 * G.f * X.d1 * dl - FG * X.d2 * dl);
-        ak.rd = zdb * (F3.d1 * G.f * X.f - FG * X.d1);
-        aj.r += zb * FG * X.d1 + zdb * (F3.d1 * rdk * G.f * X.d1 + F3.f * G.d1 * csd * X.d1 + FG * X.d2 * dl);
-        aj.rd += zdb * FG * X.d1;
-        const T cb = zb * F3.f * G.d1 * X.f +
-                     zdb * (F3.d1 * rdk * G.d1 * X.f + F3.f * G.d2 * csd * X.f + F3.f * G.d1 * X.d1 * dl);
-        const T cdb = zdb * F3.f * G.d1 * X.f;
+        const Tri<T, LAM3> tr(sraw, q, rj, rk, cs);
+        const D2<T>&F3 = tr.F3, &G = tr.G;
+        BondBar<T> ak;
+        T cb, cdb;
+        if constexpr (LAM3) {
+          const D2<T>& X = tr.X;
+          const T dl = rdj - rdk, FG = F3.f * G.f;
+          ak.r = zb * (F3.d1 * G.f * X.f - FG * X.d1) +
+                 zdb * (F3.d2 * rdk * G.f * X.f - F3.d1 * rdk * G.f * X.d1 + F3.d1 * G.d1 * csd * X.f -
+                        F3.f * G.d1 * csd * X.d1 + F3.d1 * G.f * X.d1 * dl - FG * X.d2 * dl);
+          ak.rd = zdb * (F3.d1 * G.f * X.f - FG * X.d1);
+          aj.r += zb * FG * X.d1 + zdb * (F3.d1 * rdk * G.f * X.d1 + F3.f * G.d1 * csd * X.d1 + FG * X.d2 * dl);
+          aj.rd += zdb * FG * X.d1;
+          cb = zb * F3.f * G.d1 * X.f +
+               zdb * (F3.d1 * rdk * G.d1 * X.f + F3.f * G.d2 * csd * X.f + F3.f * G.d1 * X.d1 * dl);
+          cdb = zdb * F3.f * G.d1 * X.f;
+        } else {
+          ak.r = zb * F3.d1 * G.f + zdb * (F3.d2 * rdk * G.f + F3.d1 * G.d1 * csd);
+          ak.rd = zdb * F3.d1 * G.f;
+          cb = zb * F3.f * G.d1 + zdb * (F3.d1 * rdk * G.d1 + F3.f * G.d2 * csd);
+          cdb = zdb * F3.f * G.d1;
+        }
         // cos = u_j . u_k, cos_rate = p_j . u_k + p_k . u_j
         aj.ux += cb * bk.ux + cdb * bk.px;
         aj.uy += cb * bk.uy + cdb * bk.py;
@@ -716,26 +736,28 @@ __device__ __forceinline__ void atom_hvp(const T* sraw, int ns, int ti, int coun
 
 // Per-thread bond slots of the Hessian-vector kernel in dynamic shared memory,
 // thread index innermost: the bond data (9 words, as in the parameter
-// adjoint), its adjoint accumulators (8 words) and the neighbour index.
+// adjoint), its adjoint accumulators (8 words) and the neighbour index. Two
+// shapes: 4 slots in blocks of 128 threads for atoms with at most 4 bonds
+// inside the cutoffs at the list build (bucket 0), 12 slots in blocks of 64
+// for the others. An atom with more bonds than slots inside the filter radius
+// (it has moved since the build, or has more than 12) recomputes its bonds
+// from the skin list and scatters each adjoint contribution as it is formed.
 constexpr int HVP_BAR_WORDS = 8;
-constexpr int HVP_SLOTS = 12;
-template <class T> struct HvpBlock;
-template <> struct HvpBlock<float> { static constexpr int size = 64; };
-template <> struct HvpBlock<double> { static constexpr int size = 32; };
-template <class T>
+template <class T, int ZB, int BS>
 constexpr size_t hvp_bytes() {
-  return (size_t)HvpBlock<T>::size * HVP_SLOTS *
-         ((SLOT_WORDS + HVP_BAR_WORDS) * sizeof(T) + sizeof(int));
+  return (size_t)BS * ZB * ((SLOT_WORDS + HVP_BAR_WORDS) * sizeof(T) + sizeof(int));
 }
 
-template <class T, bool BATCH>
-__global__ void __launch_bounds__(HvpBlock<T>::size) k_tersoff_hvp(const __grid_constant__ BwdArgs<T> a,
-                                                                  double* __restrict__ gx) {
+// Items: the atoms of buckets b0 .. b1 - 1 (bucket order), in a grid-stride
+// loop (grids are sized from the host's bucket counts; the device counts
+// decide).
+template <class T, bool BATCH, bool LAM3, int ZB, int BS>
+__global__ void __launch_bounds__(BS) k_tersoff_hvp(const __grid_constant__ BwdArgs<T> a,
+                                                    double* __restrict__ gx, int b0, int b1) {
   constexpr int SNS = TERSOFF_MAX_SPECIES;
-  constexpr int ZB = HVP_SLOTS;
-  constexpr int BS = HvpBlock<T>::size;
   __shared__ T sraw[SNS * SNS * SNS * NP];
   __shared__ T sfilt[SNS * SNS];
+  __shared__ int nb[3];
   extern __shared__ __align__(16) unsigned char hvp_dyn[];
   T* geo = reinterpret_cast<T*>(hvp_dyn);
   T* bar = geo + (size_t)ZB * SLOT_WORDS * BS;
@@ -744,109 +766,108 @@ __global__ void __launch_bounds__(HvpBlock<T>::size) k_tersoff_hvp(const __grid_
   const int ns = g.ns;
   for (int q = threadIdx.x; q < ns * ns * ns * NP; q += blockDim.x) sraw[q] = a.raw[q];
   if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = g.filt2[threadIdx.x];
-  __shared__ int nb[3];
   if (threadIdx.x < 3) nb[threadIdx.x] = a.counts[threadIdx.x * FLAG_STRIDE];
   __syncthreads();
-  const int item = blockIdx.x * blockDim.x + threadIdx.x;
-  const int n01 = nb[0] + nb[1];
-  const int i = item >= g.n ? g.n
-                : item < nb[0] ? a.order[item]
-                : item < n01   ? a.order[(size_t)g.n + item - nb[0]]
-                               : a.order[2 * (size_t)g.n + item - n01];
-  if (i >= g.n) return;
-  using P = typename SelfPos<T>::type;
-  const P pi = self_pos<T>(g, i);
-  fwd::Shift<T, BATCH> sh;
-  sh.load(g, i);
-  const int ti = g.types[i];
-  const int c = min(g.cnt[i], g.cap);
-  const T gfi0 = a.gF[3 * (size_t)i], gfi1 = a.gF[3 * (size_t)i + 1], gfi2 = a.gF[3 * (size_t)i + 2];
-  auto from_list = [&](int s, BondD<T>& b, int& j) -> bool {
-    T dx, dy, dz;
-    Bond<T>::vec(g, sh, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, b.t);
-    const T r2 = dx * dx + dy * dy + dz * dz;
-    if (!(r2 <= sfilt[ti * ns + b.t])) return false;
-    b.r = BM<T>::sq(r2);
-    const T ir = T(1) / b.r;
-    b.ux = dx * ir;
-    b.uy = dy * ir;
-    b.uz = dz * ir;
-    const T wx = a.gF[3 * (size_t)j] - gfi0, wy = a.gF[3 * (size_t)j + 1] - gfi1,
-            wz = a.gF[3 * (size_t)j + 2] - gfi2;
-    b.rd = b.ux * wx + b.uy * wy + b.uz * wz;
-    b.px = (wx - b.ux * b.rd) * ir;
-    b.py = (wy - b.uy * b.rd) * ir;
-    b.pz = (wz - b.uz * b.rd) * ir;
-    return true;
-  };
-  // the force term takes minus the derivative of D_w E_i: -bar(d) at atom j,
-  // +bar(d) at the centre
-  double gix = 0.0, giy = 0.0, giz = 0.0;
-  auto scatter = [&](const BondD<T>& b, int j, const BondBar<T>& q) {
-    T dx, dy, dz;
-    bond_vec_bar<T>(b, q, dx, dy, dz);
-    atomicAdd(gx + 3 * (size_t)j, -to_f64(dx));
-    atomicAdd(gx + 3 * (size_t)j + 1, -to_f64(dy));
-    atomicAdd(gx + 3 * (size_t)j + 2, -to_f64(dz));
-    gix += to_f64(dx);
-    giy += to_f64(dy);
-    giz += to_f64(dz);
-  };
-  int z = 0;
-  for (int s = 0; s < c && z <= ZB; ++s) {
-    BondD<T> b;
-    int j;
-    if (!from_list(s, b, j)) continue;
-    if (z < ZB) {
-      put_slot<T>(geo, z, b);
-      sj[z * BS + threadIdx.x] = j;
-      for (int f = 0; f < HVP_BAR_WORDS; ++f) bar[((size_t)z * HVP_BAR_WORDS + f) * BS + threadIdx.x] = T(0);
+  int total = 0;
+  for (int b = b0; b < b1; ++b) total += nb[b];
+  for (int item = blockIdx.x * BS + threadIdx.x; item < total; item += gridDim.x * BS) {
+    int b = b0, r = item;
+    while (r >= nb[b]) r -= nb[b++];
+    const int i = a.order[(size_t)b * g.n + r];
+    using P = typename SelfPos<T>::type;
+    const P pi = self_pos<T>(g, i);
+    fwd::Shift<T, BATCH> sh;
+    sh.load(g, i);
+    const int ti = g.types[i];
+    const int c = min(g.cnt[i], g.cap);
+    const T gfi0 = a.gF[3 * (size_t)i], gfi1 = a.gF[3 * (size_t)i + 1], gfi2 = a.gF[3 * (size_t)i + 2];
+    auto from_list = [&](int s, BondD<T>& bd, int& j) -> bool {
+      T dx, dy, dz;
+      Bond<T>::vec(g, sh, pi, g.nbr[(size_t)s * g.n + i], dx, dy, dz, j, bd.t);
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 <= sfilt[ti * ns + bd.t])) return false;
+      bd.r = BM<T>::sq(r2);
+      const T ir = T(1) / bd.r;
+      bd.ux = dx * ir;
+      bd.uy = dy * ir;
+      bd.uz = dz * ir;
+      const T wx = a.gF[3 * (size_t)j] - gfi0, wy = a.gF[3 * (size_t)j + 1] - gfi1,
+              wz = a.gF[3 * (size_t)j + 2] - gfi2;
+      bd.rd = bd.ux * wx + bd.uy * wy + bd.uz * wz;
+      bd.px = (wx - bd.ux * bd.rd) * ir;
+      bd.py = (wy - bd.uy * bd.rd) * ir;
+      bd.pz = (wz - bd.uz * bd.rd) * ir;
+      return true;
+    };
+    // the force term takes minus the derivative of D_w E_i: -bar(d) at atom
+    // j, +bar(d) at the centre
+    double gix = 0.0, giy = 0.0, giz = 0.0;
+    auto scatter = [&](const BondD<T>& bd, int j, const BondBar<T>& q) {
+      T dx, dy, dz;
+      bond_vec_bar<T>(bd, q, dx, dy, dz);
+      atomicAdd(gx + 3 * (size_t)j, -to_f64(dx));
+      atomicAdd(gx + 3 * (size_t)j + 1, -to_f64(dy));
+      atomicAdd(gx + 3 * (size_t)j + 2, -to_f64(dz));
+      gix += to_f64(dx);
+      giy += to_f64(dy);
+      giz += to_f64(dz);
+    };
+    int z = 0;
+    for (int s = 0; s < c && z <= ZB; ++s) {
+      BondD<T> bd;
+      int j;
+      if (!from_list(s, bd, j)) continue;
+      if (z < ZB) {
+        put_slot<T>(geo, z, bd);
+        sj[z * BS + threadIdx.x] = j;
+        for (int f = 0; f < HVP_BAR_WORDS; ++f) bar[((size_t)z * HVP_BAR_WORDS + f) * BS + threadIdx.x] = T(0);
+      }
+      ++z;
     }
-    ++z;
-  }
-  if (z <= ZB) {
-    // adjoints accumulated per slot, one scatter per bond
-    atom_hvp<T>(sraw, ns, ti, z,
-                [&](int q, BondD<T>& b, int& j) -> bool {
-                  get_slot<T>(geo, q, b);
-                  j = sj[q * BS + threadIdx.x];
-                  return true;
-                },
-                [&](int q, const BondD<T>&, int, const BondBar<T>& v) {
-                  T* p = bar + (size_t)q * HVP_BAR_WORDS * BS + threadIdx.x;
-                  p[0] += v.r;
-                  p[BS] += v.ux;
-                  p[2 * BS] += v.uy;
-                  p[3 * BS] += v.uz;
-                  p[4 * BS] += v.rd;
-                  p[5 * BS] += v.px;
-                  p[6 * BS] += v.py;
-                  p[7 * BS] += v.pz;
-                });
-    for (int q = 0; q < z; ++q) {
-      BondD<T> b;
-      get_slot<T>(geo, q, b);
-      const T* p = bar + (size_t)q * HVP_BAR_WORDS * BS + threadIdx.x;
-      BondBar<T> v;
-      v.r = p[0];
-      v.ux = p[BS];
-      v.uy = p[2 * BS];
-      v.uz = p[3 * BS];
-      v.rd = p[4 * BS];
-      v.px = p[5 * BS];
-      v.py = p[6 * BS];
-      v.pz = p[7 * BS];
-      scatter(b, sj[q * BS + threadIdx.x], v);
+    if (z <= ZB) {
+      // adjoints accumulated per slot, one scatter per bond
+      atom_hvp<T, LAM3>(sraw, ns, ti, z,
+                        [&](int q, BondD<T>& bd, int& j) -> bool {
+                          get_slot<T>(geo, q, bd);
+                          j = sj[q * BS + threadIdx.x];
+                          return true;
+                        },
+                        [&](int q, const BondD<T>&, int, const BondBar<T>& v) {
+                          T* p = bar + (size_t)q * HVP_BAR_WORDS * BS + threadIdx.x;
+                          p[0] += v.r;
+                          p[BS] += v.ux;
+                          p[2 * BS] += v.uy;
+                          p[3 * BS] += v.uz;
+                          p[4 * BS] += v.rd;
+                          p[5 * BS] += v.px;
+                          p[6 * BS] += v.py;
+                          p[7 * BS] += v.pz;
+                        });
+      for (int q = 0; q < z; ++q) {
+        BondD<T> bd;
+        get_slot<T>(geo, q, bd);
+        const T* p = bar + (size_t)q * HVP_BAR_WORDS * BS + threadIdx.x;
+        BondBar<T> v;
+        v.r = p[0];
+        v.ux = p[BS];
+        v.uy = p[2 * BS];
+        v.uz = p[3 * BS];
+        v.rd = p[4 * BS];
+        v.px = p[5 * BS];
+        v.py = p[6 * BS];
+        v.pz = p[7 * BS];
+        scatter(bd, sj[q * BS + threadIdx.x], v);
+      }
+    } else {
+      // more bonds than slots: bonds recomputed from the list, every adjoint
+      // contribution scattered as it is formed (the map to bar(d) is linear)
+      atom_hvp<T, LAM3>(sraw, ns, ti, c, from_list,
+                        [&](int, const BondD<T>& bd, int j, const BondBar<T>& v) { scatter(bd, j, v); });
     }
-  } else {
-    // more bonds than slots: bonds recomputed from the list, every adjoint
-    // contribution scattered as it is formed (the map to bar(d) is linear)
-    atom_hvp<T>(sraw, ns, ti, c, from_list,
-                [&](int, const BondD<T>& b, int j, const BondBar<T>& v) { scatter(b, j, v); });
+    atomicAdd(gx + 3 * (size_t)i, gix);
+    atomicAdd(gx + 3 * (size_t)i + 1, giy);
+    atomicAdd(gx + 3 * (size_t)i + 2, giz);
   }
-  atomicAdd(gx + 3 * (size_t)i, gix);
-  atomicAdd(gx + 3 * (size_t)i + 1, giy);
-  atomicAdd(gx + 3 * (size_t)i + 2, giz);
 }
 
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int m) {
@@ -934,20 +955,41 @@ int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* g
   return TERSOFF_OK;
 }
 
-template <class T>
-int launch_hvp_t(Ctx* c, const T* raw, const double* gF, double* gx, cudaStream_t s) {
-  const BwdArgs<T> a = make_args<T>(c, raw, nullptr, gF, nullptr, s);
-  constexpr int B = HvpBlock<T>::size;
-  constexpr size_t dyn = hvp_bytes<T>();
-  const int grid = (c->n + B - 1) / B;
-  if (grid > 0) {
-    void (*k)(BwdArgs<T>, double*) = c->n_sys > 0 ? k_tersoff_hvp<T, true> : k_tersoff_hvp<T, false>;
-    TGB_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
-    k<<<grid, B, dyn, s>>>(a, gx);
-    c->launches++;
-  }
+template <class T, bool BATCH, bool LAM3, int ZB, int BS>
+int launch_hvp_part(Ctx* c, const BwdArgs<T>& a, double* gx, int b0, int b1, cudaStream_t s) {
+  long long items = 0;
+  for (int b = b0; b < b1; ++b) items += c->nbucket[b];
+  // grid from the host's bucket counts (the kernel loops over the device's),
+  // at most 4 waves of the resident blocks
+  constexpr size_t dyn = hvp_bytes<T, ZB, BS>();
+  const int per_sm = (int)((200u << 10) / (dyn + 8192));
+  const long long cap = (long long)(c->n_sm > 0 ? c->n_sm : 152) * (per_sm > 0 ? per_sm : 1) * 4;
+  long long grid = (items + BS - 1) / BS + 1;
+  if (grid > cap) grid = cap;
+  void (*k)(BwdArgs<T>, double*, int, int) = k_tersoff_hvp<T, BATCH, LAM3, ZB, BS>;
+  TGB_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  k<<<(int)grid, BS, dyn, s>>>(a, gx, b0, b1);
+  c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;
+}
+
+template <class T, bool BATCH, bool LAM3>
+int launch_hvp_buckets(Ctx* c, const BwdArgs<T>& a, double* gx, cudaStream_t s) {
+  int st = launch_hvp_part<T, BATCH, LAM3, 4, 128>(c, a, gx, 0, 1, s);
+  if (st) return st;
+  return launch_hvp_part<T, BATCH, LAM3, 12, 64>(c, a, gx, 1, 3, s);
+}
+
+template <class T>
+int launch_hvp_t(Ctx* c, const T* raw, const double* gF, double* gx, cudaStream_t s) {
+  if (c->n == 0) return TERSOFF_OK;
+  const BwdArgs<T> a = make_args<T>(c, raw, nullptr, gF, nullptr, s);
+  if (c->n_sys > 0)
+    return c->has_lam3 ? launch_hvp_buckets<T, true, true>(c, a, gx, s)
+                       : launch_hvp_buckets<T, true, false>(c, a, gx, s);
+  return c->has_lam3 ? launch_hvp_buckets<T, false, true>(c, a, gx, s)
+                     : launch_hvp_buckets<T, false, false>(c, a, gx, s);
 }
 
 }  // namespace bwd
