@@ -65,7 +65,7 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
 inline int force_grid(const Ctx* c, int zc) {
   const int full = (c->n + BLOCK - 1) / BLOCK;
   if (c->opt_waves <= 0 || c->n_sm <= 0) return full;
-  const int resident = c->n_sm * (zc <= 4 ? 8 : 4);
+  const int resident = c->n_sm * (zc <= 4 ? 7 : 4);
   const int g = c->opt_waves * resident;
   return g < full ? g : full;
 }
@@ -142,6 +142,7 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   a.all_general = (c->ablate & 2) ? 1 : 0;
   a.f = f;
   a.contrib = c->d_contrib;
+  a.rev = c->d_rev;
   a.atomic_mode = c->scatter_atomic ? 1 : 0;
   a.own = c->d_own;
   a.acc = acc;

@@ -1,10 +1,12 @@
 // Force gathering from per-slot contributions (no atomics on the fast path).
 //
-// The force kernel stores, for every atom i, the force its own terms put on
-// each short-list neighbour (slot q of i) and on i itself. The force on atom j
-// is own_j plus, for every short-list neighbour i of j, the contribution in
-// the slot of i's list that holds j (the reverse slot, found at the build;
-// short-list membership is symmetric). Mixed path: the float contributions are
+// The force kernel stores the force that atom i's terms put on each short-list
+// neighbour j in j's column of the contribution array, at the slot of j's own
+// short list that holds i (the reverse slot, found at the build; short-list
+// membership is symmetric), and the force on i itself in own_i. The force on
+// atom j is own_j plus the slots 0 .. z_j - 1 of its column, read in slot
+// order with coalesced loads and no indirection. Mixed path: the float
+// contributions are
 // summed with error-free transformations (each float addition's rounding
 // error is recovered exactly and accumulated), and the sum and its error term
 // are converted to double and added once: the result carries the exact sum to
@@ -21,9 +23,7 @@ struct GatherArgs {
   int cap;
   int fp64;
   int atomic_mode;  // forces were scattered with FP64 atomics into extra
-  const uint32_t* shortl;
   const int* zcnt;
-  const uint8_t* rev;
   const void* contrib;
   const void* own;
   double* extra;
@@ -80,38 +80,25 @@ __device__ __forceinline__ void gather_force(const GatherArgs& g, int j, double&
     ez = e[2];
     e[0] = e[1] = e[2] = 0.0;
   }
-  // neighbour indices and reverse slots of the first GU entries, loaded
-  // together (independent loads), then the contributions
-  // (the lists have at least GU slots per atom, so these loads do not wait
-  // for the count)
-  constexpr int GU = 8;
-  int nb[GU], rq[GU];
-#pragma unroll
-  for (int p = 0; p < GU; ++p) {
-    const uint32_t e = g.shortl[(size_t)p * g.n + j];
-    const int r = g.rev[(size_t)p * g.n + j];
-    nb[p] = p < z ? (int)(e & ENTRY_JMASK) : 0;
-    rq[p] = p < z ? r : 255;
-  }
+  // the first GU slots are loaded without waiting for the count (every
+  // column has at least GU slots), the rest once it is known
+  constexpr int GU = 4;
   if (!g.fp64) {
-    const float4* c = (const float4*)g.contrib;
+    const float4* c = (const float4*)g.contrib + j;
     const float4 o = ((const float4*)g.own)[j];
     float4 v[GU];
 #pragma unroll
-    for (int p = 0; p < GU; ++p)
-      v[p] = (p < z && rq[p] != 255) ? c[(size_t)rq[p] * g.n + nb[p]] : make_float4(0, 0, 0, 0);
+    for (int p = 0; p < GU; ++p) v[p] = c[(size_t)p * g.n];
     float sx = o.x, sy = o.y, sz = o.z, cx = 0.0f, cy = 0.0f, cz = 0.0f;
 #pragma unroll
-    for (int p = 0; p < GU; ++p) {
-      two_sum_acc(sx, cx, v[p].x);
-      two_sum_acc(sy, cy, v[p].y);
-      two_sum_acc(sz, cz, v[p].z);
-    }
+    for (int p = 0; p < GU; ++p)
+      if (p < z) {
+        two_sum_acc(sx, cx, v[p].x);
+        two_sum_acc(sy, cy, v[p].y);
+        two_sum_acc(sz, cz, v[p].z);
+      }
     for (int p = GU; p < z; ++p) {
-      const int i = (int)(g.shortl[(size_t)p * g.n + j] & ENTRY_JMASK);
-      const int q = g.rev[(size_t)p * g.n + j];
-      if (q == 255) continue;  // no reverse slot: that force went through atomics
-      const float4 w = c[(size_t)q * g.n + i];
+      const float4 w = c[(size_t)p * g.n];
       two_sum_acc(sx, cx, w.x);
       two_sum_acc(sy, cy, w.y);
       two_sum_acc(sz, cz, w.z);
@@ -132,16 +119,13 @@ __device__ __forceinline__ void gather_force(const GatherArgs& g, int j, double&
       fz = gather_f2d(sz) + (gather_f2d(cz) + ez);
     }
   } else {
-    const dpos4* c = (const dpos4*)g.contrib;
+    const dpos4* c = (const dpos4*)g.contrib + j;
     const dpos4 o = ((const dpos4*)g.own)[j];
     fx = o.x + ex;
     fy = o.y + ey;
     fz = o.z + ez;
     for (int p = 0; p < z; ++p) {
-      const int i = p < GU ? nb[p] : (int)(g.shortl[(size_t)p * g.n + j] & ENTRY_JMASK);
-      const int q = p < GU ? rq[p] : g.rev[(size_t)p * g.n + j];
-      if (q == 255) continue;
-      const dpos4 w = c[(size_t)q * g.n + i];
+      const dpos4 w = c[(size_t)p * g.n];
       fx += w.x;
       fy += w.y;
       fz += w.z;
@@ -156,9 +140,7 @@ inline GatherArgs make_gather(Ctx* c) {
   g.cap = c->zs_cap;
   g.fp64 = c->precision == TERSOFF_FP64;
   g.atomic_mode = c->scatter_atomic ? 1 : 0;
-  g.shortl = c->d_short;
   g.zcnt = c->d_zcnt;
-  g.rev = c->d_rev;
   g.contrib = c->d_contrib;
   g.own = c->d_own;
   g.extra = c->d_extra;

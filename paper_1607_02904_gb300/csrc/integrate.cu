@@ -107,7 +107,7 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst) {
 // F: from f on the first step of a call, gathered from the last force
 // evaluation afterwards. All loads of an atom are issued before its stores.
 __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restrict__ x,
-                       double* __restrict__ v, const double* __restrict__ f, Coef cf,
+                       double* __restrict__ v, const double* __restrict__ f, const __grid_constant__ Coef cf,
                        double dt, int kick, int do_pack, double* ke_row, double* acc_zero) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (acc_zero && i < 8) acc_zero[i * ACC_STRIDE] = 0.0;
@@ -185,7 +185,7 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
 
 // closing half kick with gathered forces, which are also written to f
 __global__ void k_final_kick(GatherArgs ga, const int* __restrict__ types,
-                             double* __restrict__ v, double* __restrict__ f, Coef cf,
+                             double* __restrict__ v, double* __restrict__ f, const __grid_constant__ Coef cf,
                              double* ke_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double ke = 0.0;

@@ -209,11 +209,23 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
   }
 }
 
+// Positions in cell order for the candidate scan: slot s of the cell arrays
+// holds the float offsets of atom j = cell_atoms[s] and, in the fourth word,
+// the bits of 4 j + species (j < 2^26, at most 4 species).
+__global__ void k_cell_pos(int n, const int* __restrict__ cell_atoms,
+                           const float4* __restrict__ pos32, float4* __restrict__ posc) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int j = cell_atoms[s];
+  const float4 p = pos32[j];
+  posc[s] = make_float4(p.x, p.y, p.z, __int_as_float(4 * j + __float_as_int(p.w)));
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-    const int* __restrict__ cell_atoms, const __grid_constant__ GridDev g1,
+    const float4* __restrict__ posc, const __grid_constant__ GridDev g1,
     const GridDev* __restrict__ geo,
     const int* __restrict__ atom_sys, double rc2, float lo2, float hi2, int cap,
     uint32_t* __restrict__ nbr, int* __restrict__ cnt, const __grid_constant__ Radii lim,
@@ -251,9 +263,10 @@ __global__ void __launch_bounds__(128) k_neigh(
                                 ((uint32_t)(oz + 1) << 30);
           const int s1 = cell_start[c + 1];
           for (int s = cell_start[c]; s < s1; ++s) {
-            const int j = cell_atoms[s];
+            const float4 pj = posc[s];
+            const int jt = __float_as_int(pj.w);
+            const int j = jt >> 2, tj = jt & 3;
             if (j == i) continue;
-            const float4 pj = pos32[j];
             const float dx = (pj.x - pi.x) + sx;
             const float dy = (pj.y - pi.y) + sy;
             const float dz = (pj.z - pi.z) + sz;
@@ -270,10 +283,10 @@ __global__ void __launch_bounds__(128) k_neigh(
               if (count < cap) nbr[(size_t)count * n + i] = e;
               ++count;
               // short list: within the filter radius plus the margin
-              if (r2 <= lim.r2[ti * ns + __float_as_int(pj.w)]) {
+              if (r2 <= lim.r2[ti * ns + tj]) {
                 if (z < cap) shortl[(size_t)z * n + i] = e;
                 ++z;
-                zw += r2 <= core.r2[ti * ns + __float_as_int(pj.w)] ? 1 : 0;
+                zw += r2 <= core.r2[ti * ns + tj] ? 1 : 0;
               }
             }
           }
@@ -432,7 +445,8 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
     k_scatter<<<nb, B, 0, s>>>(n, c->d_cell_of, c->d_cell_fill, c->d_cell_atoms);
     k_cell_sort<<<(int)((ncell + 255) / 256), 256, 0, s>>>((int)ncell, c->d_cell_start,
                                                            c->d_cell_atoms);
-    c->launches += 2;
+    k_cell_pos<<<nb, B, 0, s>>>(n, c->d_cell_atoms, c->d_pos32, c->d_posc);
+    c->launches += 3;
   }
   const double rc2 = c->r_list * c->r_list;
   // FP32 classification band: the FP32 r^2 of a stencil candidate differs from
@@ -454,12 +468,12 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   if (n > 0) {
     if (batch)
       k_neigh<true><<<(n + 127) / 128, 128, 0, s>>>(
-          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_cell_atoms, g, c->d_geo,
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, c->d_geo,
           c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
           c->d_zcnt, c->d_bucket, c->d_flags);
     else
       k_neigh<false><<<(n + 127) / 128, 128, 0, s>>>(
-          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_cell_atoms, g, nullptr, nullptr,
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
           c->d_bucket, c->d_flags);
     k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,

@@ -160,7 +160,9 @@ template <class T> struct FwdArgs {
   int identity;          // process atoms 0..n-1 directly (no bucket order)
   int all_general;       // ablation: every atom takes the general path (Algorithm 2 loops)
   float dlim2;           // short list valid while max squared displacement <= dlim2
-  void* contrib;         // slot-major per-neighbour force contributions (T4)
+  void* contrib;         // zs_cap x n force contributions (T4), receiver-major: slot p of
+                         // atom j's column holds the force from its p-th short-list neighbour
+  const uint8_t* rev;    // zs_cap x n: slot of i in the short list of i's s-th neighbour
   void* own;             // per-atom force of its own terms (T4)
   int atomic_mode;       // scatter every force with FP64 atomics (no slots)
   double* f;             // fallback forces, accumulated atomically
@@ -358,6 +360,21 @@ __device__ __forceinline__ void store_slot(const FwdArgs<T>& a, void* base, size
                                            T z) {
   ((typename C4<T>::type*)base)[idx] = C4<T>::make(x, y, z);
 }
+// Receiving slot of the force that atom i's terms put on the neighbour j held
+// in entry s of i's short list: slot rev(i, s) of j's column (the entry of j's
+// short list that holds i). Short-list membership is symmetric and no atom
+// appears twice in a list (box edges are at least twice the list radius), so
+// every slot of every column has exactly one writer, and each atom's gather
+// reads its own column.
+template <class T>
+__device__ __forceinline__ size_t recv_slot(const FwdArgs<T>& a, int s, int i, int j) {
+  return (size_t)__ldg(&a.rev[(size_t)s * a.n + i]) * a.n + j;
+}
+template <class T>
+__device__ __forceinline__ int entry_atom(const FwdArgs<T>& a, const uint32_t* list, int s, int i) {
+  return (int)(list[(size_t)s * a.n + i] & ENTRY_JMASK);
+}
+
 template <class T>
 __device__ __forceinline__ void add_slot(const FwdArgs<T>& a, size_t idx, T x, T y, T z) {
   typename C4<T>::type* p = (typename C4<T>::type*)a.contrib + idx;
@@ -398,7 +415,8 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
   const P pi = self_pos<T>(a, i);
   T fix = 0, fiy = 0, fiz = 0;
   if (slots)
-    for (int q = 0; q < c; ++q) store_slot<T>(a, a.contrib, (size_t)q * a.n + i, T(0), T(0), T(0));
+    for (int q = 0; q < c; ++q)
+      store_slot<T>(a, a.contrib, recv_slot(a, q, i, entry_atom(a, list, q, i)), T(0), T(0), T(0));
   for (int sj = 0; sj < c; ++sj) {
     if (use_mask && !((mask >> sj) & 1ull)) continue;
     T dxj, dyj, dzj;
@@ -455,7 +473,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
       Fjz -= dz * gjz;
       const T Fkx = -dz * gkx, Fky = -dz * gky, Fkz = -dz * gkz;
       if (slots)
-        add_slot<T>(a, (size_t)sk * a.n + i, Fkx, Fky, Fkz);
+        add_slot<T>(a, recv_slot(a, sk, i, k), Fkx, Fky, Fkz);
       else
         atomic_add3(a.f, k, to_f64(Fkx), to_f64(Fky), to_f64(Fkz));
       fix -= Fkx;
@@ -469,7 +487,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
       w[5] += dyk * Fkz;
     }
     if (slots)
-      add_slot<T>(a, (size_t)sj * a.n + i, Fjx, Fjy, Fjz);
+      add_slot<T>(a, recv_slot(a, sj, i, j), Fjx, Fjy, Fjz);
     else
       atomic_add3(a.f, j, to_f64(Fjx), to_f64(Fjy), to_f64(Fjz));
     fix -= Fjx;
@@ -488,7 +506,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
     atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
 }
 
-// atomic mode: the gather must see zero in the atom's own and short-list slots
+// atomic mode: the gather must see zero in the atom's own slot and its column
 template <class T>
 __device__ __forceinline__ void clear_slots(const FwdArgs<T>& a, int i) {
   store_slot<T>(a, a.own, (size_t)i, T(0), T(0), T(0));
@@ -543,7 +561,7 @@ __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc
 
 // ---------------------------------------------------------------- the kernel
 template <class T, int NS, int ZC, int MODE, bool BATCH = false>
-__global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
+__global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
   __shared__ T srec_s[SREC];
@@ -679,10 +697,15 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
       const unsigned long long kept = mask;
       // stored short list, not filtered: the ZC entries are loaded without
       // waiting for the count (the list has at least ZC slots per atom)
+      // (with their reverse slots, for the scatter)
       uint32_t pre[ZC];
+      int rv[ZC];
       if (!filtered) {
 #pragma unroll
-        for (int q = 0; q < ZC; ++q) pre[q] = list[(size_t)q * a.n + i];
+        for (int q = 0; q < ZC; ++q) {
+          pre[q] = list[(size_t)q * a.n + i];
+          rv[q] = slots ? (int)__ldg(&a.rev[(size_t)q * a.n + i]) : 0;
+        }
       }
 #pragma unroll
       for (int q = 0; q < ZC; ++q) {
@@ -858,7 +881,9 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
           w[4] += dx * fz[q];
           w[5] += dy * fz[q];
           if (slots)
-            store_slot<T>(a, a.contrib, (size_t)sl * a.n + i, fx[q], fy[q], fz[q]);
+            store_slot<T>(a, a.contrib,
+                          filtered ? recv_slot(a, sl, i, jj[q]) : (size_t)rv[q] * a.n + jj[q],
+                          fx[q], fy[q], fz[q]);
           else
             atomic_add3(a.f, jj[q], to_f64(fx[q]), to_f64(fy[q]), to_f64(fz[q]));
         }
@@ -866,7 +891,8 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 8 : 4)) k_tersoff(const __gr
       if (slots && filtered)  // stored entries outside the cutoffs now get zero
         for (int s = 0; s < z_list; ++s)
           if (!((kept >> s) & 1ull))
-            store_slot<T>(a, a.contrib, (size_t)s * a.n + i, T(0), T(0), T(0));
+            store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, a.shortl, s, i)), T(0),
+                          T(0), T(0));
       if (slots)
         store_slot<T>(a, a.own, (size_t)i, fix, fiy, fiz);
       else
@@ -1014,7 +1040,8 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
       }
       // forces, virial and the stores of the list's slots
       if (slots)  // entries outside the cutoffs get zero; the kept ones are overwritten
-        for (int s = 0; s < c; ++s) store_slot<T>(a, a.contrib, (size_t)s * a.n + i, T(0), T(0), T(0));
+        for (int s = 0; s < c; ++s)
+          store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, list, s, i)), T(0), T(0), T(0));
       T fix = 0, fiy = 0, fiz = 0;
       for (int q = 0; q < z; ++q) {
         const T fx = at(q, 6), fy = at(q, 7), fz = at(q, 8);
@@ -1031,7 +1058,7 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
         w[5] += dy * fz;
         const int s = (int)at(q, 5);
         if (slots) {
-          store_slot<T>(a, a.contrib, (size_t)s * a.n + i, fx, fy, fz);
+          store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, list, s, i)), fx, fy, fz);
         } else {
           int j, ox, oy, oz;
           decode(list[(size_t)s * a.n + i], j, ox, oy, oz);
