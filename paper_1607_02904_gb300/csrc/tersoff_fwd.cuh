@@ -567,25 +567,24 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
   __shared__ T srec_s[SREC];
   __shared__ T sfilt[SNS * SNS];
   const int ns = NS > 0 ? NS : a.ns;
+  // launch-uniform words, read once per block (one load per lane, together)
+  __shared__ int uni[5];
   if (NS != 1)
     for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += BLOCK) srec_s[q] = a.rec[q];
   if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+  if (threadIdx.x < 5) {
+    const int* src = threadIdx.x == 0   ? a.n_items
+                     : threadIdx.x == 1 ? a.flags + FLAG_REV_MISS
+                     : threadIdx.x == 2 ? a.flags + FLAG_DMAX
+                     : threadIdx.x == 3 ? a.n_items2
+                                        : a.n_items3;
+    uni[threadIdx.x] = src ? *src : 0;
+  }
   __syncthreads();
   // parameters: shared memory for several species (type-dependent records),
   // the constant bank for one species (uniform, operands of the FP instructions)
   const T* srec = NS == 1 ? a.prm1 : srec_s;
   constexpr bool LAM3 = MODE == 1;
-
-  // launch-uniform words, read once per block
-  __shared__ int uni[5];
-  if (threadIdx.x == 0) {
-    uni[0] = *a.n_items;
-    uni[1] = a.flags[FLAG_REV_MISS];
-    uni[2] = a.flags[FLAG_DMAX];
-    uni[3] = a.n_items2 ? *a.n_items2 : 0;
-    uni[4] = a.n_items3 ? *a.n_items3 : 0;
-  }
-  __syncthreads();
   const int n_first = uni[0];
   const int n_second = uni[0] + uni[3];
   const int n_items = a.identity ? a.n : n_second + uni[4];
@@ -620,7 +619,19 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
     bool filtered = false;  // the register slots come from a cutoff mask over list
     bool have_mask = false; // mask covers every entry of list (at most 64)
     int z_list = 0;         // stored short-list length (slots mode bookkeeping)
+    using P = typename SelfPos<T>::type;
+    const P pi = self_pos<T>(a, i);
+    // the first ZC stored entries and their reverse slots (for the scatter),
+    // loaded together with the count: every atom has at least 8 list slots, so
+    // they are in bounds whatever the count
+    uint32_t pre[ZC];
+    int rv[ZC];
     if (use_short) {
+#pragma unroll
+      for (int q = 0; q < ZC; ++q) {
+        pre[q] = a.shortl[(size_t)q * a.n + i];
+        rv[q] = slots ? (int)__ldg(&a.rev[(size_t)q * a.n + i]) : 0;
+      }
       z_list = a.zcnt[i];
       ti = a.types[i];
       list = a.shortl;
@@ -689,24 +700,11 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
       general_atom<T, NS, LAM3, BATCH>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
                                        have_mask, mask, eatom_i, w);
     } else {
-      using P = typename SelfPos<T>::type;
-      const P pi = self_pos<T>(a, i);
       // 2. short list into registers
       T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC];
       int jj[ZC], tt[ZC];
       const unsigned long long kept = mask;
-      // stored short list, not filtered: the ZC entries are loaded without
-      // waiting for the count (the list has at least ZC slots per atom)
-      // (with their reverse slots, for the scatter)
-      uint32_t pre[ZC];
-      int rv[ZC];
-      if (!filtered) {
-#pragma unroll
-        for (int q = 0; q < ZC; ++q) {
-          pre[q] = list[(size_t)q * a.n + i];
-          rv[q] = slots ? (int)__ldg(&a.rev[(size_t)q * a.n + i]) : 0;
-        }
-      }
+      // stored short list, not filtered: the entries loaded above
 #pragma unroll
       for (int q = 0; q < ZC; ++q) {
         ux[q] = uy[q] = uz[q] = T(0);
