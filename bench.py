@@ -807,7 +807,9 @@ def run_accuracy(args):
     initial state integrated by the FP64 and the mixed path for args.steps
     velocity-Verlet steps (dt 1 fs, rebuilds on half the skin), total energy
     recorded every step; reports the largest relative deviation of the mixed
-    path's total energy from the FP64 path's, and each path's drift."""
+    path's total energy from the FP64 path's, and each path's drift. The same
+    for the mixed path with single-precision force sums (the paper's
+    all-single mode, ABLATE_FP32_SUMS)."""
     import numpy as np
     import torch
     import workloads as W
@@ -825,8 +827,11 @@ def run_accuracy(args):
            "atoms": int(n), "steps": args.steps, "dt_ps": DT, "temperature_K": 1000.0,
            "rebuild": "on half the skin (r_list 4.0 A)"}
     series = {}
-    for name, prec in (("fp64", T.FP64), ("mixed", T.MIXED)):
+    for name, prec, abl in (("fp64", T.FP64, 0), ("mixed", T.MIXED, 0),
+                            ("fp32_sums", T.MIXED, T.ABLATE_FP32_SUMS)):
         ctx = T.Context(prec)
+        ctx.set_ablation(abl)
+        ctx.set_scatter(T.SCATTER_GATHER)
         ctx.params(table)
         xd = torch.tensor(x, dtype=torch.float64, device="cuda")
         vd = torch.tensor(v, dtype=torch.float64, device="cuda")
@@ -843,12 +848,14 @@ def run_accuracy(args):
         series[name] = np.concatenate(etot)
         out[name + "_seconds"] = time.perf_counter() - t0
         ctx.close()
-    e64, em = series["fp64"], series["mixed"]
+    e64, em, es = series["fp64"], series["mixed"], series["fp32_sums"]
     tt = np.arange(e64.size) * DT * 1e-3  # ns
     out["max_rel_deviation"] = float(np.abs(em - e64).max() / np.abs(e64).max())
     out["final_rel_deviation"] = float(abs(em[-1] - e64[-1]) / abs(e64[-1]))
+    out["fp32_sums_max_rel_deviation"] = float(np.abs(es - e64).max() / np.abs(e64).max())
+    out["fp32_sums_final_rel_deviation"] = float(abs(es[-1] - e64[-1]) / abs(e64[-1]))
     out["paper_bound_rel"] = 2e-5
-    for name, e in (("fp64", e64), ("mixed", em)):
+    for name, e in (("fp64", e64), ("mixed", em), ("fp32_sums", es)):
         out[name + "_drift_eV_per_atom_per_ns"] = float(np.polyfit(tt, e / n, 1)[0])
         out[name + "_etot_first_last_eV"] = [float(e[0]), float(e[-1])]
     print(json.dumps(out), flush=True)
@@ -858,8 +865,11 @@ def run_ablations(args):
     """The paper's design choices measured on the benchmark workload (mixed
     path, default launch options): the stored short list (Sec. IV-D) and the
     register-resident neighbourhood with pre-computed derivatives (Sec. IV-A),
-    each switched off alone and together. Reports ms per 10 MD steps and per
-    force evaluation; the forces are the same up to rounding order."""
+    each switched off alone and together, and the compensated force sums
+    replaced by plain float sums (the paper's all-single accumulation). Reports
+    ms per 10 MD steps and per force evaluation, and the force error against
+    the default mixed path and against the FP64 path (the first three leave
+    the forces unchanged up to rounding order)."""
     import numpy as np
     import torch
     import workloads as W
@@ -871,13 +881,23 @@ def run_ablations(args):
     stream = torch.cuda.current_stream()
     out = {"metric": "ablations of the paper's design choices (mixed path)",
            "workload": workload_name(), "md_ms_per_10_steps": {}, "force_eval_ms": {},
-           "force_rms_rel_vs_default": {}}
+           "force_rms_rel_vs_default": {}, "force_rms_rel_vs_fp64": {}}
     ref = None
+    ctx = T.Context(T.FP64)
+    ctx.params(table)
+    xd = torch.tensor(x, dtype=torch.float64, device="cuda")
+    ctx.neighbor_build(xd, torch.tensor(t, dtype=torch.int32, device="cuda"), box, R_LIST)
+    fd = torch.zeros_like(xd)
+    ctx.compute(xd, None, fd)
+    f64 = fd.cpu().numpy()
+    ctx.close()
     for name, flags in (("default", 0), ("no_short_list", T.ABLATE_NO_SHORT),
                         ("general_path", T.ABLATE_GENERAL),
-                        ("both", T.ABLATE_NO_SHORT | T.ABLATE_GENERAL)):
+                        ("both", T.ABLATE_NO_SHORT | T.ABLATE_GENERAL),
+                        ("fp32_sums", T.ABLATE_FP32_SUMS)):
         ctx = T.Context(T.MIXED)
         ctx.set_ablation(flags)
+        ctx.set_scatter(T.SCATTER_GATHER)
         ctx.params(table)
         xd = torch.tensor(x, dtype=torch.float64, device="cuda")
         vd = torch.tensor(v, dtype=torch.float64, device="cuda")
@@ -889,6 +909,8 @@ def run_ablations(args):
             ref = fr
         out["force_rms_rel_vs_default"][name] = float(np.sqrt(((fr - ref) ** 2).mean()) /
                                                       np.sqrt((ref ** 2).mean()))
+        out["force_rms_rel_vs_fp64"][name] = float(np.sqrt(((fr - f64) ** 2).mean()) /
+                                                   np.sqrt((f64 ** 2).mean()))
         out["force_eval_ms"][name] = _event_time(lambda: ctx.compute(xd, None, fd), args.steps,
                                                  flush, stream)
         for _ in range(3):

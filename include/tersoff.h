@@ -278,9 +278,17 @@ int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
  *   TERSOFF_ABLATE_GENERAL    every atom takes Algorithm 2's loops over its list
  *                             with the three-body terms recomputed in the second K
  *                             loop, instead of the register-resident neighbourhood
- *                             with pre-computed derivatives (Sec. IV-A). */
+ *                             with pre-computed derivatives (Sec. IV-A);
+ *   TERSOFF_ABLATE_FP32_SUMS  mixed path, gather scatter: each atom's force is
+ *                             the plain float sum of its contributions (the
+ *                             single-precision accumulation of the paper's
+ *                             all-single mode, Sec. V-E) instead of the
+ *                             compensated float pair carried into double. This
+ *                             one changes results beyond rounding order: it
+ *                             measures what the compensated sums buy. */
 #define TERSOFF_ABLATE_NO_SHORT 1
 #define TERSOFF_ABLATE_GENERAL 2
+#define TERSOFF_ABLATE_FP32_SUMS 4
 int tersoff_set_ablation(tersoff_ctx* ctx, int flags);
 
 /* One-line text of the last tersoff_autotune: the chosen options and every

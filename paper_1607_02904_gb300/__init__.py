@@ -18,6 +18,7 @@ from ._lib import (  # noqa: F401
     REBUILD_ON_SKIN,
     ABLATE_NO_SHORT,
     ABLATE_GENERAL,
+    ABLATE_FP32_SUMS,
     load,
     library_path,
     declared_symbols,

@@ -29,6 +29,7 @@ NOALLOC_MAX_ATOMS = 65536
 REBUILD_ON_SKIN = -1
 ABLATE_NO_SHORT = 1
 ABLATE_GENERAL = 2
+ABLATE_FP32_SUMS = 4
 
 _lib = None
 
@@ -264,7 +265,8 @@ class Context:
         self._check(self.lib.tersoff_set_launch(self.h, int(waves), int(split), int(block)))
 
     def set_ablation(self, flags):
-        """ABLATE_NO_SHORT | ABLATE_GENERAL, for measuring the design choices."""
+        """ABLATE_NO_SHORT | ABLATE_GENERAL | ABLATE_FP32_SUMS, for measuring the
+        design choices."""
         self._check(self.lib.tersoff_set_ablation(self.h, int(flags)))
 
     def autotune_summary(self):

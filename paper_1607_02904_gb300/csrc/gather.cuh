@@ -23,6 +23,7 @@ struct GatherArgs {
   int cap;
   int fp64;
   int atomic_mode;  // forces were scattered with FP64 atomics into extra
+  int plain;        // mixed path: plain float sums (ablation), no error term
   const int* zcnt;
   const void* contrib;
   const void* own;
@@ -90,18 +91,34 @@ __device__ __forceinline__ void gather_force(const GatherArgs& g, int j, double&
 #pragma unroll
     for (int p = 0; p < GU; ++p) v[p] = c[(size_t)p * g.n];
     float sx = o.x, sy = o.y, sz = o.z, cx = 0.0f, cy = 0.0f, cz = 0.0f;
+    if (g.plain) {  // single-precision accumulation, same order
 #pragma unroll
-    for (int p = 0; p < GU; ++p)
-      if (p < z) {
-        two_sum_acc(sx, cx, v[p].x);
-        two_sum_acc(sy, cy, v[p].y);
-        two_sum_acc(sz, cz, v[p].z);
+      for (int p = 0; p < GU; ++p)
+        if (p < z) {
+          sx = __fadd_rn(sx, v[p].x);
+          sy = __fadd_rn(sy, v[p].y);
+          sz = __fadd_rn(sz, v[p].z);
+        }
+      for (int p = GU; p < z; ++p) {
+        const float4 w = c[(size_t)p * g.n];
+        sx = __fadd_rn(sx, w.x);
+        sy = __fadd_rn(sy, w.y);
+        sz = __fadd_rn(sz, w.z);
       }
-    for (int p = GU; p < z; ++p) {
-      const float4 w = c[(size_t)p * g.n];
-      two_sum_acc(sx, cx, w.x);
-      two_sum_acc(sy, cy, w.y);
-      two_sum_acc(sz, cz, w.z);
+    } else {
+#pragma unroll
+      for (int p = 0; p < GU; ++p)
+        if (p < z) {
+          two_sum_acc(sx, cx, v[p].x);
+          two_sum_acc(sy, cy, v[p].y);
+          two_sum_acc(sz, cz, v[p].z);
+        }
+      for (int p = GU; p < z; ++p) {
+        const float4 w = c[(size_t)p * g.n];
+        two_sum_acc(sx, cx, w.x);
+        two_sum_acc(sy, cy, w.y);
+        two_sum_acc(sz, cz, w.z);
+      }
     }
     if (sc) {  // the caller works with the pair and the fallback term separately
       sc[0] = sx;
@@ -140,6 +157,7 @@ inline GatherArgs make_gather(Ctx* c) {
   g.cap = c->zs_cap;
   g.fp64 = c->precision == TERSOFF_FP64;
   g.atomic_mode = c->scatter_atomic ? 1 : 0;
+  g.plain = (c->ablate & 4) && c->precision == TERSOFF_MIXED;
   g.zcnt = c->d_zcnt;
   g.contrib = c->d_contrib;
   g.own = c->d_own;

@@ -139,5 +139,33 @@ def test_ablations_keep_results(T, prec, flags):
     torch.cuda.synchronize()
     check(prec, (e.item(), f.cpu().numpy(), w.cpu().numpy()), REF)
     with pytest.raises(T.TersoffError):
-        ctx.set_ablation(4)
+        ctx.set_ablation(8)
     ctx.close()
+
+
+@pytest.mark.parametrize("scatter", [0, 1], ids=["gather", "atomic"])
+def test_fp32_sums_ablation(T, scatter):
+    # plain float force sums (the paper's all-single accumulation): still within
+    # the mixed path's tolerance of the oracle; in gather mode they differ from
+    # the compensated sums, in atomic mode (FP64 atomics) they are not used
+    def run(flags):
+        ctx = T.Context(T.MIXED)
+        ctx.set_scatter(scatter)
+        ctx.set_ablation(flags)
+        ctx.params(TABLE)
+        xd = dev(X)
+        ctx.neighbor_build(xd, dev(TY, torch.int32), BOX, RC + 0.5)
+        e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        f = torch.zeros_like(xd)
+        w = torch.zeros(6, dtype=torch.float64, device="cuda")
+        ctx.compute(xd, e, f, w)
+        torch.cuda.synchronize()
+        out = (e.item(), f.cpu().numpy(), w.cpu().numpy())
+        ctx.close()
+        return out
+    plain, comp = run(T.ABLATE_FP32_SUMS), run(0)
+    check(1, plain, REF)
+    if scatter == 0:
+        assert not np.array_equal(plain[1], comp[1])
+    else:
+        assert np.abs(plain[1] - comp[1]).max() <= 1e-12 * np.abs(comp[1]).max()
