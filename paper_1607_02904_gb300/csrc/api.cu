@@ -120,6 +120,7 @@ int ensure_atoms(Ctx* c, int n) {
   if ((st = dev_alloc(c, &c->d_cell_atoms, m))) return st;
   if ((st = dev_alloc(c, &c->d_pos32, m))) return st;
   if ((st = dev_alloc(c, &c->d_posc, m))) return st;
+  if ((st = dev_alloc(c, &c->d_kmask, m))) return st;
   if ((st = dev_alloc(c, &c->d_posq, m))) return st;
   if ((st = dev_alloc(c, &c->d_pos64, m))) return st;
   if ((st = dev_alloc(c, &c->d_fbuf, 3 * m))) return st;
@@ -302,7 +303,7 @@ int tersoff_destroy(tersoff_ctx* p) {
   cudaDeviceSynchronize();
   void* bufs[] = {c->d_rec64, c->d_rec32, c->d_raw64, c->d_raw32, c->d_filt64, c->d_filt32,
                   c->d_types, c->d_cnt, c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
-                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_posq,
+                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_kmask, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
                   c->d_bucket, c->d_snap, c->d_rev, c->d_contrib, c->d_own,

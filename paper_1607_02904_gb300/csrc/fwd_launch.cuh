@@ -143,6 +143,7 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   a.f = f;
   a.contrib = c->d_contrib;
   a.rev = c->d_rev;
+  a.kmask = c->d_kmask;
   a.atomic_mode = c->scatter_atomic ? 1 : 0;
   a.own = c->d_own;
   a.acc = acc;

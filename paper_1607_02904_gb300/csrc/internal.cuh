@@ -160,7 +160,9 @@ struct Ctx {
   double* d_trow = nullptr;       // MD thermo accumulation rows (ACC_LEN doubles per step)
   size_t trow_alloc = 0;
   float4* d_pos32 = nullptr;      // n: (u float, type bits)
-  float4* d_posc = nullptr;       // n, cell order: (u float, bits of 4 j + type)
+  float4* d_posc = nullptr;       // n, cell order: (u float, bits of 4 j + species)
+  unsigned long long* d_kmask = nullptr;  // n: short-list entries whose receiving slot may
+                                          // hold a nonzero force (all ones after a build)
   int4* d_posq = nullptr;         // n: (u fixed point, type)
   dpos4* d_pos64 = nullptr;     // n: (u double, type)
   int* d_flags = nullptr;         // device status words (see FLAG_*)

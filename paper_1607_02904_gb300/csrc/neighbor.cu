@@ -424,6 +424,8 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const int nb = (n + B - 1) / B;
   const double scale = ldexp(1.0, G.fix_shift);
   TGB_CUDA(c, cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (ncell + 1), s));
+  // new slots hold stale forces: every entry of every atom may be nonzero
+  if (n > 0) TGB_CUDA(c, cudaMemsetAsync(c->d_kmask, 0xff, sizeof(unsigned long long) * n, s));
   if (n > 0) {
     if (batch)
       k_bin<true><<<nb, B, 0, s>>>(n, x, g, c->d_geo, c->d_atom_sys, scale, c->d_cell_of,

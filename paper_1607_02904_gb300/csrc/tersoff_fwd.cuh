@@ -163,6 +163,7 @@ template <class T> struct FwdArgs {
   void* contrib;         // zs_cap x n force contributions (T4), receiver-major: slot p of
                          // atom j's column holds the force from its p-th short-list neighbour
   const uint8_t* rev;    // zs_cap x n: slot of i in the short list of i's s-th neighbour
+  unsigned long long* kmask;  // per atom: entries whose receiving slot may be nonzero
   void* own;             // per-atom force of its own terms (T4)
   int atomic_mode;       // scatter every force with FP64 atomics (no slots)
   double* f;             // fallback forces, accumulated atomically
@@ -699,6 +700,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
       if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
       general_atom<T, NS, LAM3, BATCH>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
                                        have_mask, mask, eatom_i, w);
+      if (slots && list == a.shortl) a.kmask[i] = ~0ull;  // every entry written
     } else {
       // 2. short list into registers
       T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC];
@@ -886,11 +888,22 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             atomic_add3(a.f, jj[q], to_f64(fx[q]), to_f64(fy[q]), to_f64(fz[q]));
         }
       }
-      if (slots && filtered)  // stored entries outside the cutoffs now get zero
-        for (int s = 0; s < z_list; ++s)
-          if (!((kept >> s) & 1ull))
-            store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, a.shortl, s, i)), T(0),
-                          T(0), T(0));
+      if (slots && filtered) {
+        // stored entries outside the cutoffs now: their receiving slots get
+        // zero, unless they hold zero already (not kept at the last
+        // evaluation); kept entries were written above
+        unsigned long long clr = a.kmask[i] & ~kept;
+        if (z_list < 64) clr &= (1ull << z_list) - 1ull;
+        while (clr) {
+          const int s = __ffsll(clr) - 1;
+          clr &= clr - 1ull;
+          store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, a.shortl, s, i)), T(0),
+                        T(0), T(0));
+        }
+        a.kmask[i] = kept;
+      } else if (ZC > 4 && slots && z_list > 4) {
+        a.kmask[i] = ~0ull;  // every entry written
+      }
       if (slots)
         store_slot<T>(a, a.own, (size_t)i, fix, fiy, fiz);
       else
@@ -993,6 +1006,7 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
       if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
       general_atom<T, NS, LAM3, false>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
                                        false, 0ull, eatom_i, w);
+      if (slots && list == a.shortl) a.kmask[i] = ~0ull;  // every entry written
     } else {
       for (int qj = 0; qj < z; ++qj) {
         const T uxj = at(qj, 0), uyj = at(qj, 1), uzj = at(qj, 2), rij = at(qj, 3);
@@ -1037,9 +1051,11 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
         at(qj, 8) += Fjz;
       }
       // forces, virial and the stores of the list's slots
-      if (slots)  // entries outside the cutoffs get zero; the kept ones are overwritten
+      if (slots) {  // entries outside the cutoffs get zero; the kept ones are overwritten
         for (int s = 0; s < c; ++s)
           store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, list, s, i)), T(0), T(0), T(0));
+        a.kmask[i] = ~0ull;
+      }
       T fix = 0, fiy = 0, fiz = 0;
       for (int q = 0; q < z; ++q) {
         const T fx = at(q, 6), fy = at(q, 7), fz = at(q, 8);
