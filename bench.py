@@ -727,7 +727,7 @@ def single_evaluations(T, W, dev, flush, cpu=True, reps=20):
     return out
 
 
-def cpu_baseline(x, v, t, box, names, table, nsteps=20):
+def cpu_baseline(x, v, t, box, names, table, nsteps=100):
     """The FP64 oracle on the host cores: full 512,000-atom system, velocity
     Verlet for nsteps steps (rebuild every 10) minus its own setup (one list
     build and one force evaluation), scaled to atom-steps/s."""
