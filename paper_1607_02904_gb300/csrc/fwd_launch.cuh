@@ -19,7 +19,7 @@ template <> inline const double* filt_ptr<double>(Ctx* c) { return c->d_filt64; 
 // over 0.5% of the atoms (e.g. SiC): the slot-cached wide kernel, on the
 // launch's stream after the main launch. A grid of a few waves loops over the
 // bucket (its size lives on the device).
-template <class T, int NS>
+template <class T, int NS, bool BATCH = false>
 void launch_wide(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
   FwdArgs<T> b2 = a;
   b2.order = c->d_bucket + 2 * (size_t)c->n;
@@ -31,7 +31,8 @@ void launch_wide(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
   const int cap = (c->n_sm > 0 ? c->n_sm : 152) * 8;
   const int need = (c->nbucket[2] + WIDE_BLOCK - 1) / WIDE_BLOCK + 1;
   const int grid = need < cap ? need : cap;
-  void (*k)(FwdArgs<T>) = c->has_lam3 ? k_tersoff_wide<T, NS, true> : k_tersoff_wide<T, NS, false>;
+  void (*k)(FwdArgs<T>) =
+      c->has_lam3 ? k_tersoff_wide<T, NS, true, BATCH> : k_tersoff_wide<T, NS, false, BATCH>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   k<<<grid, WIDE_BLOCK, dyn, s>>>(b2);
   c->launches++;
@@ -39,15 +40,15 @@ void launch_wide(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
 
 // Grids are fixed by the atom count (the bucket sizes live on the device), so
 // the launches can be captured in a CUDA graph and replayed across builds.
-template <class T, int NS, int ZC>
+template <class T, int NS, int ZC, bool BATCH = false>
 void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
   if (grid <= 0) return;
   if (c->has_lam3)
-    k_tersoff<T, NS, ZC, 1><<<grid, BLOCK, 0, s>>>(a);
+    k_tersoff<T, NS, ZC, 1, BATCH><<<grid, BLOCK, 0, s>>>(a);
   else if (c->sym_table)
-    k_tersoff<T, NS, ZC, 2><<<grid, BLOCK, 0, s>>>(a);
+    k_tersoff<T, NS, ZC, 2, BATCH><<<grid, BLOCK, 0, s>>>(a);
   else
-    k_tersoff<T, NS, ZC, 0><<<grid, BLOCK, 0, s>>>(a);
+    k_tersoff<T, NS, ZC, 0, BATCH><<<grid, BLOCK, 0, s>>>(a);
   c->launches++;
 }
 
@@ -70,7 +71,7 @@ inline int force_grid(const Ctx* c, int zc) {
   return g < full ? g : full;
 }
 
-template <class T, int NS>
+template <class T, int NS, bool BATCH = false>
 void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
   const bool split1 = c->opt_split < 0 ? (long long)c->nbucket[1] * 20 > (long long)c->n
                                        : (c->opt_split > 0 && c->nbucket[1] > 0);
@@ -88,7 +89,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
     b1.order2 = b1.order3 = nullptr;
     b1.n_items2 = b1.n_items3 = nullptr;
     b1.identity = 0;
-    launch_t<T, NS, 8>(c, b1, force_grid(c, 8), s2);
+    launch_t<T, NS, 8, BATCH>(c, b1, force_grid(c, 8), s2);
   }
   // bucket 0, then bucket 1 (unless split off), then bucket 2 (general path)
   const bool wide = (long long)c->nbucket[2] * 200 > (long long)c->n;
@@ -104,8 +105,8 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
   b0.identity = (split1 || wide) ? 0 : 1;
   {
     TimedRegion tr(c, 0, s);
-    launch_t<T, NS, 4>(c, b0, force_grid(c, 4), s);
-    if (wide) launch_wide<T, NS>(c, a, s);
+    launch_t<T, NS, 4, BATCH>(c, b0, force_grid(c, 4), s);
+    if (wide) launch_wide<T, NS, BATCH>(c, a, s);
   }
   if (fork) {
     cudaEventRecord(c->ev_join, c->side);
@@ -172,23 +173,17 @@ int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
   return TERSOFF_OK;
 }
 
-// Batch of systems: one launch over all atoms in index order with register
-// capacity 8 (the coordination of mixed packings varies widely), per-atom
-// energy and virial for the per-system sums.
+// Batch of systems: the same bucketed launches as for one system (register
+// capacity 4 for the atoms with at most 4 bonds inside the cutoffs, capacity
+// 8 on the side stream for those with 5 to 8 when they are over 5%, the
+// slot-cached wide kernel for the rest when they are over 0.5%), with
+// per-system shifts and per-atom energy and virial for the per-system sums;
+// runtime species count.
 template <class T>
 int launch_batch(Ctx* c, double* f, cudaStream_t s) {
   // energy and virial come from the per-atom stores: no block reduction
   FwdArgs<T> a = make_args<T>(c, f, nullptr, c->d_eatom);
-  const int grid = force_grid(c, 8);
-  if (grid > 0) {
-    if (c->has_lam3)
-      k_tersoff<T, 0, 8, 1, true><<<grid, BLOCK, 0, s>>>(a);
-    else if (c->sym_table)
-      k_tersoff<T, 0, 8, 2, true><<<grid, BLOCK, 0, s>>>(a);
-    else
-      k_tersoff<T, 0, 8, 0, true><<<grid, BLOCK, 0, s>>>(a);
-    c->launches++;
-  }
+  if (c->n > 0) launch_buckets<T, 0, true>(c, a, s);
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;
 }

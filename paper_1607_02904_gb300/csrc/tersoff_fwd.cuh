@@ -931,7 +931,7 @@ constexpr size_t wide_slot_bytes(size_t word) {
   return (size_t)WIDE_BLOCK * WIDE_SLOTS * WIDE_WORDS * word;
 }
 
-template <class T, int NS, bool LAM3>
+template <class T, int NS, bool LAM3, bool BATCH = false>
 __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_constant__ FwdArgs<T> a) {
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
@@ -966,7 +966,10 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
     any = true;
     const int i = a.order[item];
     if (!slots && !a.atomic_mode) clear_slots<T>(a, i);
-    Shift<T, false> sh;
+    Shift<T, BATCH> sh;
+    sh.load(a, i);
+    if (BATCH)
+      for (int q = 0; q < 6; ++q) w[q] = T(0);
     using P = typename SelfPos<T>::type;
     const P pi = self_pos<T>(a, i);
     const int ti = a.types[i];
@@ -1004,7 +1007,7 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
     if (general || z > WIDE_SLOTS) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
       if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
-      general_atom<T, NS, LAM3, false>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
+      general_atom<T, NS, LAM3, BATCH>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
                                        false, 0ull, eatom_i, w);
       if (slots && list == a.shortl) a.kmask[i] = ~0ull;  // every entry written
     } else {
@@ -1086,6 +1089,8 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
     }
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     ei += eatom_i;
+    if (BATCH)
+      for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
   if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T, WIDE_BLOCK>(ei, w, a.acc);
 }
