@@ -121,6 +121,9 @@ int ensure_atoms(Ctx* c, int n) {
   if ((st = dev_alloc(c, &c->d_pos32, m))) return st;
   if ((st = dev_alloc(c, &c->d_posc, m))) return st;
   if ((st = dev_alloc(c, &c->d_kmask, m))) return st;
+  if ((st = dev_alloc(c, &c->d_zw, m))) return st;
+  if ((st = dev_alloc(c, &c->d_fine, m))) return st;
+  if (!c->d_zbins && (st = dev_alloc(c, &c->d_zbins, (size_t)3 * 64))) return st;
   if ((st = dev_alloc(c, &c->d_posq, m))) return st;
   if ((st = dev_alloc(c, &c->d_pos64, m))) return st;
   if ((st = dev_alloc(c, &c->d_fbuf, 3 * m))) return st;
@@ -303,7 +306,7 @@ int tersoff_destroy(tersoff_ctx* p) {
   cudaDeviceSynchronize();
   void* bufs[] = {c->d_rec64, c->d_rec32, c->d_raw64, c->d_raw32, c->d_filt64, c->d_filt32,
                   c->d_types, c->d_cnt, c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
-                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_kmask, c->d_posq,
+                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_kmask, c->d_zw, c->d_fine, c->d_zbins, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
                   c->d_bucket, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
@@ -872,6 +875,7 @@ static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
 
 static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double* mass,
                    double dt, int nsteps, int rebuild_every, double* thermo, cudaStream_t s) {
+  if (c) c->fine_valid = false;  // the steps may rebuild the lists on the device
   int st = tgb::check_ctx(c);
   if (st) return st;
   if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "tersoff_neighbor_build must come first");
@@ -1094,6 +1098,7 @@ std::string opt_text(const TuneOpt& o) {
 int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, const double* mass,
                      double dt, int steps, void* stream) {
   Ctx* c = C(p);
+  if (c) c->fine_valid = false;  // trial steps rebuild the lists
   int st = tgb::check_ctx(c);
   if (st) return st;
   if (!c->have_list) return tgb::fail(c, TERSOFF_E_STATE, "a neighbour build must come first");

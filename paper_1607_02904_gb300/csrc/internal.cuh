@@ -161,6 +161,9 @@ struct Ctx {
   size_t trow_alloc = 0;
   float4* d_pos32 = nullptr;      // n: (u float, type bits)
   float4* d_posc = nullptr;       // n, cell order: (u float, bits of 4 j + species)
+  uint8_t* d_zw = nullptr;        // n: list entries inside the filter radii at the build (capped 63)
+  int* d_fine = nullptr;          // n: atoms ordered by d_zw (backward launches)
+  int* d_zbins = nullptr;         // 3 x 64: counts, offsets, cursors of that order
   unsigned long long* d_kmask = nullptr;  // n: short-list entries whose receiving slot may
                                           // hold a nonzero force (all ones after a build)
   int4* d_posq = nullptr;         // n: (u fixed point, type)
@@ -172,6 +175,8 @@ struct Ctx {
   Coef coef{};                    // the same, passed to the kernels by value
   int steps_since_build = 0;
   int last_rebuilds = 0;          // neighbour rebuilds during the last MD call
+  bool fine_valid = false;        // d_fine matches the current lists (cleared by every build,
+                                  // MD call and autotune; set by the backward that sorts)
 
   // launch options (chosen by tersoff_autotune)
   int opt_waves = 0;   // force kernel grid: 0 = one thread per item; k > 0 = k waves of the

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(128) k_neigh(
     uint32_t* __restrict__ nbr, int* __restrict__ cnt, const __grid_constant__ Radii lim,
     const __grid_constant__ Radii core, int ns,
     uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
-    int* __restrict__ flags) {
+    uint8_t* __restrict__ zwa, int* __restrict__ flags) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
   int count = 0;
@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(128) k_neigh(
     }
     cnt[i] = count;
     zcnt[i] = z;
+    zwa[i] = (uint8_t)(zw < 63 ? zw : 63);
   }
   // block-level aggregation: one atomic per block and word
   __shared__ int s_max[2], s_ovf, s_cnt[3], s_base[3], s_wcnt[4][3];
@@ -402,6 +403,7 @@ int grow(Ctx* c, T** p, size_t* have, size_t need) {
 
 int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const int n = c->n;
+  c->fine_valid = false;
   const Grid& G = c->grid;
   const bool batch = c->n_sys > 0;
   const long ncell = batch ? c->ncell_batch : (long)G.nc[0] * G.nc[1] * G.nc[2];
@@ -472,12 +474,12 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
       k_neigh<true><<<(n + 127) / 128, 128, 0, s>>>(
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, c->d_geo,
           c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
-          c->d_zcnt, c->d_bucket, c->d_flags);
+          c->d_zcnt, c->d_bucket, c->d_zw, c->d_flags);
     else
       k_neigh<false><<<(n + 127) / 128, 128, 0, s>>>(
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
-          c->d_bucket, c->d_flags);
+          c->d_bucket, c->d_zw, c->d_flags);
     k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
                                           c->d_flags);
     c->launches += 2;

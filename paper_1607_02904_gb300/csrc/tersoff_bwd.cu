@@ -50,6 +50,8 @@ template <class T> struct BwdArgs {
   double* grad;           // ns^3 x NP, accumulated
   const int* order;       // atoms by bucket (bonds inside the cutoffs: <= 4, <= 8, more) ...
   const int* counts;      // ... and the three bucket sizes (device, FLAG_STRIDE apart)
+  const int* fine;        // optional: all atoms ordered by their count of bonds inside the
+                          // cutoffs (at the build), which then replaces the bucket order
 };
 
 // ------------------------------------------------------------------ math
@@ -447,7 +449,8 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
   int ti = 0;
   const int item = blockIdx.x * blockDim.x + threadIdx.x;
   const int n01 = nb[0] + nb[1];
-  const int i = item >= g.n ? g.n
+  const int i = item >= g.n   ? g.n
+                : a.fine      ? a.fine[item]
                 : item < nb[0] ? a.order[item]
                 : item < n01   ? a.order[(size_t)g.n + item - nb[0]]
                                : a.order[2 * (size_t)g.n + item - n01];
@@ -870,6 +873,48 @@ __global__ void __launch_bounds__(BS) k_tersoff_hvp(const __grid_constant__ BwdA
   }
 }
 
+// Atoms ordered by their count of list entries inside the filter radii (at
+// the build): neighbouring lanes of the adjoint kernel then run loops of the
+// same length. A counting sort over 64 values: per-block histograms added to
+// global counts, an exclusive scan, and the placement (block base from a
+// global cursor plus the rank inside the block). bins: counts [0, 64),
+// offsets [64, 128), cursors [128, 192).
+__global__ void k_zw_count(int n, const uint8_t* __restrict__ zw, int* __restrict__ bins) {
+  __shared__ int h[64];
+  if (threadIdx.x < 64) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&h[zw[i]], 1);
+  __syncthreads();
+  if (threadIdx.x < 64 && h[threadIdx.x]) atomicAdd(&bins[threadIdx.x], h[threadIdx.x]);
+}
+__global__ void k_zw_scan(int* __restrict__ bins) {
+  if (threadIdx.x != 0) return;
+  int s = 0;
+  for (int b = 0; b < 64; ++b) {
+    bins[64 + b] = s;
+    bins[128 + b] = 0;
+    s += bins[b];
+  }
+}
+__global__ void k_zw_place(int n, const uint8_t* __restrict__ zw, int* __restrict__ bins,
+                           int* __restrict__ fine) {
+  __shared__ int h[64], base[64];
+  if (threadIdx.x < 64) h[threadIdx.x] = 0;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = 0, r = 0;
+  if (i < n) {
+    b = zw[i];
+    r = atomicAdd(&h[b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 64 && h[threadIdx.x])
+    base[threadIdx.x] = bins[64 + threadIdx.x] + atomicAdd(&bins[128 + threadIdx.x], h[threadIdx.x]);
+  __syncthreads();
+  if (i < n) fine[base[b] + r] = i;
+}
+
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int m) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < m) out[t] = (float)in[t];
@@ -928,6 +973,7 @@ BwdArgs<T> make_args(Ctx* c, const T* raw, const double* gE, const double* gF, d
   a.gF = weights_t(c, gF, s, (T*)nullptr);
   a.order = c->d_bucket;
   a.counts = c->d_flags + flag_bucket(0);
+  a.fine = nullptr;
   a.grad = grad;
   return a;
 }
@@ -935,8 +981,21 @@ BwdArgs<T> make_args(Ctx* c, const T* raw, const double* gE, const double* gF, d
 template <class T>
 int launch_t(Ctx* c, const T* raw, const double* gE, const double* gF, double* grad,
              cudaStream_t s) {
-  const BwdArgs<T> a = make_args<T>(c, raw, gE, gF, grad, s);
+  BwdArgs<T> a = make_args<T>(c, raw, gE, gF, grad, s);
   constexpr int B = BwdBlock<T>::size;
+  // atoms by bond count, sorted once per list (the placement order within a
+  // count comes from atomics: sorting again would change the summation order
+  // between calls on the same list); blocks of 256 cover the 64 bins
+  if (c->n > 0 && !c->fine_valid) {
+    const int nb = (c->n + 255) / 256;
+    TGB_CUDA(c, cudaMemsetAsync(c->d_zbins, 0, sizeof(int) * 64, s));
+    k_zw_count<<<nb, 256, 0, s>>>(c->n, c->d_zw, c->d_zbins);
+    k_zw_scan<<<1, 32, 0, s>>>(c->d_zbins);
+    k_zw_place<<<nb, 256, 0, s>>>(c->n, c->d_zw, c->d_zbins, c->d_fine);
+    c->launches += 3;
+    c->fine_valid = true;
+  }
+  if (c->n > 0) a.fine = c->d_fine;
   constexpr size_t dyn = slot_bytes<T>();
   const int grid = (c->n + B - 1) / B;
   if (grid > 0) {
