@@ -103,6 +103,51 @@ def test_batched_compute_matches_oracle(T, prec, scatter):
     ctx.close()
 
 
+def _bcc_dense(n, a, seed):
+    # 8 first and 6 second neighbours inside the Si cutoff: more than 8 bonds
+    g = np.arange(n)
+    base = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    x = np.concatenate([base, base + 0.5]) * a
+    rng = np.random.Generator(np.random.Philox(seed))
+    box = np.full(3, n * a)
+    return W.jitter_gaussian(x, 0.04, rng) % box, np.zeros(len(x), np.int32), box
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_batch_with_dense_cells_wide_kernel(T, prec):
+    # two dense bcc cells (every atom has 13-14 bonds inside the cutoff: the
+    # batch variant of the wide kernel), a SiC crystal and a packing (the
+    # capacity-4 and capacity-8 launches) in one batch, against the oracle
+    cells = [_bcc_dense(5, 2.9, 140), S.sic_cell(n=3, sigma=0.12, seed=141),
+             _bcc_dense(4, 2.95, 142), S.packing_cell(n=120, c_frac=0.4, seed=143)]
+    off = np.cumsum([0] + [len(c[0]) for c in cells]).astype(np.int32)
+    x = np.concatenate([c[0] for c in cells])
+    t = np.concatenate([c[1] for c in cells]).astype(np.int32)
+    boxes = np.stack([c[2] for c in cells])
+    ctx = T.Context(prec)
+    ctx.params(TABLE)
+    xd = dev(x)
+    ctx.neighbor_build_batched(xd, dev(t, torch.int32), off, boxes, R_LIST)
+    ns = len(cells)
+    e = torch.full((ns,), np.nan, dtype=torch.float64, device="cuda")
+    f = torch.full_like(xd, np.nan)
+    w = torch.full((ns, 6), np.nan, dtype=torch.float64, device="cuda")
+    ctx.compute_batched(xd, e, f, w)
+    torch.cuda.synchronize()
+    e, f, w = e.cpu().numpy(), f.cpu().numpy(), w.cpu().numpy()
+    ctx.close()
+    for s, (xs, ts, bs) in enumerate(cells):
+        er, fr, wr = oracle.compute(xs, ts, bs, TABLE, oracle.neighbors(xs, bs, RC))
+        fs = f[off[s]:off[s + 1]]
+        tol = 1e-10 if prec == 0 else 1e-5
+        if prec == 0:
+            assert np.abs(fs - fr).max() <= tol * np.abs(fr).max()
+        else:
+            assert np.sqrt(((fs - fr) ** 2).mean() / (fr ** 2).mean()) <= tol
+        assert abs(e[s] - er) <= tol * abs(er)
+        assert np.abs(w[s] - wr).max() <= tol * np.abs(wr).max()
+
+
 def test_batched_lists_bit_exact(T):
     ctx, xd = batch_ctx(T, 1)
     cap, mx = ctx.neighbor_capacity()
