@@ -376,6 +376,18 @@ __device__ __forceinline__ int entry_atom(const FwdArgs<T>& a, const uint32_t* l
   return (int)(list[(size_t)s * a.n + i] & ENTRY_JMASK);
 }
 
+// An atom whose stored short list was truncated (more entries than its
+// capacity) scatters with atomics; the receiving slots of its stored entries
+// must then read zero.
+template <class T>
+__device__ __forceinline__ void zero_stored(const FwdArgs<T>& a, int i, int z_list) {
+  const int zs = z_list < a.zs_cap ? z_list : a.zs_cap;
+  for (int s = 0; s < zs; ++s)
+    store_slot<T>(a, a.contrib, recv_slot(a, s, i, entry_atom(a, a.shortl, s, i)), T(0), T(0),
+                  T(0));
+  a.kmask[i] = 0ull;
+}
+
 template <class T>
 __device__ __forceinline__ void add_slot(const FwdArgs<T>& a, size_t idx, T x, T y, T z) {
   typename C4<T>::type* p = (typename C4<T>::type*)a.contrib + idx;
@@ -697,7 +709,10 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
     if (!slots && !a.atomic_mode) clear_slots<T>(a, i);
     if (general) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
-      if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
+      if (slots && list != a.shortl) {
+        atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
+        zero_stored<T>(a, i, z_list);
+      }
       general_atom<T, NS, LAM3, BATCH>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
                                        have_mask, mask, eatom_i, w);
       if (slots && list == a.shortl) a.kmask[i] = ~0ull;  // every entry written
@@ -1006,7 +1021,10 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
     T eatom_i = T(0);
     if (general || z > WIDE_SLOTS) {
       atomicAdd(&a.flags[FLAG_FALLBACK], 1);
-      if (slots && list != a.shortl) atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
+      if (slots && list != a.shortl) {
+        atomicOr(&a.flags[FLAG_EXTRA_STICKY], 1);
+        zero_stored<T>(a, i, a.zcnt[i]);
+      }
       general_atom<T, NS, LAM3, BATCH>(a, sh, srec, i, ti, list, c, slots && list == a.shortl,
                                        false, 0ull, eatom_i, w);
       if (slots && list == a.shortl) a.kmask[i] = ~0ull;  // every entry written
