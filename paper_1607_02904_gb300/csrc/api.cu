@@ -304,7 +304,7 @@ int tersoff_destroy(tersoff_ctx* p) {
   Ctx* c = &p->impl;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  void* bufs[] = {c->d_rec64, c->d_rec32, c->d_raw64, c->d_raw32, c->d_filt64, c->d_filt32,
+  void* bufs[] = {c->d_rec64, c->d_rec32, c->d_raw64, c->d_raw32, c->d_filt64, c->d_filt32, c->d_near32,
                   c->d_types, c->d_cnt, c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
                   c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_kmask, c->d_zw, c->d_fine, c->d_zbins, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
@@ -394,11 +394,15 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
     o[tgb::K_DFC2] = -tgb::PI / (4.0 * D);
     o[tgb::K_RIN2] = R - D;
     o[tgb::K_ROUT2] = R + D;
+    o[tgb::K_ROUT3LO] = 0.0;
+    o[tgb::K_ROUT2LO] = 0.0;
     if (t[TERSOFF_P_LAMBDA3] != 0.0) lam3 = true;
     float* of = &r32[(size_t)r * tgb::RSTRIDE];
     for (int k = 0; k < tgb::RSTRIDE; ++k) of[k] = (float)o[k];
     of[tgb::K_LAM1LO] = (float)(o[tgb::K_LAM1] - (double)of[tgb::K_LAM1]);
     of[tgb::K_LAM2LO] = (float)(o[tgb::K_LAM2] - (double)of[tgb::K_LAM2]);
+    of[tgb::K_ROUT3LO] = (float)(o[tgb::K_ROUT3] - (double)of[tgb::K_ROUT3]);
+    of[tgb::K_ROUT2LO] = (float)(o[tgb::K_ROUT2] - (double)of[tgb::K_ROUT2]);
   }
   // symmetric three-body terms: gamma, c, d, h of (i,j,k) equal those of
   // (i,k,j), and the R, D of f_C(r_ik) do not depend on j
@@ -417,13 +421,20 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
   // filter radius for (ti, tx): largest outer cutoff of any term in which an
   // atom of type tx is the bond partner j or the third atom k of a type-ti atom
   std::vector<double> filt((size_t)ns * ns, 0.0);
+  std::vector<float> near32((size_t)ns * ns, 0.0f);
   double rmax = 0.0;
   for (int ti = 0; ti < ns; ++ti)
     for (int tx = 0; tx < ns; ++tx) {
       double rf = r64[(size_t)((ti * ns + tx) * ns + tx) * tgb::RSTRIDE + tgb::K_ROUT2];
-      for (int tj = 0; tj < ns; ++tj)
-        rf = std::fmax(rf, r64[(size_t)((ti * ns + tj) * ns + tx) * tgb::RSTRIDE + tgb::K_ROUT3]);
+      double rn = rf;  // and the smallest such cutoff
+      for (int tj = 0; tj < ns; ++tj) {
+        const double r3 = r64[(size_t)((ti * ns + tj) * ns + tx) * tgb::RSTRIDE + tgb::K_ROUT3];
+        rf = std::fmax(rf, r3);
+        rn = std::fmin(rn, r3);
+      }
       filt[(size_t)ti * ns + tx] = rf;
+      const double rl = std::fmax(rn - 2e-3, 0.0);
+      near32[(size_t)ti * ns + tx] = (float)(rl * rl);
       rmax = std::fmax(rmax, rf);
     }
   std::vector<double> f64(filt.size());
@@ -438,6 +449,7 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
   if ((st = tgb::dev_alloc(c, &c->d_rec32, r32.size()))) return st;
   if ((st = tgb::dev_alloc(c, &c->d_filt64, f64.size()))) return st;
   if ((st = tgb::dev_alloc(c, &c->d_filt32, f32.size()))) return st;
+  if ((st = tgb::dev_alloc(c, &c->d_near32, near32.size()))) return st;
   TGB_CUDA(c, cudaMemcpy(c->d_rec64, r64.data(), sizeof(double) * r64.size(), cudaMemcpyHostToDevice));
   TGB_CUDA(c, cudaMemcpy(c->d_rec32, r32.data(), sizeof(float) * r32.size(), cudaMemcpyHostToDevice));
   {
@@ -452,6 +464,8 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
   }
   TGB_CUDA(c, cudaMemcpy(c->d_filt64, f64.data(), sizeof(double) * f64.size(), cudaMemcpyHostToDevice));
   TGB_CUDA(c, cudaMemcpy(c->d_filt32, f32.data(), sizeof(float) * f32.size(), cudaMemcpyHostToDevice));
+  TGB_CUDA(c, cudaMemcpy(c->d_near32, near32.data(), sizeof(float) * near32.size(),
+                         cudaMemcpyHostToDevice));
   c->gen++;
   c->ns = ns;
   c->h_rec64 = r64;

@@ -128,6 +128,7 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   a.rec = rec_ptr<T>(c);
   for (int q = 0; q < RSTRIDE; ++q) a.prm1[q] = rec_host<T>(c)[q];
   a.filt2 = filt_ptr<T>(c);
+  a.near2 = c->d_near32;
   const double scale = ldexp(1.0, c->grid.fix_shift);
   for (int q = 0; q < 3; ++q) {
     a.h[q] = (T)c->grid.h[q];

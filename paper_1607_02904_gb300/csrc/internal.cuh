@@ -48,6 +48,8 @@ enum : int {
   K_DFC2,       // -pi / (4 D)
   K_RIN2,       // R - D
   K_ROUT2,      // R + D
+  K_ROUT3LO,    // (R + D) - (T)(R + D) of the three-body record (float records only)
+  K_ROUT2LO,    // the same for the pair record
   RSTRIDE = 32
 };
 
@@ -116,6 +118,8 @@ struct Ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* d_filt64 = nullptr;     // (ti,tj) filter radius^2
   float* d_filt32 = nullptr;
+  float* d_near32 = nullptr;      // (ti,tj): squared (smallest outer cutoff - 2e-3 A); bonds
+                                  // beyond it get their exact length residual (float path)
   std::vector<double> filt;       // host copy, radius (not squared)
   bool has_lam3 = false;
   bool sym_table = false;         // angular terms symmetric in (j,k), f_C(r_ik) j-independent

@@ -145,6 +145,8 @@ template <class T> struct FwdArgs {
   T prm1[RSTRIDE];       // the record of a one-species table (read from the
                          // kernel-parameter constant bank)
   const T* filt2;        // ns x ns squared filter radii
+  const float* near2;    // ns x ns: squared radii beyond which a bond gets its exact length
+                         // residual (float path; unused by the double path)
   T h[3];                // cell edges
   int hq[3];             // cell edges in fixed point
   float qinv;            // 2^-fix_shift
@@ -263,6 +265,36 @@ template <> struct Bond<double> {
   }
 };
 
+// Exact length minus r for the bond to entry e (float path: from the exact
+// fixed-point bond vector, whose squared length is an exact integer; the
+// double path's r is already accurate to rounding: 0).
+template <class T> struct Exact;
+template <> struct Exact<float> {
+  template <bool B>
+  static __device__ float residual(const FwdArgs<float>& a, const Shift<float, B>& sh, int4 qi,
+                                   uint32_t e, float r) {
+    int j, ox, oy, oz;
+    decode(e, j, ox, oy, oz);
+    const int4 qj = __ldg(&a.posq[j]);
+    const long long ix = qj.x - qi.x + ox * sh.hq(a, 0);
+    const long long iy = qj.y - qi.y + oy * sh.hq(a, 1);
+    const long long iz = qj.z - qi.z + oz * sh.hq(a, 2);
+    const double q2 = (double)a.qinv * (double)a.qinv;
+    const double r2 = (double)(ix * ix + iy * iy + iz * iz) * q2;  // exact up to one rounding
+    const double rd = (double)r;
+    return (float)((r2 - rd * rd) / (2.0 * rd));
+  }
+};
+template <> struct Exact<double> {
+  template <bool B>
+  static __device__ double residual(const FwdArgs<double>&, const Shift<double, B>&, dpos4,
+                                    uint32_t, double) {
+    return 0.0;
+  }
+};
+// bonds within this distance of their pair cutoff get the exact residual
+constexpr float NEAR_CUT = 2e-3f;
+
 template <class T> struct SelfPos;
 template <> struct SelfPos<float> { using type = int4; };
 template <> struct SelfPos<double> { using type = dpos4; };
@@ -279,19 +311,31 @@ __device__ __forceinline__ dpos4 self_pos<double>(const FwdArgs<double>& a, int 
 }
 
 // ---------------------------------------------------------------- term pieces
-// f_C and its derivative (Tersoff's cutoff), fields at offsets R, PID, DFC, RIN
+// f_C and its derivative (Tersoff's cutoff), fields at offsets PID (pi/(2D)),
+// DFC (-pi/(4D)), RIN (R - D), ROUT (R + D) and ROUTLO (the rounding residual
+// of R + D in T). In the taper, with delta = R + D - r, f_C = 1/2 - 1/2
+// sin(pi (r - R)/(2D)) = sin^2(pi delta/(4D)) and df_C/dr = -pi/(4D)
+// sin(pi delta/(2D)): the form without cancellation as r reaches R + D, where
+// f_C ~ delta^2 and, for n < 1, the bond order's derivative ~ zeta^(n-1) makes
+// the force sensitive to delta itself. rex: exact r minus r, for bonds within
+// a few thousandths of an Angstrom of a cutoff (0 otherwise).
 template <class T>
-__device__ __forceinline__ void cutoff(const T* p, int kR, int kPID, int kDFC, int kRIN, T r,
-                                       T& fc, T& dfc) {
+__device__ __forceinline__ void cutoff(const T* p, int kPID, int kDFC, int kRIN, int kROUT,
+                                       int kROUTLO, T r, T& fc, T& dfc, T rex = T(0)) {
   if (r <= p[kRIN]) {
     fc = T(1);
     dfc = T(0);
   } else {
+    const T delta = (p[kROUT] - r) + (p[kROUTLO] - rex);
+    if (!(delta > T(0))) {
+      fc = dfc = T(0);
+      return;
+    }
     T s, c;
-    // sin(pi/2 (r-R)/D) = sinpi((r-R)/(2D)); p[kPID] = pi/(2D) so divide by pi
-    M<T>::sincospi_((r - p[kR]) * p[kPID] * T(0.31830988618379067), &s, &c);
-    fc = T(0.5) - T(0.5) * s;
-    dfc = p[kDFC] * c;
+    // sin(pi delta/(4D)) = sinpi(delta/(4D)); p[kPID] / (2 pi) = 1/(4D)
+    M<T>::sincospi_(delta * p[kPID] * T(0.15915494309189534), &s, &c);
+    fc = s * s;
+    dfc = p[kDFC] * (T(2) * s * c);
   }
 }
 
@@ -299,9 +343,9 @@ __device__ __forceinline__ void cutoff(const T* p, int kR, int kPID, int kDFC, i
 //   d zeta = A1 d(cos) + A2 d(r_ij) + (A3 - A2) d(r_ik)
 template <class T, bool LAM3>
 __device__ __forceinline__ void triplet(const T* p3, T rij, T rik, T cs, T& zt, T& A1, T& A2,
-                                        T& A3) {
+                                        T& A3, T rexk = T(0)) {
   T fc, dfc;
-  cutoff<T>(p3, K_R3, K_PID3, K_DFC3, K_RIN3, rik, fc, dfc);
+  cutoff<T>(p3, K_PID3, K_DFC3, K_RIN3, K_ROUT3, K_ROUT3LO, rik, fc, dfc, rexk);
   const T t = p3[K_H] - cs;
   const T t2 = t * t;
   const T q = M<T>::rcp_nr(p3[K_D2] + t2);
@@ -326,11 +370,12 @@ __device__ __forceinline__ void triplet(const T* p3, T rij, T rik, T cs, T& zt, 
 
 // pair part: V = 1/2 fc (fR + b fA), dV/dr, dV/dzeta
 template <class T>
-__device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, T& dz) {
+__device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, T& dz,
+                                     T rexj = T(0)) {
   T b, db;
   M<T>::bond(zeta, p2[K_BETA], p2[K_N], p2[K_NINV2], b, db);
   T fc, dfc;
-  cutoff<T>(p2, K_R2, K_PID2, K_DFC2, K_RIN2, rij, fc, dfc);
+  cutoff<T>(p2, K_PID2, K_DFC2, K_RIN2, K_ROUT2, K_ROUT2LO, rij, fc, dfc, rexj);
   const T er = M<T>::exp_neg_lr(p2[K_LAM1], p2[K_LAM1LO], rij);
   const T ea = M<T>::exp_neg_lr(p2[K_LAM2], p2[K_LAM2LO], rij);
   const T fr = p2[K_A] * er;
@@ -427,6 +472,11 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
   const int ns = NS > 0 ? NS : a.ns;
   const P pi = self_pos<T>(a, i);
   T fix = 0, fiy = 0, fiz = 0;
+  // exact length residual of a bond near a cutoff (float path)
+  auto near_res = [&](uint32_t e, T r2, T r, int tx) -> T {
+    if (sizeof(T) == 4 && r2 > a.near2[ti * ns + tx]) return Exact<T>::residual(a, sh, pi, e, r);
+    return T(0);
+  };
   if (slots)
     for (int q = 0; q < c; ++q)
       store_slot<T>(a, a.contrib, recv_slot(a, q, i, entry_atom(a, list, q, i)), T(0), T(0), T(0));
@@ -439,6 +489,7 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
     const T r2j = dxj * dxj + dyj * dyj + dzj * dzj;
     const T rij = r2j * M<T>::rsqrt_nr(r2j);
     if (!(rij < p2[K_ROUT2])) continue;
+    const T rexj = near_res(list[(size_t)sj * a.n + i], r2j, rij, tj);
     const T rinj = T(1) / rij;
     const T uxj = dxj * rinj, uyj = dyj * rinj, uzj = dzj * rinj;
     T zeta = 0;
@@ -453,11 +504,12 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
       if (!(rik < p3[K_ROUT3])) continue;
       const T cs = (dxj * dxk + dyj * dyk + dzj * dzk) * rinj / rik;
       T zt, A1, A2, A3;
-      triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+      triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3,
+                       near_res(list[(size_t)sk * a.n + i], r2k, rik, tk));
       zeta += zt;
     }
     T V, dVdr, dz;
-    pair<T>(p2, rij, zeta, V, dVdr, dz);
+    pair<T>(p2, rij, zeta, V, dVdr, dz, rexj);
     ei += V;
     T Fjx = -dVdr * uxj, Fjy = -dVdr * uyj, Fjz = -dVdr * uzj;
     for (int sk = 0; sk < c; ++sk) {
@@ -473,7 +525,8 @@ __device__ __forceinline__ void general_atom(const FwdArgs<T>& a, const Shift<T,
       const T uxk = dxk * rink, uyk = dyk * rink, uzk = dzk * rink;
       const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
       T zt, A1, A2, A3;
-      triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+      triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3,
+                       near_res(list[(size_t)sk * a.n + i], r2k, rik, tk));
       // d zeta / d x_j and d x_k
       const T gjx = A1 * (uxk - cs * uxj) * rinj + A2 * uxj;
       const T gjy = A1 * (uyk - cs * uyj) * rinj + A2 * uyj;
@@ -582,9 +635,13 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
   const int ns = NS > 0 ? NS : a.ns;
   // launch-uniform words, read once per block (one load per lane, together)
   __shared__ int uni[5];
+  __shared__ float snear[SNS * SNS];
   if (NS != 1)
     for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += BLOCK) srec_s[q] = a.rec[q];
-  if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+  if (threadIdx.x < ns * ns) {
+    sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+    snear[threadIdx.x] = sizeof(T) == 4 ? a.near2[threadIdx.x] : 0.0f;
+  }
   if (threadIdx.x < 5) {
     const int* src = threadIdx.x == 0   ? a.n_items
                      : threadIdx.x == 1 ? a.flags + FLAG_REV_MISS
@@ -718,7 +775,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
       if (slots && list == a.shortl) a.kmask[i] = ~0ull;  // every entry written
     } else {
       // 2. short list into registers
-      T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC];
+      T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC], rex[ZC];
       int jj[ZC], tt[ZC];
       const unsigned long long kept = mask;
       // stored short list, not filtered: the entries loaded above
@@ -727,6 +784,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
         ux[q] = uy[q] = uz[q] = T(0);
         rr[q] = T(1);
         ri[q] = T(1);
+        rex[q] = T(0);
         jj[q] = i;
         tt[q] = 0;
         if (q < z) {
@@ -745,6 +803,8 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
           const T inv = M<T>::rsqrt_nr(r2);
           ri[q] = inv;
           rr[q] = r2 * inv;
+          if (sizeof(T) == 4 && r2 > snear[ti * ns + tj])  // near a cutoff: exact length
+            rex[q] = Exact<T>::residual(a, sh, pi, e, rr[q]);
           ux[q] = dx * inv;
           uy[q] = dy * inv;
           uz[q] = dz * inv;
@@ -768,7 +828,8 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
           if (q < z) {
             const T* pq = srec + rec_off<NS>(ns, ti, tt[q], tt[q]);
             if (rr[q] < pq[K_ROUT3])
-              cutoff<T>(pq, K_R3, K_PID3, K_DFC3, K_RIN3, rr[q], fc3[q], dfc3[q]);
+              cutoff<T>(pq, K_PID3, K_DFC3, K_RIN3, K_ROUT3, K_ROUT3LO, rr[q], fc3[q], dfc3[q],
+                        rex[q]);
           }
         }
         // pass 1: zeta_ij = sum_k f_C(r_ik) g(theta_ijk)
@@ -793,7 +854,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             const T* p2 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qj]);
             if (rr[qj] < p2[K_ROUT2]) {
               T V, dVdr, dz;
-              pair<T>(p2, rr[qj], zeta[qj], V, dVdr, dz);
+              pair<T>(p2, rr[qj], zeta[qj], V, dVdr, dz, rex[qj]);
               eatom_i += V;
               dzt[qj] = dz;
               fx[qj] -= dVdr * ux[qj];
@@ -844,7 +905,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
                 if (rik < p3[K_ROUT3]) {
                   const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
                   T zt, A1, A2, A3;
-                  triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+                  triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3, rex[qk]);
                   zeta += zt;
                   const T a1j = A1 * ri[qj], a1k = A1 * ri[qk];
                   gjx += a1j * (ux[qk] - cs * ux[qj]) + A2 * ux[qj];
@@ -858,7 +919,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
               }
             }
             T V, dVdr, dz;
-            pair<T>(p2, rij, zeta, V, dVdr, dz);
+            pair<T>(p2, rij, zeta, V, dVdr, dz, rex[qj]);
             eatom_i += V;
             fx[qj] -= dVdr * ux[qj] + dz * gjx;
             fy[qj] -= dVdr * uy[qj] + dz * gjy;
@@ -941,7 +1002,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
 // Atoms with more bonds than slots take the general path.
 constexpr int WIDE_BLOCK = 64;
 constexpr int WIDE_SLOTS = 16;
-constexpr int WIDE_WORDS = 9;  // ux uy uz r t s fx fy fz
+constexpr int WIDE_WORDS = 10;  // ux uy uz r t s fx fy fz, exact length residual
 constexpr size_t wide_slot_bytes(size_t word) {
   return (size_t)WIDE_BLOCK * WIDE_SLOTS * WIDE_WORDS * word;
 }
@@ -958,7 +1019,11 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
   const int ns = NS > 0 ? NS : a.ns;
   if (NS != 1)
     for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += WIDE_BLOCK) srec_s[q] = a.rec[q];
-  if (threadIdx.x < ns * ns) sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+  __shared__ float snear[SNS * SNS];
+  if (threadIdx.x < ns * ns) {
+    sfilt[threadIdx.x] = a.filt2[threadIdx.x];
+    snear[threadIdx.x] = sizeof(T) == 4 ? a.near2[threadIdx.x] : 0.0f;
+  }
   if (threadIdx.x == 0) {
     uni[0] = *a.n_items;
     uni[1] = a.flags[FLAG_REV_MISS];
@@ -1015,6 +1080,9 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
           at(z, 4) = T(tj);
           at(z, 5) = T(s);
           at(z, 6) = at(z, 7) = at(z, 8) = T(0);
+          at(z, 9) = (sizeof(T) == 4 && r2 > snear[ti * ns + tj])
+                         ? Exact<T>::residual(a, sh, pi, list[(size_t)s * a.n + i], r)
+                         : T(0);
         }
         ++z;
       }
@@ -1042,11 +1110,11 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
           if (!(rik < p3[K_ROUT3])) continue;
           const T cs = uxj * at(qk, 0) + uyj * at(qk, 1) + uzj * at(qk, 2);
           T zt, A1, A2, A3;
-          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3, at(qk, 9));
           zeta += zt;
         }
         T V, dVdr, dzv;
-        pair<T>(p2, rij, zeta, V, dVdr, dzv);
+        pair<T>(p2, rij, zeta, V, dVdr, dzv, at(qj, 9));
         eatom_i += V;
         T Fjx = -dVdr * uxj, Fjy = -dVdr * uyj, Fjz = -dVdr * uzj;
         const T rinj = T(1) / rij;
@@ -1058,7 +1126,7 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
           const T uxk = at(qk, 0), uyk = at(qk, 1), uzk = at(qk, 2);
           const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
           T zt, A1, A2, A3;
-          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3);
+          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3, at(qk, 9));
           const T rink = T(1) / rik;
           Fjx -= dzv * (A1 * (uxk - cs * uxj) * rinj + A2 * uxj);
           Fjy -= dzv * (A1 * (uyk - cs * uyj) * rinj + A2 * uyj);
