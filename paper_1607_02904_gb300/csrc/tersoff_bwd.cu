@@ -93,14 +93,17 @@ __device__ __forceinline__ Cut<T> cutoff_ad(T r, T R, T D) {
     o.fc = o.dfc = o.fc_R = o.fc_D = o.dfc_R = o.dfc_D = T(0);
     return o;
   }
-  // x = pi (r - R) / (2 D)
-  const T q = (r - R) / (T(2) * D);
-  T s, c;
-  BM<T>::scpi(q, &s, &c);
+  // x = pi (r - R) / (2 D) = pi/2 - pi delta/(2D), delta = R + D - r: with
+  // sh, ch = sin, cos(pi delta/(4D)), sin x = 1 - 2 sh^2 and cos x = 2 sh ch,
+  // and f_C = 1/2 - 1/2 sin x = sh^2 without cancellation near R + D
+  const T delta = (R + D) - r;
+  T sh, ch;
+  BM<T>::scpi(delta / (T(4) * D), &sh, &ch);
+  const T s = T(1) - T(2) * sh * sh, c = T(2) * sh * ch;
   const T PI = T(3.14159265358979323846);
-  const T x = PI * q;
+  const T x = PI * (r - R) / (T(2) * D);
   const T k = PI / (T(4) * D);  // pi / (4 D)
-  o.fc = T(0.5) - T(0.5) * s;
+  o.fc = sh * sh;
   o.dfc = -k * c;
   o.fc_R = k * c;
   o.fc_D = T(0.5) * c * x / D;
@@ -547,12 +550,13 @@ __device__ __forceinline__ D2<T> cutoff2(T r, T R, T D) {
     o.f = o.d1 = o.d2 = T(0);
     return o;
   }
-  const T q = (r - R) / (T(2) * D);
-  T sn, cn;
-  BM<T>::scpi(q, &sn, &cn);
+  // in delta = R + D - r, as in cutoff_ad: sin x = 1 - 2 sh^2, cos x = 2 sh ch
+  T sh, ch;
+  BM<T>::scpi(((R + D) - r) / (T(4) * D), &sh, &ch);
+  const T sn = T(1) - T(2) * sh * sh, cn = T(2) * sh * ch;
   const T PI = T(3.14159265358979323846);
   const T k = PI / (T(4) * D);
-  o.f = T(0.5) - T(0.5) * sn;
+  o.f = sh * sh;
   o.d1 = -k * cn;
   o.d2 = k * PI / (T(2) * D) * sn;
   return o;
