@@ -43,7 +43,7 @@ PEAK_MUFU_TOPS_NOMINAL = 152 * 16 * 2.07e9 / 1e12  # SMs x special-function ops 
 PEAK_ISSUE_WARP_INST = 152 * 4 * 2.07e9  # SMs x schedulers (one warp instruction each) x clock
 # warp instructions of one force launch on this workload (ncu smsp__inst_executed.sum, the same
 # capture as the traffic); like the traffic, valid only for the sources it was taken with
-FORCE_WARP_INST = 27_386_809
+FORCE_WARP_INST = 28_019_987
 PEAK_FP64_TFLOPS_NOMINAL = 1.25
 
 # Algorithmic FP32 operations of the mixed force kernel per unit of work
@@ -58,9 +58,9 @@ MUFU_SHORT, MUFU_PAIR, MUFU_TRIPLET = 1, 7, 1
 # workload, from an ncu capture (profiles/k_tersoff_si512k_mixed.md). Valid only
 # for the kernel sources it was taken with, identified by their SHA-256; once
 # those change the traffic is reported as null until it is measured again.
-FORCE_TRAFFIC_BYTES = 21_761_024 + 2_755_584
+FORCE_TRAFFIC_BYTES = 23_627_008 + 3_176_960
 FORCE_TRAFFIC_SOURCES = ("tersoff_fwd.cuh", "fwd_launch.cuh", "fwd_f32.cu")
-FORCE_TRAFFIC_SHA256 = "ae02177fa391217d9f7d4d4e86a35c71c31582b864aa64a87842a685435f4811"
+FORCE_TRAFFIC_SHA256 = "df2924a7a5a74c8556af056a8f8d92987ba177303853cb57d948c5f69c36bb16"
 
 
 def ceilings_us(flop, mufu, peaks, kern_ms):

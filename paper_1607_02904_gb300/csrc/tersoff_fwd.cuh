@@ -368,14 +368,13 @@ __device__ __forceinline__ void triplet(const T* p3, T rij, T rik, T cs, T& zt, 
   A3 = dfc * g * ex;
 }
 
-// pair part: V = 1/2 fc (fR + b fA), dV/dr, dV/dzeta
+// pair part: V = 1/2 fc (fR + b fA), dV/dr, dV/dzeta, for given f_C(r_ij)
+// and its derivative
 template <class T>
-__device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, T& dz,
-                                     T rexj = T(0)) {
+__device__ __forceinline__ void pair_fc(const T* p2, T rij, T zeta, T fc, T dfc, T& V, T& dVdr,
+                                        T& dz) {
   T b, db;
   M<T>::bond(zeta, p2[K_BETA], p2[K_N], p2[K_NINV2], b, db);
-  T fc, dfc;
-  cutoff<T>(p2, K_PID2, K_DFC2, K_RIN2, K_ROUT2, K_ROUT2LO, rij, fc, dfc, rexj);
   const T er = M<T>::exp_neg_lr(p2[K_LAM1], p2[K_LAM1LO], rij);
   const T ea = M<T>::exp_neg_lr(p2[K_LAM2], p2[K_LAM2LO], rij);
   const T fr = p2[K_A] * er;
@@ -385,6 +384,14 @@ __device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, 
   // d/dr [fc (fR + b fA)] at fixed b: fR' = -l1 fR, fA' = -l2 fA
   dVdr = T(0.5) * (dfc * s - fc * (p2[K_LAM1] * fr + p2[K_LAM2] * b * fa));
   dz = T(0.5) * fc * fa * db;
+}
+
+template <class T>
+__device__ __forceinline__ void pair(const T* p2, T rij, T zeta, T& V, T& dVdr, T& dz,
+                                     T rexj = T(0)) {
+  T fc, dfc;
+  cutoff<T>(p2, K_PID2, K_DFC2, K_RIN2, K_ROUT2, K_ROUT2LO, rij, fc, dfc, rexj);
+  pair_fc<T>(p2, rij, zeta, fc, dfc, V, dVdr, dz);
 }
 
 template <class T> struct C4;
@@ -776,6 +783,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
     } else {
       // 2. short list into registers
       T ux[ZC], uy[ZC], uz[ZC], rr[ZC], ri[ZC], rex[ZC];
+      T fc3[ZC], dfc3[ZC];  // MODE 2: f_C(r_iq) of the bond's own record
       int jj[ZC], tt[ZC];
       const unsigned long long kept = mask;
       // stored short list, not filtered: the entries loaded above
@@ -785,6 +793,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
         rr[q] = T(1);
         ri[q] = T(1);
         rex[q] = T(0);
+        fc3[q] = dfc3[q] = T(0);
         jj[q] = i;
         tt[q] = 0;
         if (q < z) {
@@ -803,8 +812,17 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
           const T inv = M<T>::rsqrt_nr(r2);
           ri[q] = inv;
           rr[q] = r2 * inv;
+          T rx = T(0);
           if (sizeof(T) == 4 && r2 > snear[ti * ns + tj])  // near a cutoff: exact length
-            rex[q] = Exact<T>::residual(a, sh, pi, e, rr[q]);
+            rx = Exact<T>::residual(a, sh, pi, e, rr[q]);
+          rex[q] = rx;
+          if (MODE == 2) {
+            // symmetric tables: f_C(r_iq) of record (ti, tq, tq) serves both
+            // the three-body terms with k = q and the pair term of bond q
+            const T* pq = srec + rec_off<NS>(ns, ti, tj, tj);
+            if (rr[q] < pq[K_ROUT3])
+              cutoff<T>(pq, K_PID3, K_DFC3, K_RIN3, K_ROUT3, K_ROUT3LO, rr[q], fc3[q], dfc3[q], rx);
+          }
           ux[q] = dx * inv;
           uy[q] = dy * inv;
           uz[q] = dz * inv;
@@ -821,17 +839,9 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
         // zeta(i,j,k) and zeta(i,k,j) is the same, and f_C(r_ik) does not
         // depend on j. Each unordered neighbour pair {j,k} is evaluated once
         // for the zeta sums and once (recomputed) for the forces.
-        T fc3[ZC], dfc3[ZC], zeta[ZC], dzt[ZC];
+        T zeta[ZC], dzt[ZC];
 #pragma unroll
-        for (int q = 0; q < ZC; ++q) {
-          fc3[q] = dfc3[q] = zeta[q] = dzt[q] = T(0);
-          if (q < z) {
-            const T* pq = srec + rec_off<NS>(ns, ti, tt[q], tt[q]);
-            if (rr[q] < pq[K_ROUT3])
-              cutoff<T>(pq, K_PID3, K_DFC3, K_RIN3, K_ROUT3, K_ROUT3LO, rr[q], fc3[q], dfc3[q],
-                        rex[q]);
-          }
-        }
+        for (int q = 0; q < ZC; ++q) zeta[q] = dzt[q] = T(0);
         // pass 1: zeta_ij = sum_k f_C(r_ik) g(theta_ijk)
 #pragma unroll
         for (int qj = 0; qj < ZC; ++qj)
@@ -854,7 +864,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             const T* p2 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qj]);
             if (rr[qj] < p2[K_ROUT2]) {
               T V, dVdr, dz;
-              pair<T>(p2, rr[qj], zeta[qj], V, dVdr, dz, rex[qj]);
+              pair_fc<T>(p2, rr[qj], zeta[qj], fc3[qj], dfc3[qj], V, dVdr, dz);
               eatom_i += V;
               dzt[qj] = dz;
               fx[qj] -= dVdr * ux[qj];
