@@ -81,14 +81,19 @@ inline double dist2(const double* xi, const double* xj, const double* box,
 }
 
 // ---------------------------------------------------------------- pieces of Eq. 5-7
+// In the taper, written in delta = R + D - r: 1/2 - 1/2 sin(pi/2 (r-R)/D) =
+// sin^2(pi delta/(4D)) and -pi/(4D) cos(pi/2 (r-R)/D) = -pi/(4D) sin(pi
+// delta/(2D)) (the same functions; these forms keep their relative accuracy
+// as r -> R + D, where f_C ~ delta^2 and the textbook form cancels).
 template <class T> T f_c(const T& r, const T& R, const T& D) {
   if (re(r) < re(R - D)) return T(1.0);
   if (re(r) > re(R + D)) return T(0.0);
-  return 0.5 - 0.5 * std::sin(0.5 * PI * (r - R) / D);
+  T s = std::sin(0.25 * PI * ((R + D) - r) / D);
+  return s * s;
 }
 template <class T> T f_c_d(const T& r, const T& R, const T& D) {
   if (re(r) < re(R - D) || re(r) > re(R + D)) return T(0.0);
-  return -0.25 * PI / D * std::cos(0.5 * PI * (r - R) / D);
+  return -0.25 * PI / D * std::sin(0.5 * PI * ((R + D) - r) / D);
 }
 template <class T> T g_ang(const T& cs, const T* p) {
   T c2 = p[I_C] * p[I_C], d2 = p[I_D] * p[I_D];

@@ -355,3 +355,31 @@ def test_force_derivative_complex_step_vs_fd():
     for p in keys:
         for q in keys:
             assert abs(cols[p][q] - cols[q][p]) <= 1e-9 * np.abs(cols[p]).max()
+
+
+def test_cutoff_edge_keeps_relative_accuracy():
+    # dimer in the taper just inside R + D (zeta = 0, b = 1): E = f_C(r) (f_R +
+    # f_A) and F = -dE/dr, against 50-digit arithmetic on the same double
+    # inputs. f_C ~ delta^2 there (delta = R + D - r): the textbook
+    # 1/2 - 1/2 sin(...) loses ~1e-16 absolute, 4e-10 relative at delta = 1e-4
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    rec = table.reshape(-1, 14)[0]
+    R, D, A, B, l1, l2 = (mpmath.mpf(float(rec[k])) for k in (10, 11, 13, 9, 12, 8))
+    box = np.array([20.0, 20.0, 20.0])
+    t = np.zeros(2, np.int32)
+
+    def energy(r):
+        fc = mpmath.sin(mpmath.pi * ((R + D) - r) / (4 * D)) ** 2
+        return fc * (A * mpmath.exp(-l1 * r) - B * mpmath.exp(-l2 * r))
+
+    for delta in (1e-2, 1e-3, 1e-4):
+        x = np.array([[5.0, 5.0, 5.0], [5.0 + (3.0 - delta), 5.0, 5.0]])
+        r = mpmath.mpf(float(x[1, 0])) - mpmath.mpf(float(x[0, 0]))  # exact difference
+        e, f, _ = oracle.compute(x, t, box, table, oracle.neighbors(x, box, 3.5))
+        e_ref = energy(r)
+        f_ref = -mpmath.diff(energy, r)  # force on atom 1 along +x
+        assert abs(e - float(e_ref)) <= 1e-11 * abs(float(e_ref)), delta
+        assert abs(f[1, 0] - float(f_ref)) <= 1e-11 * abs(float(f_ref)), delta
+        assert f[0, 0] == -f[1, 0]
