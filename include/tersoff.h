@@ -300,9 +300,9 @@ const char* tersoff_autotune_summary(const tersoff_ctx* ctx);
 int tersoff_md_rebuilds(const tersoff_ctx* ctx, int* count);
 
 /* Force scatter. TERSOFF_SCATTER_GATHER (default): every atom stores the
- * forces its own terms put on each short-list neighbour in per-neighbour
- * slots (plain stores), and the force on an atom is gathered from its
- * neighbours' slots in a fixed order, summed with exact error compensation
+ * force its own terms put on each short-list neighbour in a slot of that
+ * neighbour (plain stores), and the force on an atom is gathered from its own
+ * slots in a fixed order, summed with exact error compensation
  * (mixed path; the rounding error of every float addition is carried and
  * added in double) or in double (FP64 path): deterministic, no atomics.
  * TERSOFF_SCATTER_ATOMIC: every force contribution is added to the force

@@ -311,12 +311,11 @@ int launch_forward_batch_f32(Ctx* c, double* f, cudaStream_t s);
 // (either may be NULL).
 int launch_system_sums(Ctx* c, double* energy, double* virial, cudaStream_t s);
 
-// Force gathering (integrate.cu): F_j = own_j + contributions of the terms of
-// j's short-list neighbours (+ the atomic fallback buffer when flagged), in
-// exact 64-bit fixed point (mixed) or double (FP64), written to f.
+// Force gathering (integrate.cu): F_j = own_j + the slots of j's column (the
+// contributions of the terms of j's short-list neighbours) + the atomic
+// fallback buffer when flagged; compensated float sums carried into double
+// (mixed) or double sums (FP64), written to f.
 int launch_gather(Ctx* c, double* f, cudaStream_t s);
-// Reverse short-list slots (neighbor.cu); after a build.
-int launch_reverse_slots(Ctx* c, cudaStream_t s);
 
 // Velocity Verlet (integrate.cu) with the coefficients c->coef.
 //   step kernel: v += kick * c F (kick = 1 on the first step of a call, with
