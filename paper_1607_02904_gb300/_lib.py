@@ -202,8 +202,10 @@ class Context:
                                              _ptr(forces), _ptr(virial), _stream(stream)))
 
     def backward(self, x, gE, gF=None, grad_x=None, grad_table=None, stream=None):
-        """gE: device float64 (1,); gF: device (N, 3) or None. Writes grad_x
-        (-gE F) and grad_table (d/dtheta [gE E + sum gF . F], flat table layout)."""
+        """gE: device float64 (1,) (one per system in batch mode); gF: device
+        (N, 3) or None. Writes grad_x = d/dx [gE E + sum gF . F] = -gE F - H gF
+        (H the Hessian; -gE F alone when gF is None) and grad_table =
+        d/dtheta [gE E + sum gF . F] (flat table layout); either may be None."""
         self._check(self.lib.tersoff_backward(self.h, _ptr(x), int(x.shape[0]), _ptr(gE), _ptr(gF),
                                               _ptr(grad_x), _ptr(grad_table), _stream(stream)))
 
