@@ -1,5 +1,5 @@
 """Spatial decomposition with a ghost exchange (paper_1607_02904_gb300.halo),
-on CPU ranks: gloo process groups of 2 and 3 ranks, each rank evaluating its
+on CPU ranks: gloo process groups of 2 to 4 ranks, each rank evaluating its
 local system with the oracle.
 
 Owner computes with a ghost shell of 2 r_c: the energy summed over ranks and
@@ -126,7 +126,7 @@ def _worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("world", [2, 3, 4])
 def test_halo_exchange_gloo_ranks(world):
     port = _free_port()
     mgr = mp.get_context("spawn").Manager()
