@@ -383,3 +383,34 @@ def test_cutoff_edge_keeps_relative_accuracy():
         assert abs(e - float(e_ref)) <= 1e-11 * abs(float(e_ref)), delta
         assert abs(f[1, 0] - float(f_ref)) <= 1e-11 * abs(float(f_ref)), delta
         assert f[0, 0] == -f[1, 0]
+
+
+def test_dimer_force_derivative_closed_form():
+    # the Hessian of a dimer (zeta = 0, b = 1, E = f_C (f_R + f_A)): along the
+    # bond dF/dx = -E''(r), across it -E'(r)/r; the oracle's complex-step force
+    # derivative (the reference of the Hessian-vector product) against
+    # 50-digit arithmetic, inside the cutoff region and in the taper
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    rec = table.reshape(-1, 14)[0]
+    R, D, A, B, l1, l2 = (mpmath.mpf(float(rec[k])) for k in (10, 11, 13, 9, 12, 8))
+    box = np.array([20.0, 20.0, 20.0])
+    t = np.zeros(2, np.int32)
+
+    def energy(r):
+        fc = 1 if r <= R - D else mpmath.sin(mpmath.pi * ((R + D) - r) / (4 * D)) ** 2
+        return fc * (A * mpmath.exp(-l1 * r) - B * mpmath.exp(-l2 * r))
+
+    for r0 in (2.35, 2.95):
+        x = np.array([[5.0, 5.0, 5.0], [5.0 + r0, 5.0, 5.0]])
+        r = mpmath.mpf(float(x[1, 0])) - mpmath.mpf(float(x[0, 0]))
+        nl = oracle.neighbors(x, box, 3.5)
+        _, df_along = oracle.cs_pos(x, t, box, table, nl, 1, 0, forces=True)
+        _, df_across = oracle.cs_pos(x, t, box, table, nl, 1, 1, forces=True)
+        e2 = float(mpmath.diff(energy, r, 2))
+        e1 = float(mpmath.diff(energy, r))
+        assert abs(df_along[1, 0] + e2) <= 1e-10 * abs(e2), r0
+        assert abs(df_across[1, 1] + e1 / float(r)) <= 1e-10 * abs(e1 / float(r)), r0
+        # Newton's third law in the derivative
+        assert abs(df_along[0, 0] - e2) <= 1e-10 * abs(e2)
