@@ -414,3 +414,33 @@ def test_dimer_force_derivative_closed_form():
         assert abs(df_across[1, 1] + e1 / float(r)) <= 1e-10 * abs(e1 / float(r)), r0
         # Newton's third law in the derivative
         assert abs(df_along[0, 0] - e2) <= 1e-10 * abs(e2)
+
+
+def test_dimer_parameter_derivatives_closed_form():
+    # dE/dtheta of a dimer (zeta = 0, b = 1) for A, B, lambda1, lambda2, R, D
+    # in the taper, the oracle's complex step against 50-digit differentiation
+    # of E = f_C(r; R, D) (A e^(-lambda1 r) - B e^(-lambda2 r))
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    rec = table.reshape(-1, 14)[0]
+    box = np.array([20.0, 20.0, 20.0])
+    t = np.zeros(2, np.int32)
+    x = np.array([[5.0, 5.0, 5.0], [5.0 + 2.93, 5.0, 5.0]])
+    r = mpmath.mpf(float(x[1, 0])) - mpmath.mpf(float(x[0, 0]))
+    nl = oracle.neighbors(x, box, 3.5)
+    fields = {"A": 13, "B": 9, "lambda1": 12, "lambda2": 8, "R": 10, "D": 11}
+    base = {k: mpmath.mpf(float(rec[v])) for k, v in fields.items()}
+
+    def energy(p):
+        fc = mpmath.sin(mpmath.pi * ((p["R"] + p["D"]) - r) / (4 * p["D"])) ** 2
+        return fc * (p["A"] * mpmath.exp(-p["lambda1"] * r) - p["B"] * mpmath.exp(-p["lambda2"] * r))
+
+    for name, k in fields.items():
+        def along(h, name=name):
+            p = dict(base)
+            p[name] = p[name] + h
+            return energy(p)
+        ref = float(mpmath.diff(along, 0))
+        de, _ = oracle.cs_param(x, t, box, table, nl, k)
+        assert abs(de - ref) <= 1e-10 * abs(ref), (name, de, ref)
