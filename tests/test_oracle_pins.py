@@ -444,3 +444,191 @@ def test_dimer_parameter_derivatives_closed_form():
         ref = float(mpmath.diff(along, 0))
         de, _ = oracle.cs_param(x, t, box, table, nl, k)
         assert abs(de - ref) <= 1e-10 * abs(ref), (name, de, ref)
+
+
+# ----------------------------------------------------------------------------- trimer closed form
+# A centre atom i with two neighbours j and k at unequal distances and an angle
+# away from the tetrahedral one, j and k out of each other's range. Four directed
+# bonds: i->j and i->k carry a bond order with one three-body term each (Eq. 7),
+# j->i and k->i have zeta = 0 (b = 1). E = 1/2 sum of f_C [f_R + b f_A] (Eq. 5-6),
+# written out here from the coordinates in 50-digit arithmetic with the
+# textbook cutoff function, the exponent (lambda3 (r_ij - r_ik))^m, and the
+# record convention: (ti, tj, tk) gives m, gamma, lambda3, c, d, h and the
+# cutoff of f_C(r_ik); (ti, tj, tj) gives the pair terms and f_C(r_ij).
+def _trimer_energy(mp, X, types, rec):
+    """X: three mpf 3-vectors (i, j, k); rec(a, b, c) -> dict of mpf fields."""
+    def sub(a, b):
+        return [X[b][q] - X[a][q] for q in range(3)]
+
+    def norm(v):
+        return mp.sqrt(v[0] ** 2 + v[1] ** 2 + v[2] ** 2)
+
+    def fc(r, R, D):
+        if r < R - D:
+            return mp.mpf(1)
+        if r > R + D:
+            return mp.mpf(0)
+        return mp.mpf(1) / 2 - mp.sin(mp.pi / 2 * (r - R) / D) / 2
+
+    def g(cs, p):
+        c2, d2 = p["c"] ** 2, p["d"] ** 2
+        return p["gamma"] * (1 + c2 / d2 - c2 / (d2 + (p["h"] - cs) ** 2))
+
+    def bond(a, b, third):
+        tp = rec(types[a], types[b], types[b])
+        rab = norm(sub(a, b))
+        zeta = mp.mpf(0)
+        if third is not None:
+            p3 = rec(types[a], types[b], types[third])
+            vab, vac = sub(a, b), sub(a, third)
+            rac = norm(vac)
+            cs = (vab[0] * vac[0] + vab[1] * vac[1] + vab[2] * vac[2]) / (rab * rac)
+            m = int(p3["m"])
+            zeta = fc(rac, p3["R"], p3["D"]) * g(cs, p3) * mp.exp((p3["lambda3"] * (rab - rac)) ** m)
+        b = mp.mpf(1) if zeta == 0 else (1 + (tp["beta"] * zeta) ** tp["n"]) ** (-1 / (2 * tp["n"]))
+        return fc(rab, tp["R"], tp["D"]) * (tp["A"] * mp.exp(-tp["lambda1"] * rab)
+                                             - b * tp["B"] * mp.exp(-tp["lambda2"] * rab)) / 2
+
+    return bond(0, 1, 2) + bond(0, 2, 1) + bond(1, 0, None) + bond(2, 0, None)
+
+
+def _trimer_positions(r_ij, r_ik, theta_deg, seed):
+    th = math.radians(theta_deg)
+    loc = np.array([[0.0, 0.0, 0.0], [r_ij, 0.0, 0.0],
+                    [r_ik * math.cos(th), r_ik * math.sin(th), 0.0]])
+    q, _ = np.linalg.qr(np.random.default_rng(seed).normal(size=(3, 3)))  # generic orientation
+    return loc @ q.T + np.array([11.3, 12.1, 10.7])
+
+
+def _custom_sic_table():
+    # The Si/C mixing rule's table with lambda3, m, gamma, h and the three-body
+    # cutoff radius R varied record by record, so that taking any of them from
+    # the wrong record changes the energy
+    t = sic_table().reshape(8, 14).copy()
+    for q in range(8):
+        ti, tj, tk = q // 4, (q // 2) % 2, q % 2
+        t[q, 2] = 0.9 + 0.15 * q
+        t[q, 0] = 3.0 if q % 2 == 0 else 1.0
+        t[q, 1] = 1.0 + 0.07 * q
+        t[q, 5] = t[q, 5] + 0.02 * q
+        if tj != tk:
+            t[q, 10] = t[q, 10] + 0.004 * q
+    return t.ravel()
+
+
+TRIMERS = [
+    # name, table builder, species (i, j, k), r_ij, r_ik (k in the taper of f_C(r_ik)), angle
+    ("si-l3m3", lambda: S.with_lambda3(si_table(), 1.7322, 3), (0, 0, 0), 2.25, 2.92, 125.0),
+    ("si-l3m1", lambda: S.with_lambda3(si_table(), 1.3, 1), (0, 0, 0), 2.25, 2.92, 125.0),
+    ("si-c-si", _custom_sic_table, (0, 1, 0), 1.95, 2.88, 118.0),
+    ("c-si-c", _custom_sic_table, (1, 0, 1), 2.0, 1.98, 140.0),
+]
+
+
+@pytest.mark.parametrize("case", TRIMERS, ids=[c[0] for c in TRIMERS])
+def test_trimer_closed_form(case):
+    mp = pytest.importorskip("mpmath").mp
+    mp.dps = 50
+    _, mk, species, r_ij, r_ik, theta = case
+    table = mk()
+    ns = round((table.size // 14) ** (1 / 3))
+    x = _trimer_positions(r_ij, r_ik, theta, seed=hash(case[0]) % 1000)
+    t = np.array(species, dtype=np.int32)
+    box = np.array([30.0, 30.0, 30.0])
+    assert np.linalg.norm(x[1] - x[2]) > 3.05  # j and k out of each other's range
+    nl = oracle.neighbors(x, box, 3.5)
+    e, f, _ = oracle.compute(x, t, box, table, nl)
+
+    def rec(a, b, c):
+        r = table.reshape(-1, 14)[(a * ns + b) * ns + c]
+        return {name: mp.mpf(float(r[q])) for q, name in enumerate(oracle.FIELDS)}
+
+    X = [[mp.mpf(float(v)) for v in row] for row in x]
+    e_ref = _trimer_energy(mp, X, t, rec)
+    assert abs(e - float(e_ref)) <= 1e-12 * abs(float(e_ref))
+    f_ref = np.zeros((3, 3))
+    for a in range(3):
+        for c in range(3):
+            def along(s, a=a, c=c):
+                Y = [list(row) for row in X]
+                Y[a][c] = s
+                return _trimer_energy(mp, Y, t, rec)
+            f_ref[a, c] = -float(mp.diff(along, X[a][c]))
+    assert np.abs(f - f_ref).max() <= 1e-10 * np.abs(f_ref).max()
+    # the three-body term matters: with gamma = 0 in every record the energy changes
+    t0 = table.reshape(-1, 14).copy()
+    t0[:, 1] = 0.0
+    e0, _, _ = oracle.compute(x, t, box, t0.ravel(), nl)
+    assert abs(e0 - e) > 1e-5 * abs(e)
+
+
+# ----------------------------------------------------------------------------- MD units
+# Metal units: mass in amu, length in Angstrom, time in ps, energy in eV. The
+# conversion 1 amu A^2/ps^2 in eV follows from the CODATA 2018 atomic mass
+# constant and the exact SI electronvolt; MD codes quote it to 8 digits
+# (1.0364269e-4), so the pins below hold to 1e-7.
+AMU_KG = 1.66053906660e-27
+EV_J = 1.602176634e-19
+MVV2EV_CODATA = AMU_KG * (1e-10 / 1e-12) ** 2 / EV_J
+
+
+def _dimer_energy_derivs(r):
+    el = W.ELEMENTS_TERSOFF89["Si"]
+    A, B, l1, l2 = el[0], el[1], el[2], el[3]
+    e1 = -l1 * A * math.exp(-l1 * r) + l2 * B * math.exp(-l2 * r)
+    e2 = l1 * l1 * A * math.exp(-l1 * r) - l2 * l2 * B * math.exp(-l2 * r)
+    return e1, e2
+
+
+def test_md_one_step_metal_units():
+    # A Si dimer at rest at r = 2.5 A (inside R - D: zeta = 0, b = 1, f_C = 1).
+    # One velocity-Verlet step of dt: dx = dt^2/2 F0/m, v = dt/2 (F0 + F1)/m, in
+    # metal units.
+    table = si_table()
+    m = W.MASS_AMU["Si"]
+    dt = 0.002
+    r0 = 2.5
+    x = np.array([[10.0, 10.0, 10.0], [10.0 + r0, 10.0, 10.0]])
+    v = np.zeros_like(x)
+    t = np.zeros(2, np.int32)
+    box = np.array([30.0, 30.0, 30.0])
+    x1, v1, thermo, f1 = oracle.md_run(x, v, t, box, table, [m], dt, 1, 3.5, 0)
+    e1, _ = _dimer_energy_derivs(r0)
+    f0 = -e1  # force on atom 1 along +x
+    dx_ref = 0.5 * dt * dt * f0 / (m * MVV2EV_CODATA)
+    assert abs((x1[1, 0] - x[1, 0]) - dx_ref) <= 1e-7 * abs(dx_ref)
+    assert abs((x1[0, 0] - x[0, 0]) + dx_ref) <= 1e-7 * abs(dx_ref)
+    r1 = r0 + 2 * dx_ref
+    f1_ref = -_dimer_energy_derivs(r1)[0]
+    v_ref = 0.5 * dt * (f0 + f1_ref) / (m * MVV2EV_CODATA)
+    assert abs(v1[1, 0] - v_ref) <= 1e-7 * abs(v_ref)
+    ke_ref = 2 * 0.5 * m * v_ref * v_ref * MVV2EV_CODATA  # eV
+    assert abs(thermo[0, 1] - ke_ref) <= 2e-7 * ke_ref
+
+
+def test_md_dimer_period_metal_units():
+    # Small oscillation of a Si dimer about its minimum r_e: the period is
+    # 2 pi sqrt(mu / E''(r_e)) with the reduced mass mu = m/2, in metal units.
+    el = W.ELEMENTS_TERSOFF89["Si"]
+    A, B, l1, l2 = el[0], el[1], el[2], el[3]
+    r_e = math.log(l1 * A / (l2 * B)) / (l1 - l2)  # E'(r_e) = 0
+    _, k = _dimer_energy_derivs(r_e)
+    m = W.MASS_AMU["Si"]
+    period = 2 * math.pi * math.sqrt(0.5 * m * MVV2EV_CODATA / k)  # ps
+    table = si_table()
+    dt = 5e-5
+    x = np.array([[10.0, 10.0, 10.0], [10.0 + r_e + 2e-3, 10.0, 10.0]])
+    v = np.zeros_like(x)
+    t = np.zeros(2, np.int32)
+    box = np.array([30.0, 30.0, 30.0])
+    rs = [x[1, 0] - x[0, 0]]
+    nsteps = int(2.2 * period / dt)
+    for _ in range(nsteps):
+        x, v, _, _ = oracle.md_run(x, v, t, box, table, [m], dt, 1, 3.5, 0)
+        rs.append(x[1, 0] - x[0, 0])
+    u = np.array(rs) - r_e
+    # downward zero crossings of r - r_e, linearly interpolated
+    cross = [s + u[s] / (u[s] - u[s + 1]) for s in range(len(u) - 1) if u[s] > 0 >= u[s + 1]]
+    assert len(cross) >= 2
+    measured = (cross[1] - cross[0]) * dt
+    assert abs(measured - period) <= 1e-4 * period
