@@ -38,19 +38,21 @@ DT = 0.001
 R_LIST = 4.0
 RC_SI = 3.0  # largest f_C outer cutoff of the Tersoff 1989 Si / C tables (R + D)
 NPARAM_TABLE_SI = 14
-PEAK_FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
-PEAK_MUFU_TOPS_NOMINAL = 152 * 16 * 2.07e9 / 1e12  # SMs x special-function ops per clock x clock
+# Derived from unit counts and the maximum clock, for cross-checking the
+# measured peaks (tersoff_pipe_peaks: FFMA, DFMA and MUFU loop kernels, run at
+# the start of every benchmark); the roofline fractions use the measured ones.
+PEAK_FP32_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
 PEAK_ISSUE_WARP_INST = 152 * 4 * 2.07e9  # SMs x schedulers (one warp instruction each) x clock
 # warp instructions of one force launch on this workload (ncu smsp__inst_executed.sum, the same
 # capture as the traffic); like the traffic, valid only for the sources it was taken with
 FORCE_WARP_INST = 28_019_987
-PEAK_FP64_TFLOPS_NOMINAL = 1.25
 
-# Algorithmic FP32 operations of the mixed force kernel per unit of work
-# (additions, multiplications, one per FMA half; special-function ops counted
-# separately): per skin-list entry scanned by the filter, per short-list
-# neighbour (bond vector, length, unit vector, force/virial epilogue), per pair
-# term and per three-body term.
+# Algorithmic FP32 operations of the force evaluation per unit of work
+# (additions and multiplications, an FMA counting 2; special-function ops
+# counted separately): per bond inside the cutoffs (bond vector, length, unit
+# vector, its share of the force and virial epilogue), per pair term and per
+# three-body term. The filter pass over the skin list (FLOP_SKIN per entry)
+# is not the method's work and is reported on its own.
 FLOP_SKIN, FLOP_SHORT, FLOP_PAIR, FLOP_TRIPLET = 15, 36, 63, 61
 MUFU_SHORT, MUFU_PAIR, MUFU_TRIPLET = 1, 7, 1
 
@@ -63,13 +65,20 @@ FORCE_TRAFFIC_SOURCES = ("tersoff_fwd.cuh", "fwd_launch.cuh", "fwd_f32.cu")
 FORCE_TRAFFIC_SHA256 = "df2924a7a5a74c8556af056a8f8d92987ba177303853cb57d948c5f69c36bb16"
 
 
-def ceilings_us(flop, mufu, peaks, kern_ms):
+def mufu_peak(pk):
+    """Largest measured special-function rate (1e12 ops/s): a lower bound on
+    the time of any mix of rsqrt, ex2 and lg2."""
+    return max(pk["rsqrt_tops"], pk["ex2_tops"], pk["lg2_tops"])
+
+
+def ceilings_us(flop, mufu, peaks, pk, kern_ms):
     """Lower bounds on one force launch (us) from each resource, beside the
-    measured time: FP32 arithmetic (the FLOP model), special-function
-    operations, DRAM traffic (ncu bytes over the measured copy bandwidth), and
-    instruction issue (ncu warp instructions over 4 per SM per clock)."""
-    out = {"fp32_flops": flop / (PEAK_FP32_TFLOPS_NOMINAL * 1e12) * 1e6,
-           "mufu": mufu / (PEAK_MUFU_TOPS_NOMINAL * 1e12) * 1e6,
+    measured time: FP32 arithmetic (the FLOP model over the measured FFMA
+    peak), special-function operations (over the measured MUFU rate), DRAM
+    traffic (ncu bytes over the measured copy bandwidth), and instruction issue
+    (ncu warp instructions over 4 per SM per clock)."""
+    out = {"fp32_flops": flop / (pk["fp32_tflops"] * 1e12) * 1e6,
+           "mufu": mufu / (mufu_peak(pk) * 1e12) * 1e6,
            "measured": kern_ms * 1e3}
     tr = force_traffic()
     if tr is not None and peaks.get("hbm_gbs"):
@@ -313,6 +322,8 @@ def run_ours(args):
         ctx.set_timing(False)
         return sum(ms), launches, kern, build, integ, clocks
 
+    # arithmetic-pipe peaks of this device, measured now (loop kernels)
+    pk = T.pipe_peaks()
     out = {}
     # ---------------- accuracy of the mixed path against the FP64 path (same start)
     ctx64, xd64, vd64, td, f64, e64, w64 = setup(T.FP64)
@@ -330,8 +341,8 @@ def run_ours(args):
     skin, nshort, npair, ntrip = work_counts(x, t, box, cnt.cpu().numpy(), nbr.cpu().numpy(),
                                              table, len(names))
     del cnt, nbr
-    flop_launch = (FLOP_SKIN * skin + FLOP_SHORT * nshort + FLOP_PAIR * npair +
-                   FLOP_TRIPLET * ntrip)
+    flop_launch = FLOP_SHORT * nshort + FLOP_PAIR * npair + FLOP_TRIPLET * ntrip
+    filter_flop_launch = FLOP_SKIN * skin
     mufu_launch = MUFU_SHORT * nshort + MUFU_PAIR * npair + MUFU_TRIPLET * ntrip
 
     # ---------------- launch options chosen by the library's autotuner (MD
@@ -416,9 +427,16 @@ def run_ours(args):
             "dtype": "f64",
             "launch": best64,
             "force_kernel_ms": kern_ms_d,
-            "force_kernel_tflops": flop_launch / (kern_ms_d * 1e-3) / 1e12,
-            "force_kernel_frac_of_fp64_nominal": flop_launch / (kern_ms_d * 1e-3) / 1e12 /
-            PEAK_FP64_TFLOPS_NOMINAL,
+            "roofline": {
+                "bound": "fp64",
+                "kernel": "k_tersoff<double>",
+                "achieved": flop_launch / (kern_ms_d * 1e-3) / 1e12,
+                "peak": pk["fp64_tflops"],
+                "unit": "TFLOP/s",
+                "frac": flop_launch / (kern_ms_d * 1e-3) / 1e12 / pk["fp64_tflops"],
+                "peak_source": "measured in this run: DFMA loop kernel (tersoff_pipe_peaks)",
+                "flop_per_launch": flop_launch,
+            },
             "gpu_launches": launches_d,
         },
         "mixed_over_fp64": value / value_d,
@@ -426,13 +444,23 @@ def run_ours(args):
             "bound": "alu",
             "kernel": "k_tersoff<float> (fused zeta/bond-order/force)",
             "achieved": achieved,
-            "peak": PEAK_FP32_TFLOPS_NOMINAL,
+            "peak": pk["fp32_tflops"],
             "unit": "TFLOP/s",
-            "frac": achieved / PEAK_FP32_TFLOPS_NOMINAL,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max clock",
+            "frac": achieved / pk["fp32_tflops"],
+            "peak_source": "measured in this run: FFMA loop kernel (tersoff_pipe_peaks)",
+            "peak_derived": PEAK_FP32_TFLOPS_DERIVED,
+            "peak_derived_source": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz max clock",
+            "flop_model": {"per_bond_in_cutoff": FLOP_SHORT, "per_pair_term": FLOP_PAIR,
+                           "per_three_body_term": FLOP_TRIPLET,
+                           "formula": "short_entries x 36 + pairs x 63 + triplets x 61"},
+            "filter_flop_per_launch": filter_flop_launch,
+            "mufu": {"ops_per_launch": mufu_launch,
+                     "achieved_tops": mufu_launch / (kern_ms * 1e-3) / 1e12,
+                     "peak_tops": mufu_peak(pk),
+                     "frac": mufu_launch / (kern_ms * 1e-3) / 1e12 / mufu_peak(pk)},
             "traffic": force_traffic(),
             "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-            "ceilings_us": ceilings_us(flop_launch, mufu_launch, peaks, kern_ms),
+            "ceilings_us": ceilings_us(flop_launch, mufu_launch, peaks, pk, kern_ms),
             "flop_per_launch": flop_launch,
             "mufu_per_launch": mufu_launch,
             "work_per_launch": {"skin_entries": skin, "short_entries": nshort, "pairs": npair,
@@ -459,6 +487,7 @@ def run_ours(args):
         "gpu_launches": launches_m,
         "clocks": clocks,
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
+        "pipe_peaks": pk,
     }
     if rank == 0 and not args.no_extra:
         out["backward"] = time_backward(T, ctxm, xdm, ctx64, xd64, flush)
@@ -470,6 +499,8 @@ def run_ours(args):
         del flush
         torch.cuda.empty_cache()
         out["large_md"] = large_md(T, W, dev, best64)
+        if args.accuracy_steps > 0:
+            out["accuracy"] = accuracy_run(T, W, args.accuracy_steps, with_fp32_sums=False)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x, v, t, box, names, table)
     if rank == 0:
@@ -614,7 +645,7 @@ def batched_fit(T, W, dev, flush, cells, gen_seconds, reps=20):
     return out
 
 
-def large_md(T, W, dev, opt64, steps_mixed=1000, steps_fp64=100, chunk=100):
+def large_md(T, W, dev, opt64, steps_mixed=1000, steps_fp64=1000, chunk=100):
     """Si diamond 160x160x80 cells (16,384,000 atoms) at 1000 K: NVE velocity
     Verlet, dt 1 fs, r_list 4.0 A (skin 1.0), rebuilds triggered by the
     displacement (half the skin), all steps of a call in one CUDA graph. Reports
@@ -751,34 +782,37 @@ def cpu_baseline(x, v, t, box, names, table, nsteps=100):
 
 def run_reference(args):
     """The oracle on the host cores (there is no reference implementation to
-    install): each step is oracle velocity-Verlet MD of MD_PER_STEP steps on a
-    64,000-atom sample of the benchmark system (Si diamond 20x20x20 cells, same
-    recipe), including the oracle's own list build and first force evaluation,
-    so that the default run ends within minutes."""
+    install), on the benchmark's own system: Si diamond 40x40x40 cells,
+    512,000 atoms, same recipe. Each step is one oracle md_run call of
+    MD_PER_STEP velocity-Verlet steps continuing the trajectory of the previous
+    call; a call also builds its list and evaluates its forces once before the
+    first step (two list builds and 11 force evaluations per 10 steps, against
+    one build and 10 evaluations on the GPU), so the oracle's rate is, if
+    anything, understated by about a tenth."""
     world, rank, local = dist_info()
     if rank != 0:
         return
     import oracle
     import workloads as W
-    x, v, t, box, names = W.config_si_md(ncell=20)
+    x, v, t, box, names = W.config_si_md()
     table = oracle.mix_tersoff89(*W.element_records(names))
     mass = [W.MASS_AMU[s] for s in names]
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
-        oracle.md_run(x, v, t, box, table, mass, DT, 1, R_LIST, MD_PER_STEP, cap=48,
-                      nthreads=cores)
+        x, v, _, _ = oracle.md_run(x, v, t, box, table, mass, DT, MD_PER_STEP, R_LIST,
+                                   MD_PER_STEP, cap=48, nthreads=cores)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.md_run(x, v, t, box, table, mass, DT, MD_PER_STEP, R_LIST, MD_PER_STEP, cap=48,
-                      nthreads=cores)
+        x, v, _, _ = oracle.md_run(x, v, t, box, table, mass, DT, MD_PER_STEP, R_LIST,
+                                   MD_PER_STEP, cap=48, nthreads=cores)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     units = x.shape[0] * MD_PER_STEP * args.steps
     value = units / total
-    sample = (f"each step: oracle md_run of {MD_PER_STEP} VV steps on a {x.shape[0]}-atom sample "
-              f"(Si diamond 20x20x20 cells, same recipe) including its list build and first "
-              f"force evaluation, {cores} OpenMP threads")
+    sample = (f"each step: oracle md_run of {MD_PER_STEP} VV steps on the full {x.shape[0]}-atom "
+              f"benchmark system, continuing the previous step's trajectory, including the "
+              f"call's own list build and first force evaluation, {cores} OpenMP threads")
     out = {
         "impl": "reference",
         "metric": METRIC,
@@ -793,7 +827,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": base_config(512000, world),
+        "config": base_config(x.shape[0], world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -801,19 +835,17 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def run_accuracy(args):
+def accuracy_run(T, W, steps, with_fp32_sums=True):
     """Long-run accuracy of the mixed path (the paper's accuracy experiment,
     Sec. V-D): Si diamond 20x20x10 cells (32,000 atoms) at 1000 K, the same
-    initial state integrated by the FP64 and the mixed path for args.steps
+    initial state integrated by the FP64 and the mixed path for `steps`
     velocity-Verlet steps (dt 1 fs, rebuilds on half the skin), total energy
-    recorded every step; reports the largest relative deviation of the mixed
-    path's total energy from the FP64 path's, and each path's drift. The same
-    for the mixed path with single-precision force sums (the paper's
+    recorded every step; the largest relative deviation of the mixed path's
+    total energy from the FP64 path's, and each path's drift. Optionally the
+    same for the mixed path with single-precision force sums (the paper's
     all-single mode, ABLATE_FP32_SUMS)."""
     import numpy as np
     import torch
-    import workloads as W
-    import paper_1607_02904_gb300 as T
     names = ["Si"]
     x, t, box = W.diamond(20, 20, 10, 5.432)
     rng = W.rng_for(6)
@@ -824,11 +856,13 @@ def run_accuracy(args):
     mass = [W.MASS_AMU[s] for s in names]
     chunk = 1000
     out = {"metric": "total-energy deviation of the mixed path from the FP64 path",
-           "atoms": int(n), "steps": args.steps, "dt_ps": DT, "temperature_K": 1000.0,
+           "atoms": int(n), "steps": steps, "dt_ps": DT, "temperature_K": 1000.0,
            "rebuild": "on half the skin (r_list 4.0 A)"}
     series = {}
-    for name, prec, abl in (("fp64", T.FP64, 0), ("mixed", T.MIXED, 0),
-                            ("fp32_sums", T.MIXED, T.ABLATE_FP32_SUMS)):
+    variants = [("fp64", T.FP64, 0), ("mixed", T.MIXED, 0)]
+    if with_fp32_sums:
+        variants.append(("fp32_sums", T.MIXED, T.ABLATE_FP32_SUMS))
+    for name, prec, abl in variants:
         ctx = T.Context(prec)
         ctx.set_ablation(abl)
         ctx.set_scatter(T.SCATTER_GATHER)
@@ -841,32 +875,43 @@ def run_accuracy(args):
         th = torch.zeros((chunk, 3), dtype=torch.float64, device="cuda")
         etot = []
         t0 = time.perf_counter()
-        for _ in range(args.steps // chunk):
+        for _ in range(steps // chunk):
             ctx.md_step(xd, vd, fd, mass, DT, chunk, -1, th)
             etot.append(th[:, 2].cpu().numpy().copy())
         torch.cuda.synchronize()
         series[name] = np.concatenate(etot)
         out[name + "_seconds"] = time.perf_counter() - t0
         ctx.close()
-    e64, em, es = series["fp64"], series["mixed"], series["fp32_sums"]
+    e64, em = series["fp64"], series["mixed"]
     tt = np.arange(e64.size) * DT * 1e-3  # ns
     out["max_rel_deviation"] = float(np.abs(em - e64).max() / np.abs(e64).max())
     out["final_rel_deviation"] = float(abs(em[-1] - e64[-1]) / abs(e64[-1]))
-    out["fp32_sums_max_rel_deviation"] = float(np.abs(es - e64).max() / np.abs(e64).max())
-    out["fp32_sums_final_rel_deviation"] = float(abs(es[-1] - e64[-1]) / abs(e64[-1]))
+    if with_fp32_sums:
+        es = series["fp32_sums"]
+        out["fp32_sums_max_rel_deviation"] = float(np.abs(es - e64).max() / np.abs(e64).max())
+        out["fp32_sums_final_rel_deviation"] = float(abs(es[-1] - e64[-1]) / abs(e64[-1]))
     out["paper_bound_rel"] = 2e-5
-    for name, e in (("fp64", e64), ("mixed", em), ("fp32_sums", es)):
+    for name, e in series.items():
         out[name + "_drift_eV_per_atom_per_ns"] = float(np.polyfit(tt, e / n, 1)[0])
         out[name + "_etot_first_last_eV"] = [float(e[0]), float(e[-1])]
-    print(json.dumps(out), flush=True)
+    return out
+
+
+def run_accuracy(args):
+    """--accuracy: the long-run accuracy experiment for --steps MD steps, with
+    the single-precision force-sum variant (one JSON line)."""
+    import workloads as W
+    import paper_1607_02904_gb300 as T
+    print(json.dumps(accuracy_run(T, W, args.steps)), flush=True)
 
 
 def run_ablations(args):
     """The paper's design choices measured on the benchmark workload (mixed
     path, default launch options): the stored short list (Sec. IV-D) and the
     register-resident neighbourhood with pre-computed derivatives (Sec. IV-A),
-    each switched off alone and together, and the compensated force sums
-    replaced by plain float sums (the paper's all-single accumulation). Reports
+    each switched off alone and together, the compensated force sums replaced
+    by plain float sums (the paper's all-single accumulation), and no list
+    filtering at all with the fast-forward lane scheme (Sec. IV-C). Reports
     ms per 10 MD steps and per force evaluation, and the force error against
     the default mixed path and against the FP64 path (the first three leave
     the forces unchanged up to rounding order)."""
@@ -894,7 +939,8 @@ def run_ablations(args):
     for name, flags in (("default", 0), ("no_short_list", T.ABLATE_NO_SHORT),
                         ("general_path", T.ABLATE_GENERAL),
                         ("both", T.ABLATE_NO_SHORT | T.ABLATE_GENERAL),
-                        ("fp32_sums", T.ABLATE_FP32_SUMS)):
+                        ("fp32_sums", T.ABLATE_FP32_SUMS),
+                        ("fast_forward", T.ABLATE_FASTFWD)):
         ctx = T.Context(T.MIXED)
         ctx.set_ablation(flags)
         ctx.set_scatter(T.SCATTER_GATHER)
@@ -1000,6 +1046,9 @@ def main():
                     help="long-run accuracy of the mixed path against the FP64 path "
                          "(32,000 atoms, --steps MD steps; one JSON line)")
     ap.add_argument("--scatter", choices=["gather", "atomic"], default="gather")
+    ap.add_argument("--accuracy-steps", type=int, default=1_000_000,
+                    help="MD steps of the long-run accuracy leg of the default run (32,000 "
+                         "atoms, FP64 and mixed paths; 0 skips it)")
     args = ap.parse_args()
     if args.only:
         run_profile_case(args)

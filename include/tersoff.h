@@ -185,14 +185,20 @@ int tersoff_backward(tersoff_ctx* ctx, const double* x, int n, const double* gE,
  * back), and a latency-sensitive loop sharing the GPU with other streams
  * (freeing device memory waits for the whole device). tersoff_compute may
  * allocate per-neighbour buffers on its first call and after a precision or
- * capacity change; this call never does.
+ * capacity change; this call allocates no device memory. (With kernel timing
+ * on, tersoff_set_timing, it records event pairs in a host-side list, which
+ * can allocate host memory.)
  *
  * How: forces are added with FP64 atomics (as with TERSOFF_SCATTER_ATOMIC,
  * whatever the context's scatter mode) into a scratch array of fixed size
  * that is part of the library (one per device, about 1.5 MiB), then copied to
- * the outputs. The first call on a device looks up that array's address (and
- * makes the CUDA runtime load the library's device code there if it has not
- * yet); make that first call before any stream capture.
+ * the outputs. The context's scatter mode and the TERSOFF_ABLATE_FP32_SUMS
+ * switch (which act on the gather of tersoff_compute) therefore do not apply;
+ * the other ablation switches do. The first call on a device looks up that
+ * array's address (and makes the CUDA runtime load the library's device code
+ * there if it has not yet) and keeps it for the life of the process; make that
+ * first call before any stream capture. A device reset (cudaDeviceReset) after
+ * that first call is not supported: the kept address would be stale.
  *
  * Limits: n <= TERSOFF_NOALLOC_MAX_ATOMS, else TERSOFF_E_INVALID_ARG with
  * nothing enqueued. Every call on a device, from any context, uses the same
@@ -285,10 +291,20 @@ int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
  *                             all-single mode, Sec. V-E) instead of the
  *                             compensated float pair carried into double. This
  *                             one changes results beyond rounding order: it
- *                             measures what the compensated sums buy. */
+ *                             measures what the compensated sums buy;
+ *   TERSOFF_ABLATE_FASTFWD    no list filtering at all: one lane per centre atom
+ *                             walks the full skin list, each lane moving its own
+ *                             J (and, inside, K) index forward to the next entry
+ *                             inside the cutoff while the ready lanes wait, the
+ *                             body running once a warp vote finds every lane
+ *                             ready (the fast-forward scheme of Sec. IV-C, Fig. 2,
+ *                             with the warp vote of the paper's CUDA back-end,
+ *                             Sec. VI-B); forces through FP64 atomics. Single
+ *                             systems only (batches ignore it). */
 #define TERSOFF_ABLATE_NO_SHORT 1
 #define TERSOFF_ABLATE_GENERAL 2
 #define TERSOFF_ABLATE_FP32_SUMS 4
+#define TERSOFF_ABLATE_FASTFWD 8
 int tersoff_set_ablation(tersoff_ctx* ctx, int flags);
 
 /* One-line text of the last tersoff_autotune: the chosen options and every
@@ -335,6 +351,18 @@ int tersoff_set_timing(tersoff_ctx* ctx, int enable);
  * `kind` since timing was enabled (host outputs). Waits for the recorded
  * events. */
 int tersoff_timing(tersoff_ctx* ctx, int kind, double* total_ms, long long* launches);
+
+/* Arithmetic-pipe peaks of the current device, measured by loop kernels (the
+ * paper reports run times only; these are the denominators of the force
+ * kernels' rooflines). Runs five short kernels on `stream` (about 10 ms in
+ * all), each the median of 5 event-timed launches after an untimed one:
+ * chains of FP32 fused multiply-adds, of FP64 fused multiply-adds, and of the
+ * special-function unit's rsqrt, ex2 and lg2. out: HOST array of 6 doubles
+ * receiving FP32 TFLOP/s (an FMA counts 2), FP64 TFLOP/s, rsqrt, ex2 and lg2
+ * rates in 1e12 operations/s, and the multiprocessor count. Allocates a
+ * scratch buffer for the kernels' results during the call; synchronises
+ * `stream`. Returns TERSOFF_E_CUDA when no device is usable. */
+int tersoff_pipe_peaks(double* out, void* stream);
 
 #ifdef __cplusplus
 }

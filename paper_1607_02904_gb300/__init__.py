@@ -19,9 +19,11 @@ from ._lib import (  # noqa: F401
     ABLATE_NO_SHORT,
     ABLATE_GENERAL,
     ABLATE_FP32_SUMS,
+    ABLATE_FASTFWD,
     load,
     library_path,
     declared_symbols,
+    pipe_peaks,
 )
 from .params import mix_tersoff89, FIELDS  # noqa: F401
 from .autograd import TersoffSystem, TersoffBatch, TersoffFunction, energy_forces  # noqa: F401

@@ -30,6 +30,7 @@ REBUILD_ON_SKIN = -1
 ABLATE_NO_SHORT = 1
 ABLATE_GENERAL = 2
 ABLATE_FP32_SUMS = 4
+ABLATE_FASTFWD = 8
 
 _lib = None
 
@@ -64,6 +65,7 @@ _SIG = {
     "tersoff_set_graphs": ([_P, _I], _I),
     "tersoff_set_scatter": ([_P, _I], _I),
     "tersoff_timing": ([_P, _I, _P, _P], _I),
+    "tersoff_pipe_peaks": ([_P, _P], _I),
 }
 
 
@@ -98,6 +100,19 @@ def declared_symbols():
     hdr = os.path.join(os.path.dirname(_build.HERE), "include", "tersoff.h")
     text = open(hdr).read()
     return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(tersoff_\w+)\(", text, re.M)))
+
+
+def pipe_peaks(stream=None):
+    """Measured arithmetic peaks of the current device (tersoff_pipe_peaks):
+    dict of FP32 and FP64 TFLOP/s, rsqrt / ex2 / lg2 rates (1e12 ops/s) and the
+    multiprocessor count."""
+    lib = load()
+    out = (_D * 6)()
+    st = lib.tersoff_pipe_peaks(out, _stream(stream))
+    if st != OK:
+        raise TersoffError(st, "tersoff_pipe_peaks failed")
+    keys = ("fp32_tflops", "fp64_tflops", "rsqrt_tops", "ex2_tops", "lg2_tops", "sms")
+    return dict(zip(keys, [float(v) for v in out]))
 
 
 def _ptr(t):
@@ -267,8 +282,8 @@ class Context:
         self._check(self.lib.tersoff_set_launch(self.h, int(waves), int(split), int(block)))
 
     def set_ablation(self, flags):
-        """ABLATE_NO_SHORT | ABLATE_GENERAL | ABLATE_FP32_SUMS, for measuring the
-        design choices."""
+        """ABLATE_NO_SHORT | ABLATE_GENERAL | ABLATE_FP32_SUMS | ABLATE_FASTFWD,
+        for measuring the design choices."""
         self._check(self.lib.tersoff_set_ablation(self.h, int(flags)))
 
     def autotune_summary(self):

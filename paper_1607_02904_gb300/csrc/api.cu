@@ -768,6 +768,12 @@ int tersoff_compute_noalloc(tersoff_ctx* p, const double* x, int n, double* ener
   if ((st = tgb::launch_pack_positions(c, x, false, s))) return st;
   TGB_CUDA(c, cudaMemsetAsync(scr, 0, sizeof(double) * used, s));
   TGB_CUDA(c, cudaMemsetAsync(c->d_flags + tgb::FLAG_EXTRA_STICKY, 0, sizeof(int), s));
+  // The force kernel also writes the context's status words FLAG_EXTRA and
+  // (for atoms on the general path) FLAG_EXTRA_STICKY, which the gather of
+  // tersoff_compute and the MD steps read. Both are rewritten before any such
+  // read: every compute and MD call clears FLAG_EXTRA_STICKY and runs a force
+  // launch (which sets FLAG_EXTRA) before its gather, and tersoff_md_step's
+  // first step uses the caller's f, not a gather.
   const bool was_atomic = c->scatter_atomic;
   c->scatter_atomic = true;  // read by the launch below only
   st = tgb::launch_forward(c, scr + tgb::ACC_LEN, scr, nullptr, s);
@@ -1215,7 +1221,7 @@ int tersoff_set_launch(tersoff_ctx* p, int waves, int split, int block) {
 int tersoff_set_ablation(tersoff_ctx* p, int flags) {
   Ctx* c = C(p);
   if (!c) return TERSOFF_E_INVALID_ARG;
-  if (flags & ~7) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "ablation flags are bits 0 to 2");
+  if (flags & ~15) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "ablation flags are bits 0 to 3");
   c->ablate = flags;
   c->gen++;  // captured MD graphs hold the old kernel arguments
   return TERSOFF_OK;

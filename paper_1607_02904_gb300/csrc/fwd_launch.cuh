@@ -162,9 +162,31 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   return a;
 }
 
+// Ablation TERSOFF_ABLATE_FASTFWD: the fast-forward lane scheme over the full
+// skin list, one launch over all atoms in index order.
+template <class T, int NS>
+void launch_ffwd(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
+  const int grid = (c->n + BLOCK - 1) / BLOCK;
+  TimedRegion tr(c, 0, s);
+  if (c->has_lam3)
+    k_tersoff_ffwd<T, NS, true><<<grid, BLOCK, 0, s>>>(a);
+  else
+    k_tersoff_ffwd<T, NS, false><<<grid, BLOCK, 0, s>>>(a);
+  c->launches++;
+}
+
 template <class T>
 int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
   FwdArgs<T> a = make_args<T>(c, f, acc, eatom);
+  if (c->ablate & TERSOFF_ABLATE_FASTFWD) {
+    switch (c->ns) {
+      case 1: launch_ffwd<T, 1>(c, a, s); break;
+      case 2: launch_ffwd<T, 2>(c, a, s); break;
+      default: launch_ffwd<T, 0>(c, a, s); break;
+    }
+    TGB_CUDA(c, cudaGetLastError());
+    return TERSOFF_OK;
+  }
   switch (c->ns) {
     case 1: launch_buckets<T, 1>(c, a, s); break;
     case 2: launch_buckets<T, 2>(c, a, s); break;

@@ -589,40 +589,43 @@ __device__ __forceinline__ void clear_slots(const FwdArgs<T>& a, int i) {
 }
 
 // ---------------------------------------------------------------- reduction
-// Energy and virial: the 7 per-thread values (padded to 8) are reduce-scattered
-// across the warp (halving exchanges: 4, 2, 1 values), then summed over the
-// remaining lanes; lanes 0, 4, ..., 28 end with the 8 warp totals. Warp totals
-// are summed in double over the block and added to acc with one atomic each.
+// Energy and virial: the 7 per-thread values (padded to 8) are converted to
+// double (exactly) and reduce-scattered across the warp in double (halving
+// exchanges: 4, 2, 1 values), then summed over the remaining lanes; lanes 0,
+// 4, ..., 28 end with the 8 warp totals. Warp totals are summed in double over
+// the block and added to acc with one atomic each. Every sum across atoms is
+// thus in double.
 template <class T, int NB = BLOCK>
 __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc) {
   __shared__ double part[NB / 32][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T v[8] = {ei, w[0], w[1], w[2], w[3], w[4], w[5], T(0)};
+  double v[8] = {to_f64(ei),   to_f64(w[0]), to_f64(w[1]), to_f64(w[2]),
+                 to_f64(w[3]), to_f64(w[4]), to_f64(w[5]), 0.0};
   const bool hi16 = lane & 16;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const T send = hi16 ? v[q] : v[q + 4];
-    const T keep = hi16 ? v[q + 4] : v[q];
+    const double send = hi16 ? v[q] : v[q + 4];
+    const double keep = hi16 ? v[q + 4] : v[q];
     v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
   const bool hi8 = lane & 8;
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
-    const T send = hi8 ? v[q] : v[q + 2];
-    const T keep = hi8 ? v[q + 2] : v[q];
+    const double send = hi8 ? v[q] : v[q + 2];
+    const double keep = hi8 ? v[q + 2] : v[q];
     v[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
   }
   const bool hi4 = lane & 4;
   {
-    const T send = hi4 ? v[0] : v[1];
-    const T keep = hi4 ? v[1] : v[0];
+    const double send = hi4 ? v[0] : v[1];
+    const double keep = hi4 ? v[1] : v[0];
     v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
   }
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
   v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
   if ((lane & 3) == 0) {
     const int idx = (hi16 ? 4 : 0) + (hi8 ? 2 : 0) + (hi4 ? 1 : 0);
-    part[wid][idx] = to_f64(v[0]);
+    part[wid][idx] = v[0];
   }
   __syncthreads();
   if (threadIdx.x < 7) {
@@ -1189,6 +1192,174 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
   if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T, WIDE_BLOCK>(ei, w, a.acc);
+}
+
+// ---------------------------------------------------------------- fast-forward ablation
+// The paper's lane scheme without list filtering (Sec. IV-C, Fig. 2), with the
+// vector-wide conditional taken as a warp vote as in its CUDA back-end
+// (Sec. VI-B): one lane per centre atom i walks i's full skin list. Each lane
+// moves its own J index forward to the next entry inside the pair cutoff while
+// the lanes that have found one wait; the body for (i, j) runs once every lane
+// of the warp is ready or has finished its list. Both K loops inside the body
+// advance the same way, to entries inside the three-body cutoff. Forces go to
+// the fallback buffer through FP64 atomics. For measurement only
+// (TERSOFF_ABLATE_FASTFWD): the stored short list makes this unnecessary.
+template <class T, int NS, bool LAM3>
+__global__ void __launch_bounds__(BLOCK) k_tersoff_ffwd(const __grid_constant__ FwdArgs<T> a) {
+  constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
+  constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ T srec_s[SREC];
+  __shared__ float snear[SNS * SNS];
+  const int ns = NS > 0 ? NS : a.ns;
+  if (NS != 1)
+    for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += BLOCK) srec_s[q] = a.rec[q];
+  if (threadIdx.x < ns * ns) snear[threadIdx.x] = sizeof(T) == 4 ? a.near2[threadIdx.x] : 0.0f;
+  __syncthreads();
+  const T* srec = NS == 1 ? a.prm1 : srec_s;
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[FLAG_EXTRA] = 1;
+  using P = typename SelfPos<T>::type;
+  const Shift<T, false> sh;
+  T ei = 0;
+  T w[6] = {0, 0, 0, 0, 0, 0};
+  // block-uniform loop: every lane of a warp takes part in every vote
+  for (int i0 = blockIdx.x * BLOCK; i0 < a.n; i0 += gridDim.x * BLOCK) {
+    const int i = i0 + threadIdx.x;
+    const bool have = i < a.n;
+    const int ti = have ? a.types[i] : 0;
+    const int c = have ? min(a.cnt[i], a.cap) : 0;
+    P pi{};
+    if (have) {
+      pi = self_pos<T>(a, i);
+      if (!a.atomic_mode) clear_slots<T>(a, i);
+    }
+    T eatom_i = 0, fix = 0, fiy = 0, fiz = 0;
+    // bond to the entry in slot s: vector, length, exact residual near a cutoff
+    auto bond = [&](int s, T& dx, T& dy, T& dz, T& r, T& rx, int& j, int& tj) {
+      const uint32_t e = a.nbr[(size_t)s * a.n + i];
+      Bond<T>::vec(a, sh, pi, e, dx, dy, dz, j, tj);
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      r = r2 * M<T>::rsqrt_nr(r2);
+      rx = (sizeof(T) == 4 && r2 > snear[ti * ns + tj]) ? Exact<T>::residual(a, sh, pi, e, r)
+                                                         : T(0);
+    };
+    // J loop: candidate sj is ready when it is inside the pair cutoff or the
+    // list is exhausted
+    int sj = 0, j = i, tj = 0;
+    T dxj = 0, dyj = 0, dzj = 0, rij = 1, rexj = 0;
+    auto ready_j = [&]() -> bool {
+      if (sj >= c) return true;
+      bond(sj, dxj, dyj, dzj, rij, rexj, j, tj);
+      return rij < srec[rec_off<NS>(ns, ti, tj, tj) + K_ROUT2];
+    };
+    bool rj = ready_j();
+    while (!__all_sync(FULL, rj))
+      if (!rj) {
+        ++sj;
+        rj = ready_j();
+      }
+    while (__any_sync(FULL, sj < c)) {
+      const bool act = sj < c;
+      const T* p2 = srec + rec_off<NS>(ns, ti, tj, tj);
+      const T rinj = T(1) / rij;
+      const T uxj = dxj * rinj, uyj = dyj * rinj, uzj = dzj * rinj;
+      int sk = 0, k = i, tk = 0;
+      T dxk = 0, dyk = 0, dzk = 0, rik = 1, rexk = 0;
+      auto ready_k = [&]() -> bool {
+        if (!act || sk >= c) return true;
+        if (sk == sj) return false;
+        bond(sk, dxk, dyk, dzk, rik, rexk, k, tk);
+        return rik < srec[rec_off<NS>(ns, ti, tj, tk) + K_ROUT3];
+      };
+      // first K loop: zeta_ij
+      T zeta = 0;
+      bool rk = ready_k();
+      for (;;) {
+        while (!__all_sync(FULL, rk))
+          if (!rk) {
+            ++sk;
+            rk = ready_k();
+          }
+        if (!__any_sync(FULL, act && sk < c)) break;
+        if (act && sk < c) {
+          const T* p3 = srec + rec_off<NS>(ns, ti, tj, tk);
+          const T cs = (dxj * dxk + dyj * dyk + dzj * dzk) * rinj / rik;
+          T zt, A1, A2, A3;
+          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3, rexk);
+          zeta += zt;
+        }
+        ++sk;
+        rk = ready_k();
+      }
+      T V = 0, dVdr = 0, dz = 0;
+      if (act) pair<T>(p2, rij, zeta, V, dVdr, dz, rexj);
+      eatom_i += V;
+      T Fjx = -dVdr * uxj, Fjy = -dVdr * uyj, Fjz = -dVdr * uzj;
+      // second K loop: three-body forces
+      sk = 0;
+      rk = ready_k();
+      for (;;) {
+        while (!__all_sync(FULL, rk))
+          if (!rk) {
+            ++sk;
+            rk = ready_k();
+          }
+        if (!__any_sync(FULL, act && sk < c)) break;
+        if (act && sk < c) {
+          const T* p3 = srec + rec_off<NS>(ns, ti, tj, tk);
+          const T rink = T(1) / rik;
+          const T uxk = dxk * rink, uyk = dyk * rink, uzk = dzk * rink;
+          const T cs = uxj * uxk + uyj * uyk + uzj * uzk;
+          T zt, A1, A2, A3;
+          triplet<T, LAM3>(p3, rij, rik, cs, zt, A1, A2, A3, rexk);
+          Fjx -= dz * (A1 * (uxk - cs * uxj) * rinj + A2 * uxj);
+          Fjy -= dz * (A1 * (uyk - cs * uyj) * rinj + A2 * uyj);
+          Fjz -= dz * (A1 * (uzk - cs * uzj) * rinj + A2 * uzj);
+          const T Fkx = -dz * (A1 * (uxj - cs * uxk) * rink + (A3 - A2) * uxk);
+          const T Fky = -dz * (A1 * (uyj - cs * uyk) * rink + (A3 - A2) * uyk);
+          const T Fkz = -dz * (A1 * (uzj - cs * uzk) * rink + (A3 - A2) * uzk);
+          atomic_add3(a.f, k, to_f64(Fkx), to_f64(Fky), to_f64(Fkz));
+          fix -= Fkx;
+          fiy -= Fky;
+          fiz -= Fkz;
+          w[0] += dxk * Fkx;
+          w[1] += dyk * Fky;
+          w[2] += dzk * Fkz;
+          w[3] += dxk * Fky;
+          w[4] += dxk * Fkz;
+          w[5] += dyk * Fkz;
+        }
+        ++sk;
+        rk = ready_k();
+      }
+      if (act) {
+        atomic_add3(a.f, j, to_f64(Fjx), to_f64(Fjy), to_f64(Fjz));
+        fix -= Fjx;
+        fiy -= Fjy;
+        fiz -= Fjz;
+        w[0] += dxj * Fjx;
+        w[1] += dyj * Fjy;
+        w[2] += dzj * Fjz;
+        w[3] += dxj * Fjy;
+        w[4] += dxj * Fjz;
+        w[5] += dyj * Fjz;
+      }
+      // next J candidate, fast-forwarded
+      if (act) ++sj;
+      rj = ready_j();
+      while (!__all_sync(FULL, rj))
+        if (!rj) {
+          ++sj;
+          rj = ready_j();
+        }
+    }
+    if (have) {
+      atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+      if (a.eatom) a.eatom[i] = to_f64(eatom_i);
+    }
+    ei += eatom_i;
+  }
+  if (a.acc != nullptr) block_reduce_store<T>(ei, w, a.acc);
 }
 
 }  // namespace fwd

@@ -125,7 +125,7 @@ def test_autotune_batch_compute(T):
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
-@pytest.mark.parametrize("flags", [1, 2, 3])
+@pytest.mark.parametrize("flags", [1, 2, 3, 8, 9])
 def test_ablations_keep_results(T, prec, flags):
     ctx = T.Context(prec)
     ctx.set_ablation(flags)
@@ -139,7 +139,7 @@ def test_ablations_keep_results(T, prec, flags):
     torch.cuda.synchronize()
     check(prec, (e.item(), f.cpu().numpy(), w.cpu().numpy()), REF)
     with pytest.raises(T.TersoffError):
-        ctx.set_ablation(8)
+        ctx.set_ablation(16)
     ctx.close()
 
 
@@ -169,3 +169,70 @@ def test_fp32_sums_ablation(T, scatter):
         assert not np.array_equal(plain[1], comp[1])
     else:
         assert np.abs(plain[1] - comp[1]).max() <= 1e-12 * np.abs(comp[1]).max()
+
+
+# The fast-forward lane scheme (Sec. IV-C, Fig. 2) over the full skin list:
+# lanes of a warp hold atoms with different numbers of bonds and of skin
+# entries (random packings, lambda3 tables, a ragged last warp), in both paths
+# and both scatter modes, against the oracle.
+FF_CASES = []
+_xp, _tp, _bp = S.packing_cell(n=300, seed=95)
+FF_CASES.append(("packing", _xp, _tp, _bp, TABLE))
+_xs, _ts, _bs = S.si_cell(n=3, seed=96, amp=0.3)
+FF_CASES.append(("si-l3m3", _xs, _ts, _bs,
+                 S.with_lambda3(S.table_for(["Si"], oracle.mix_tersoff89), 1.7322, 3)))
+FF_CASES.append(("sic", X, TY, BOX, TABLE))
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("scatter", [0, 1], ids=["gather", "atomic"])
+@pytest.mark.parametrize("case", FF_CASES, ids=[c[0] for c in FF_CASES])
+def test_fastforward_ablation_against_oracle(T, prec, scatter, case):
+    _, x, t, box, table = case
+    ref = oracle.compute(x, t, box, table, oracle.neighbors(x, box, RC))
+    ctx = T.Context(prec)
+    ctx.set_scatter(scatter)
+    ctx.set_ablation(T.ABLATE_FASTFWD)
+    ctx.params(table)
+    xd = dev(x)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    f = torch.zeros_like(xd)
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ea = torch.zeros(len(x), dtype=torch.float64, device="cuda")
+    for _ in range(2):  # the fallback buffer is cleared by the gather between calls
+        ctx.compute(xd, e, f, w)
+    ctx.compute_peratom(xd, ea)
+    torch.cuda.synchronize()
+    check(prec, (e.item(), f.cpu().numpy(), w.cpu().numpy()), ref)
+    _, _, _, ea_ref = oracle.compute(x, t, box, table, oracle.neighbors(x, box, RC), eatom=True)
+    tol = 1e-10 if prec == 0 else 1e-5
+    assert np.abs(ea.cpu().numpy() - ea_ref).max() <= tol * np.abs(ea_ref).max()
+    # switching back to the default path gives the default results
+    ctx.set_ablation(0)
+    f2 = torch.zeros_like(xd)
+    ctx.compute(xd, None, f2)
+    torch.cuda.synchronize()
+    check(prec, (ref[0], f2.cpu().numpy(), ref[2]), ref)
+    ctx.close()
+
+
+def test_fastforward_ablation_md_fp64_against_oracle(T):
+    x, t, box = W.diamond(4, 4, 4, 5.432)
+    rng = np.random.Generator(np.random.Philox(97))
+    x = W.jitter_gaussian(x, 0.05, rng)
+    v = W.maxwell_velocities(t, np.array(MASS), 1000.0, rng)
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    ctx = T.Context(0)
+    ctx.set_ablation(T.ABLATE_FASTFWD)
+    ctx.params(table)
+    xd, vd = dev(x), dev(v)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+    fd = torch.zeros_like(xd)
+    ctx.compute(xd, None, fd)
+    ctx.md_step(xd, vd, fd, MASS, 0.001, 20, 10)
+    torch.cuda.synchronize()
+    xo, vo, _, fo = oracle.md_run(x, v, t, box, table, MASS, 0.001, 20, RC + 1.0, 10)
+    assert np.abs(xd.cpu().numpy() - xo).max() < 1e-9
+    assert np.abs(fd.cpu().numpy() - fo).max() < 1e-8 * np.abs(fo).max()
+    ctx.close()

@@ -84,6 +84,18 @@ def scaled_err(table, got, ref):
     return np.abs(s * (got - ref)).max() / np.abs(s * ref).max()
 
 
+# Per entry: every entry whose scaled value is at least FLOOR of the largest
+# must also match on its own, to TOL_ENTRY relative.
+FLOOR = 1e-3
+TOL_ENTRY = {0: 1e-8, 1: 1e-3}
+
+
+def entry_err(table, got, ref):
+    s = np.where(table != 0.0, np.abs(table), 1.0)
+    big = np.abs(s * ref) >= FLOOR * np.abs(s * ref).max()
+    return (np.abs(got - ref)[big] / np.abs(ref)[big]).max()
+
+
 def gpu_grad(T, prec, name, with_f):
     x, t, box, table = SYS[name]
     gE, gF = weights(len(x), 91, with_f)
@@ -108,6 +120,8 @@ def test_param_vjp_matches_oracle(T, prec, name):
     assert np.all(got[::oracle.NPAR] == 0.0)  # m
     err = scaled_err(table, got, ref)
     assert err <= TOL[prec], err
+    e1 = entry_err(table, got, ref)
+    assert e1 <= TOL_ENTRY[prec], e1
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])

@@ -140,3 +140,31 @@ def test_mixed_thermo_when_short_list_expires(T, graphs):
     scale = np.abs(d[:, 2]).max()
     assert np.abs(m[:, 2] - d[:, 2]).max() <= 1e-6 * scale  # total energy
     assert np.abs(m[:, 1] - d[:, 1]).max() <= 1e-5 * np.abs(d[:, 1]).max()  # kinetic
+
+
+@pytest.mark.parametrize("rebuild", [10, -1], ids=["every-10", "on-skin"])
+def test_mixed_forces_after_in_graph_rebuild_match_oracle(T, rebuild):
+    # Mixed path, MD steps as a replayed CUDA graph with the neighbour rebuild
+    # inside it (a fixed period, or the conditional node of the displacement
+    # trigger): the forces left in f after the call are F(x) at the final
+    # positions, evaluated over the list rebuilt inside the graph; against the
+    # FP64 oracle at those positions, to the mixed path's tolerance.
+    x, v, t, box = hot_si(seed=64)
+    table = S.table_for(["Si"], oracle.mix_tersoff89)
+    ctx = T.Context(T.MIXED)
+    ctx.params(table)
+    xd, vd = dev(x), dev(v)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + SKIN)
+    fd = torch.zeros_like(xd)
+    ctx.compute(xd, None, fd)
+    rebuilds = []
+    for _ in range(3):  # the first call captures the graph, the others replay it
+        ctx.md_step(xd, vd, fd, MASS, 0.001, 10, T.REBUILD_ON_SKIN if rebuild < 0 else rebuild)
+        rebuilds.append(ctx.md_rebuilds())
+    torch.cuda.synchronize()
+    assert rebuilds[-1] >= 1 and sum(rebuilds) >= 3
+    xg, fg = xd.cpu().numpy(), fd.cpu().numpy()
+    ctx.close()
+    _, fo, _ = oracle.compute(xg, t, box, table, oracle.neighbors(xg, box, RC))
+    rms = np.sqrt(((fg - fo) ** 2).mean()) / np.sqrt((fo ** 2).mean())
+    assert rms <= 1e-5, rms

@@ -136,3 +136,59 @@ def test_noalloc_rejects_oversize(T):
     with pytest.raises(T.TersoffError):  # atom count differs from the build
         ctx.compute_noalloc(_dev(x[:-1]), *_outputs(len(x) - 1))
     ctx.close()
+
+
+def test_noalloc_allocates_no_device_memory(T):
+    # The call's defining property, observed through cudaMemGetInfo: after a
+    # first call (which looks up the scratch array's address), further calls
+    # leave the device's free memory unchanged. A first tersoff_compute on the
+    # same fresh context does allocate its per-neighbour buffers, which shows
+    # that the check would see an allocation.
+    x, t, box, table = _system(T, "max")
+    n = len(x)
+    for prec in (0, 1):
+        ctx = T.Context(prec)
+        ctx.params(table)
+        xd, td = _dev(x), _dev(t, torch.int32)
+        ctx.neighbor_build(xd, td, box, RC + 0.5)
+        out = _outputs(n)
+        ctx.compute_noalloc(xd, *out)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(3):
+            ctx.compute_noalloc(xd, *out)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (prec, free0 - free1)
+        ctx.compute(xd, *_outputs(n))
+        torch.cuda.synchronize()
+        free2, _ = torch.cuda.mem_get_info()
+        assert free2 < free1
+        ctx.close()
+
+
+def test_md_after_noalloc_equals_md_without(T):
+    # The call shares the context's status words with the force kernel; MD
+    # that follows it must equal MD on a context that never made the call.
+    x, t, box = W.diamond(4, 4, 4, 5.432)
+    rng = np.random.Generator(np.random.Philox(75))
+    x = W.jitter_gaussian(x, 0.05, rng)
+    mass = [W.MASS_AMU["Si"]]
+    v = W.maxwell_velocities(t, np.array(mass), 1000.0, rng)
+    table = S.table_for(["Si"], T.mix_tersoff89)
+    runs = []
+    for use_noalloc in (False, True):
+        ctx = T.Context(1)
+        ctx.params(table)
+        xd, vd = _dev(x), _dev(v)
+        ctx.neighbor_build(xd, _dev(t, torch.int32), box, RC + 1.0)
+        f = torch.zeros_like(xd)
+        ctx.compute(xd, None, f)
+        if use_noalloc:
+            ctx.compute_noalloc(xd, *_outputs(len(x)))
+        ctx.md_step(xd, vd, f, mass, 0.001, 15, 10)
+        torch.cuda.synchronize()
+        runs.append((xd.cpu().numpy(), vd.cpu().numpy(), f.cpu().numpy()))
+        ctx.close()
+    for a, b in zip(runs[0], runs[1]):
+        assert np.array_equal(a, b)
