@@ -151,7 +151,7 @@ def test_noalloc_allocates_no_device_memory(T):
         ctx.params(table)
         xd, td = _dev(x), _dev(t, torch.int32)
         ctx.neighbor_build(xd, td, box, RC + 0.5)
-        out = _outputs(n)
+        out, out2 = _outputs(n), _outputs(n)  # every tensor of the test allocated up front
         ctx.compute_noalloc(xd, *out)
         torch.cuda.synchronize()
         free0, _ = torch.cuda.mem_get_info()
@@ -160,7 +160,7 @@ def test_noalloc_allocates_no_device_memory(T):
         torch.cuda.synchronize()
         free1, _ = torch.cuda.mem_get_info()
         assert free1 == free0, (prec, free0 - free1)
-        ctx.compute(xd, *_outputs(n))
+        ctx.compute(xd, *out2)
         torch.cuda.synchronize()
         free2, _ = torch.cuda.mem_get_info()
         assert free2 < free1
