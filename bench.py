@@ -911,7 +911,9 @@ def run_ablations(args):
     register-resident neighbourhood with pre-computed derivatives (Sec. IV-A),
     each switched off alone and together, the compensated force sums replaced
     by plain float sums (the paper's all-single accumulation), and no list
-    filtering at all with the fast-forward lane scheme (Sec. IV-C). Reports
+    filtering at all with the fast-forward lane scheme (Sec. IV-C); and, under
+    the atomic scatter, each atom's own sums in plain float (the default)
+    against compensated sums carried into double. Reports
     ms per 10 MD steps and per force evaluation, and the force error against
     the default mixed path and against the FP64 path (the first three leave
     the forces unchanged up to rounding order)."""
@@ -926,31 +928,43 @@ def run_ablations(args):
     stream = torch.cuda.current_stream()
     out = {"metric": "ablations of the paper's design choices (mixed path)",
            "workload": workload_name(), "md_ms_per_10_steps": {}, "force_eval_ms": {},
-           "force_rms_rel_vs_default": {}, "force_rms_rel_vs_fp64": {}}
+           "force_rms_rel_vs_default": {}, "force_rms_rel_vs_fp64": {},
+           "energy_rel_vs_fp64": {}, "virial_max_rel_vs_fp64": {}}
     ref = None
     ctx = T.Context(T.FP64)
     ctx.params(table)
     xd = torch.tensor(x, dtype=torch.float64, device="cuda")
     ctx.neighbor_build(xd, torch.tensor(t, dtype=torch.int32, device="cuda"), box, R_LIST)
     fd = torch.zeros_like(xd)
-    ctx.compute(xd, None, fd)
+    e64 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    w64 = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(xd, e64, fd, w64)
     f64 = fd.cpu().numpy()
+    e64, w64 = e64.item(), w64.cpu().numpy()
     ctx.close()
     for name, flags in (("default", 0), ("no_short_list", T.ABLATE_NO_SHORT),
                         ("general_path", T.ABLATE_GENERAL),
                         ("both", T.ABLATE_NO_SHORT | T.ABLATE_GENERAL),
                         ("fp32_sums", T.ABLATE_FP32_SUMS),
-                        ("fast_forward", T.ABLATE_FASTFWD)):
+                        ("fast_forward", T.ABLATE_FASTFWD),
+                        ("atomic_scatter", "atomic"),
+                        ("atomic_scatter_comp_atom_sums", T.ABLATE_COMP_ATOM_SUMS)):
         ctx = T.Context(T.MIXED)
-        ctx.set_ablation(flags)
-        ctx.set_scatter(T.SCATTER_GATHER)
+        ctx.set_ablation(0 if flags == "atomic" else flags)
+        ctx.set_scatter(T.SCATTER_ATOMIC if flags in ("atomic", T.ABLATE_COMP_ATOM_SUMS)
+                        else T.SCATTER_GATHER)
         ctx.params(table)
         xd = torch.tensor(x, dtype=torch.float64, device="cuda")
         vd = torch.tensor(v, dtype=torch.float64, device="cuda")
         ctx.neighbor_build(xd, torch.tensor(t, dtype=torch.int32, device="cuda"), box, R_LIST)
         fd = torch.zeros_like(xd)
-        ctx.compute(xd, None, fd)
+        ee = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ww = torch.zeros(6, dtype=torch.float64, device="cuda")
+        ctx.compute(xd, ee, fd, ww)
         fr = fd.cpu().numpy()
+        out["energy_rel_vs_fp64"][name] = abs(ee.item() - e64) / abs(e64)
+        out["virial_max_rel_vs_fp64"][name] = float(np.abs(ww.cpu().numpy() - w64).max() /
+                                                    np.abs(w64).max())
         if ref is None:
             ref = fr
         out["force_rms_rel_vs_default"][name] = float(np.sqrt(((fr - ref) ** 2).mean()) /

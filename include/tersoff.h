@@ -42,8 +42,10 @@ typedef struct tersoff_ctx tersoff_ctx;
 
 /* arithmetic paths */
 #define TERSOFF_FP64 0  /* all arithmetic in double (the paper's Opt-D mode, Sec. V-E) */
-#define TERSOFF_MIXED 1 /* per-term arithmetic in float, sums across atoms in double
-                           (the paper's Opt-M mode, Sec. V-E) */
+#define TERSOFF_MIXED 1 /* per-term arithmetic and each atom's own sums over its
+                           terms in float; every sum across atoms in double, or in
+                           compensated float carried exactly into double (the
+                           paper's Opt-M mode, Sec. V-E) */
 
 /* Number of doubles per parameter record and their order. */
 #define TERSOFF_NPARAM 14
@@ -305,6 +307,17 @@ int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
 #define TERSOFF_ABLATE_GENERAL 2
 #define TERSOFF_ABLATE_FP32_SUMS 4
 #define TERSOFF_ABLATE_FASTFWD 8
+/* TERSOFF_ABLATE_COMP_ATOM_SUMS (mixed path, one species, single systems; a
+ * variant rather than a removal): the sums that one thread forms over the
+ * terms of its centre atom -- the force on each neighbour and on the atom,
+ * the atom's energy and virial, at most z(z-1) + z terms each -- are carried
+ * as compensated float pairs (TwoSum) and converted into double, and forces
+ * are scattered with FP64 atomics (whatever the scatter mode): every sum is
+ * then exact to double rounding beyond the float terms themselves, the strict
+ * reading of the paper's mixed mode (Sec. V-E). By default those per-atom sums
+ * are plain float; this switch measures what that costs. Atoms on the general
+ * path (more bonds than the register capacity) keep float per-atom sums. */
+#define TERSOFF_ABLATE_COMP_ATOM_SUMS 16
 int tersoff_set_ablation(tersoff_ctx* ctx, int flags);
 
 /* One-line text of the last tersoff_autotune: the chosen options and every

@@ -20,6 +20,7 @@ from ._lib import (  # noqa: F401
     ABLATE_GENERAL,
     ABLATE_FP32_SUMS,
     ABLATE_FASTFWD,
+    ABLATE_COMP_ATOM_SUMS,
     load,
     library_path,
     declared_symbols,

@@ -31,6 +31,7 @@ ABLATE_NO_SHORT = 1
 ABLATE_GENERAL = 2
 ABLATE_FP32_SUMS = 4
 ABLATE_FASTFWD = 8
+ABLATE_COMP_ATOM_SUMS = 16
 
 _lib = None
 
@@ -282,8 +283,8 @@ class Context:
         self._check(self.lib.tersoff_set_launch(self.h, int(waves), int(split), int(block)))
 
     def set_ablation(self, flags):
-        """ABLATE_NO_SHORT | ABLATE_GENERAL | ABLATE_FP32_SUMS | ABLATE_FASTFWD,
-        for measuring the design choices."""
+        """ABLATE_NO_SHORT | ABLATE_GENERAL | ABLATE_FP32_SUMS | ABLATE_FASTFWD |
+        ABLATE_COMP_ATOM_SUMS, for measuring the design choices."""
         self._check(self.lib.tersoff_set_ablation(self.h, int(flags)))
 
     def autotune_summary(self):

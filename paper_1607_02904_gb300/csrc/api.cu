@@ -1221,7 +1221,7 @@ int tersoff_set_launch(tersoff_ctx* p, int waves, int split, int block) {
 int tersoff_set_ablation(tersoff_ctx* p, int flags) {
   Ctx* c = C(p);
   if (!c) return TERSOFF_E_INVALID_ARG;
-  if (flags & ~15) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "ablation flags are bits 0 to 3");
+  if (flags & ~31) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "ablation flags are bits 0 to 4");
   c->ablate = flags;
   c->gen++;  // captured MD graphs hold the old kernel arguments
   return TERSOFF_OK;

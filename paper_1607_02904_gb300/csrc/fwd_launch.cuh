@@ -43,6 +43,10 @@ void launch_wide(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
 template <class T, int NS, int ZC, bool BATCH = false>
 void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
   if (grid <= 0) return;
+  if (sizeof(T) == 4 && NS == 1 && !BATCH && comp_atom_sums(c)) {
+    launch_forward_cs(c, &a, ZC, grid, s);
+    return;
+  }
   if (c->has_lam3)
     k_tersoff<T, NS, ZC, 1, BATCH><<<grid, BLOCK, 0, s>>>(a);
   else if (c->sym_table)
@@ -146,7 +150,7 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   a.contrib = c->d_contrib;
   a.rev = c->d_rev;
   a.kmask = c->d_kmask;
-  a.atomic_mode = c->scatter_atomic ? 1 : 0;
+  a.atomic_mode = (c->scatter_atomic || comp_atom_sums(c)) ? 1 : 0;
   a.own = c->d_own;
   a.acc = acc;
   a.eatom = eatom;

@@ -156,7 +156,7 @@ inline GatherArgs make_gather(Ctx* c) {
   g.n = c->n;
   g.cap = c->zs_cap;
   g.fp64 = c->precision == TERSOFF_FP64;
-  g.atomic_mode = c->scatter_atomic ? 1 : 0;
+  g.atomic_mode = (c->scatter_atomic || comp_atom_sums(c)) ? 1 : 0;
   g.plain = (c->ablate & 4) && c->precision == TERSOFF_MIXED;
   g.zcnt = c->d_zcnt;
   g.contrib = c->d_contrib;

@@ -278,6 +278,13 @@ __host__ __device__ constexpr int flag_bucket(int b) { return FLAG_BUCKET + b * 
 constexpr int ACC_STRIDE = 16;            // doubles
 constexpr int ACC_LEN = 8 * ACC_STRIDE;   // one accumulator row
 
+// The TERSOFF_ABLATE_COMP_ATOM_SUMS variant is active: mixed path, one
+// species, a single system. Its force kernel scatters with FP64 atomics.
+inline bool comp_atom_sums(const Ctx* c) {
+  return (c->ablate & TERSOFF_ABLATE_COMP_ATOM_SUMS) && c->precision == TERSOFF_MIXED &&
+         c->ns == 1 && c->n_sys == 0;
+}
+
 int fail(Ctx* c, int code, const std::string& msg);
 int cuda_fail(Ctx* c, cudaError_t e, const char* where);
 
@@ -303,6 +310,9 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s);
 int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f32(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
 int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
+// the force launches of the TERSOFF_ABLATE_COMP_ATOM_SUMS variant (fwd_f32_cs.cu),
+// register capacity 4 or 8; args is a fwd::FwdArgs<float>
+int launch_forward_cs(Ctx* c, const void* args, int zc, int grid, cudaStream_t s);
 // Batch of systems: forces (slots or atomics into f, as launch_forward),
 // per-atom energy d_eatom and virial d_vatom.
 int launch_forward_batch(Ctx* c, double* f, cudaStream_t s);

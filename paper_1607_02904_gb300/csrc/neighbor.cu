@@ -66,11 +66,8 @@ __global__ void k_bin(int n, const double* __restrict__ x, const __grid_constant
       finite = false;
       xa = 0.0;
     }
-    // periodic image k and wrapped coordinate w; atoms inside the box (the
-    // common case) skip the image arithmetic (FP64 operations are scarce)
-    const bool inside = xa >= 0.0 && xa < g.L[a];
-    const double k = inside ? 0.0 : floor(xa * g.invL[a]);
-    const double w = inside ? xa : xa - g.L[a] * k;
+    const double k = floor(xa * g.invL[a]);  // periodic image
+    const double w = xa - g.L[a] * k;
     int c = (int)(w * g.invh[a]);
     c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
     // origin = image corner of the cell; offsets x - o start inside the cell
@@ -224,16 +221,8 @@ __global__ void k_cell_pos(int n, const int* __restrict__ cell_atoms,
   posc[s] = make_float4(p.x, p.y, p.z, __int_as_float(4 * j + __float_as_int(p.w)));
 }
 
-constexpr int NEIGH_BLOCK = 128;
-
-// One thread per atom i. Phase 1 looks up the slot ranges of the 27 stencil
-// cells (in stencil order: oz, then oy, then ox) into the thread's column of
-// a shared-memory table. Phase 2 walks all candidates of the 27 ranges in one
-// flat loop, moving to the next non-empty range when the current one ends:
-// the lanes of a warp then run loops whose lengths differ only by their
-// candidate totals, instead of 27 nested loops of different lengths each.
 template <bool BATCH>
-__global__ void __launch_bounds__(NEIGH_BLOCK) k_neigh(
+__global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
     const float4* __restrict__ posc, const __grid_constant__ GridDev g1,
@@ -243,7 +232,6 @@ __global__ void __launch_bounds__(NEIGH_BLOCK) k_neigh(
     const __grid_constant__ Radii core, int ns,
     uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
     uint8_t* __restrict__ zwa, int* __restrict__ flags) {
-  __shared__ int2 rng[27][NEIGH_BLOCK];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
   int count = 0;
@@ -257,69 +245,51 @@ __global__ void __launch_bounds__(NEIGH_BLOCK) k_neigh(
     const int cx = ci % g.nc[0];
     const int cy = (ci / g.nc[0]) % g.nc[1];
     const int cz = ci / (g.nc[0] * g.nc[1]);
-    int total = 0;
-#pragma unroll
-    for (int r = 0; r < 27; ++r) {
-      int ax = cx + r % 3 - 1, ay = cy + (r / 3) % 3 - 1, az = cz + r / 9 - 1;
-      ax += (ax < 0) ? g.nc[0] : 0;
-      ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
-      ay += (ay < 0) ? g.nc[1] : 0;
-      ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
+    for (int oz = -1; oz <= 1; ++oz) {
+      int az = cz + oz;
       az += (az < 0) ? g.nc[2] : 0;
       az -= (az >= g.nc[2]) ? g.nc[2] : 0;
-      const int c = g.cell_base + (az * g.nc[1] + ay) * g.nc[0] + ax;
-      const int2 q = make_int2(cell_start[c], cell_start[c + 1]);
-      rng[r][threadIdx.x] = q;
-      total += q.y - q.x;
-    }
-    // current range r: slots [s, e), stencil shift and entry code
-    int r = 0;
-    int2 q = rng[0][threadIdx.x];
-    int s = q.x, e = q.y;
-    float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-    uint32_t code = 0;
-    bool fresh = true;  // shift and code of r not yet formed
-    for (int t = 0; t < total; ++t) {
-      while (s == e) {
-        ++r;
-        q = rng[r][threadIdx.x];
-        s = q.x;
-        e = q.y;
-        fresh = true;
-      }
-      if (fresh) {
-        const int ox = r % 3 - 1, oy = (r / 3) % 3 - 1, oz = r / 9 - 1;
-        sx = ox * g.hf[0];
-        sy = oy * g.hf[1];
-        sz = oz * g.hf[2];
-        code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) | ((uint32_t)(oz + 1) << 30);
-        fresh = false;
-      }
-      const float4 pj = posc[s];
-      ++s;
-      const int jt = __float_as_int(pj.w);
-      const int j = jt >> 2, tj = jt & 3;
-      if (j == i) continue;
-      const float dx = (pj.x - pi.x) + sx;
-      const float dy = (pj.y - pi.y) + sy;
-      const float dz = (pj.z - pi.z) + sz;
-      const float r2 = dx * dx + dy * dy + dz * dz;
-      bool in;
-      if (r2 < lo2)
-        in = true;
-      else if (r2 > hi2)
-        in = false;
-      else
-        in = exact_member(x, i, j, g, rc2, dx, dy, dz);
-      if (in) {
-        const uint32_t en = (uint32_t)j | code;
-        if (count < cap) nbr[(size_t)count * n + i] = en;
-        ++count;
-        // short list: within the filter radius plus the margin
-        if (r2 <= lim.r2[ti * ns + tj]) {
-          if (z < cap) shortl[(size_t)z * n + i] = en;
-          ++z;
-          zw += r2 <= core.r2[ti * ns + tj] ? 1 : 0;
+      for (int oy = -1; oy <= 1; ++oy) {
+        int ay = cy + oy;
+        ay += (ay < 0) ? g.nc[1] : 0;
+        ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
+        for (int ox = -1; ox <= 1; ++ox) {
+          int ax = cx + ox;
+          ax += (ax < 0) ? g.nc[0] : 0;
+          ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
+          const int c = g.cell_base + (az * g.nc[1] + ay) * g.nc[0] + ax;
+          const float sx = ox * g.hf[0], sy = oy * g.hf[1], sz = oz * g.hf[2];
+          const uint32_t code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) |
+                                ((uint32_t)(oz + 1) << 30);
+          const int s1 = cell_start[c + 1];
+          for (int s = cell_start[c]; s < s1; ++s) {
+            const float4 pj = posc[s];
+            const int jt = __float_as_int(pj.w);
+            const int j = jt >> 2, tj = jt & 3;
+            if (j == i) continue;
+            const float dx = (pj.x - pi.x) + sx;
+            const float dy = (pj.y - pi.y) + sy;
+            const float dz = (pj.z - pi.z) + sz;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            bool in;
+            if (r2 < lo2)
+              in = true;
+            else if (r2 > hi2)
+              in = false;
+            else
+              in = exact_member(x, i, j, g, rc2, dx, dy, dz);
+            if (in) {
+              const uint32_t e = (uint32_t)j | code;
+              if (count < cap) nbr[(size_t)count * n + i] = e;
+              ++count;
+              // short list: within the filter radius plus the margin
+              if (r2 <= lim.r2[ti * ns + tj]) {
+                if (z < cap) shortl[(size_t)z * n + i] = e;
+                ++z;
+                zw += r2 <= core.r2[ti * ns + tj] ? 1 : 0;
+              }
+            }
+          }
         }
       }
     }
@@ -501,12 +471,12 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
     }
   if (n > 0) {
     if (batch)
-      k_neigh<true><<<(n + NEIGH_BLOCK - 1) / NEIGH_BLOCK, NEIGH_BLOCK, 0, s>>>(
+      k_neigh<true><<<(n + 127) / 128, 128, 0, s>>>(
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, c->d_geo,
           c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
           c->d_zcnt, c->d_bucket, c->d_zw, c->d_flags);
     else
-      k_neigh<false><<<(n + NEIGH_BLOCK - 1) / NEIGH_BLOCK, NEIGH_BLOCK, 0, s>>>(
+      k_neigh<false><<<(n + 127) / 128, 128, 0, s>>>(
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
           c->d_bucket, c->d_zw, c->d_flags);

@@ -589,18 +589,17 @@ __device__ __forceinline__ void clear_slots(const FwdArgs<T>& a, int i) {
 }
 
 // ---------------------------------------------------------------- reduction
-// Energy and virial: the 7 per-thread values (padded to 8) are converted to
-// double (exactly) and reduce-scattered across the warp in double (halving
+// Energy and virial: the 7 per-thread sums in double (padded to 8) are
+// reduce-scattered across the warp in double (halving
 // exchanges: 4, 2, 1 values), then summed over the remaining lanes; lanes 0,
 // 4, ..., 28 end with the 8 warp totals. Warp totals are summed in double over
 // the block and added to acc with one atomic each. Every sum across atoms is
 // thus in double.
-template <class T, int NB = BLOCK>
-__device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc) {
+template <int NB = BLOCK>
+__device__ __forceinline__ void block_reduce_store_d(double ei, const double* w, double* acc) {
   __shared__ double part[NB / 32][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double v[8] = {to_f64(ei),   to_f64(w[0]), to_f64(w[1]), to_f64(w[2]),
-                 to_f64(w[3]), to_f64(w[4]), to_f64(w[5]), 0.0};
+  double v[8] = {ei, w[0], w[1], w[2], w[3], w[4], w[5], 0.0};
   const bool hi16 = lane & 16;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -636,8 +635,39 @@ __device__ __forceinline__ void block_reduce_store(T ei, const T* w, double* acc
 }
 
 // ---------------------------------------------------------------- the kernel
-template <class T, int NS, int ZC, int MODE, bool BATCH = false>
+// Running sum of one thread: plain (CS false) or compensated (CS true: Knuth's
+// TwoSum keeps the rounding error of every float addition in e, so s + e is
+// the exact sum of the added terms up to the rounding of e itself).
+template <class T, bool CS> struct Acc {
+  T s = T(0);
+  __device__ __forceinline__ void add(T x) { s += x; }
+  __device__ __forceinline__ void sub(const Acc& o) { s -= o.s; }
+  __device__ __forceinline__ T lo() const { return T(0); }
+  __device__ __forceinline__ double d() const { return to_f64(s); }
+};
+template <class T> struct Acc<T, true> {
+  T s = T(0), e = T(0);
+  __device__ __forceinline__ void add(T x) {
+    const T t = s + x;
+    const T bp = t - s;
+    e += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ void sub(const Acc& o) {
+    add(-o.s);
+    e -= o.e;
+  }
+  __device__ __forceinline__ T lo() const { return e; }
+  __device__ __forceinline__ double d() const { return to_f64(s) + to_f64(e); }
+};
+
+// CS (float, one species, single systems only): every sum a thread forms over
+// the terms of its atom -- the force on each neighbour and on the atom, its
+// energy and virial -- is compensated, carried into double, and forces are
+// scattered with FP64 atomics (the TERSOFF_ABLATE_COMP_ATOM_SUMS variant).
+template <class T, int NS, int ZC, int MODE, bool BATCH = false, bool CS = false>
 __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
+  static_assert(!(CS && BATCH), "compensated per-atom sums: single systems only");
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
   __shared__ T srec_s[SREC];
@@ -676,8 +706,14 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
   const bool use_short = __int_as_float(uni[2]) <= a.dlim2;
   const bool slots = !a.atomic_mode && use_short && slots_ok;
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[FLAG_EXTRA] = slots ? 0 : 1;
-  T ei = 0;
-  T w[6] = {0, 0, 0, 0, 0, 0};
+  // the atom's own virial sums (float), and the thread's energy and virial
+  // over its atoms in double, kept in the thread's column of a shared-memory
+  // table (not in registers) and formed only when the reduction is wanted
+  T w[6];
+  __shared__ double tsum[7][BLOCK];
+  const bool want_acc = a.acc != nullptr;
+  if (want_acc)
+    for (int q = 0; q < 7; ++q) tsum[q][threadIdx.x] = 0.0;
   bool any = false;
   for (int item = blockIdx.x * BLOCK + threadIdx.x; item < n_items;
        item += gridDim.x * BLOCK) {
@@ -686,10 +722,11 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
                   : (item < n_first ? a.order[item]
                      : (item < n_second ? a.order2[item - n_first] : a.order3[item - n_second]));
     T eatom_i = T(0);
+    Acc<T, CS> eatom_c;  // CS: the atom's energy (fast path)
+    Acc<T, CS> wa[6];    // CS: the atom's virial (fast path)
+    for (int q = 0; q < 6; ++q) w[q] = T(0);
     Shift<T, BATCH> sh;
     sh.load(a, i);
-    if (BATCH)
-      for (int q = 0; q < 6; ++q) w[q] = T(0);
     int ti;
     int z;
     unsigned long long mask = 0ull;
@@ -833,9 +870,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
           tt[q] = tj;
         }
       }
-      T fx[ZC], fy[ZC], fz[ZC];
-#pragma unroll
-      for (int q = 0; q < ZC; ++q) fx[q] = fy[q] = fz[q] = T(0);
+      Acc<T, CS> fx[ZC], fy[ZC], fz[ZC];
 
       if (MODE == 2) {
         // Symmetric tables without a lambda3 term: the angular part of
@@ -868,11 +903,11 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             if (rr[qj] < p2[K_ROUT2]) {
               T V, dVdr, dz;
               pair_fc<T>(p2, rr[qj], zeta[qj], fc3[qj], dfc3[qj], V, dVdr, dz);
-              eatom_i += V;
+              eatom_c.add(V);
               dzt[qj] = dz;
-              fx[qj] -= dVdr * ux[qj];
-              fy[qj] -= dVdr * uy[qj];
-              fz[qj] -= dVdr * uz[qj];
+              fx[qj].add(-dVdr * ux[qj]);
+              fy[qj].add(-dVdr * uy[qj]);
+              fz[qj].add(-dVdr * uz[qj]);
             }
           }
         // pass 2: -dV/dzeta_ij d zeta_ij/dx - dV/dzeta_ik d zeta_ik/dx per pair {j,k}
@@ -892,12 +927,12 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
               const T cj = A * ri[qj], ck = A * ri[qk];
               const T bj = -dzt[qk] * dfc3[qj] * g;
               const T bk = -dzt[qj] * dfc3[qk] * g;
-              fx[qj] += cj * (ux[qk] - cs * ux[qj]) + bj * ux[qj];
-              fy[qj] += cj * (uy[qk] - cs * uy[qj]) + bj * uy[qj];
-              fz[qj] += cj * (uz[qk] - cs * uz[qj]) + bj * uz[qj];
-              fx[qk] += ck * (ux[qj] - cs * ux[qk]) + bk * ux[qk];
-              fy[qk] += ck * (uy[qj] - cs * uy[qk]) + bk * uy[qk];
-              fz[qk] += ck * (uz[qj] - cs * uz[qk]) + bk * uz[qk];
+              fx[qj].add(cj * (ux[qk] - cs * ux[qj]) + bj * ux[qj]);
+              fy[qj].add(cj * (uy[qk] - cs * uy[qj]) + bj * uy[qj]);
+              fz[qj].add(cj * (uz[qk] - cs * uz[qj]) + bj * uz[qj]);
+              fx[qk].add(ck * (ux[qj] - cs * ux[qk]) + bk * ux[qk]);
+              fy[qk].add(ck * (uy[qj] - cs * uy[qk]) + bk * uy[qk]);
+              fz[qk].add(ck * (uz[qj] - cs * uz[qk]) + bk * uz[qk]);
             }
       } else
 #pragma unroll
@@ -933,23 +968,23 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             }
             T V, dVdr, dz;
             pair<T>(p2, rij, zeta, V, dVdr, dz, rex[qj]);
-            eatom_i += V;
-            fx[qj] -= dVdr * ux[qj] + dz * gjx;
-            fy[qj] -= dVdr * uy[qj] + dz * gjy;
-            fz[qj] -= dVdr * uz[qj] + dz * gjz;
+            eatom_c.add(V);
+            fx[qj].add(-(dVdr * ux[qj] + dz * gjx));
+            fy[qj].add(-(dVdr * uy[qj] + dz * gjy));
+            fz[qj].add(-(dVdr * uz[qj] + dz * gjz));
 #pragma unroll
             for (int qk = 0; qk < ZC; ++qk) {
               if (qk != qj) {
-                fx[qk] -= dz * gkx[qk];
-                fy[qk] -= dz * gky[qk];
-                fz[qk] -= dz * gkz[qk];
+                fx[qk].add(-dz * gkx[qk]);
+                fy[qk].add(-dz * gky[qk]);
+                fz[qk].add(-dz * gkz[qk]);
               }
             }
           }
         }
       }
       // force on i and virial from the neighbour forces; scatter
-      T fix = 0, fiy = 0, fiz = 0;
+      Acc<T, CS> fix, fiy, fiz;
       unsigned long long left = kept;
 #pragma unroll
       for (int q = 0; q < ZC; ++q) {
@@ -959,22 +994,31 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             sl = __ffsll(left) - 1;
             left &= left - 1ull;
           }
-          fix -= fx[q];
-          fiy -= fy[q];
-          fiz -= fz[q];
+          fix.sub(fx[q]);
+          fiy.sub(fy[q]);
+          fiz.sub(fz[q]);
           const T dx = ux[q] * rr[q], dy = uy[q] * rr[q], dz = uz[q] * rr[q];
-          w[0] += dx * fx[q];
-          w[1] += dy * fy[q];
-          w[2] += dz * fz[q];
-          w[3] += dx * fy[q];
-          w[4] += dx * fz[q];
-          w[5] += dy * fz[q];
+          if (CS) {
+            wa[0].add(dx * fx[q].s + dx * fx[q].lo());
+            wa[1].add(dy * fy[q].s + dy * fy[q].lo());
+            wa[2].add(dz * fz[q].s + dz * fz[q].lo());
+            wa[3].add(dx * fy[q].s + dx * fy[q].lo());
+            wa[4].add(dx * fz[q].s + dx * fz[q].lo());
+            wa[5].add(dy * fz[q].s + dy * fz[q].lo());
+          } else {
+            w[0] += dx * fx[q].s;
+            w[1] += dy * fy[q].s;
+            w[2] += dz * fz[q].s;
+            w[3] += dx * fy[q].s;
+            w[4] += dx * fz[q].s;
+            w[5] += dy * fz[q].s;
+          }
           if (slots)
             store_slot<T>(a, a.contrib,
                           filtered ? recv_slot(a, sl, i, jj[q]) : (size_t)rv[q] * a.n + jj[q],
-                          fx[q], fy[q], fz[q]);
+                          fx[q].s, fy[q].s, fz[q].s);
           else
-            atomic_add3(a.f, jj[q], to_f64(fx[q]), to_f64(fy[q]), to_f64(fz[q]));
+            atomic_add3(a.f, jj[q], fx[q].d(), fy[q].d(), fz[q].d());
         }
       }
       if (slots && filtered) {
@@ -994,16 +1038,35 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
         a.kmask[i] = ~0ull;  // every entry written
       }
       if (slots)
-        store_slot<T>(a, a.own, (size_t)i, fix, fiy, fiz);
+        store_slot<T>(a, a.own, (size_t)i, fix.s, fiy.s, fiz.s);
       else
-        atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
+        atomic_add3(a.f, i, fix.d(), fiy.d(), fiz.d());
     }
+    if (CS) {
+      // the general path's float sums (eatom_i, w) and the fast path's
+      // compensated ones (eatom_c, wa), into the thread's double sums
+      const double e_at = to_f64(eatom_i) + eatom_c.d();
+      if (a.eatom) a.eatom[i] = e_at;
+      if (want_acc) {
+        tsum[0][threadIdx.x] += e_at;
+        for (int q = 0; q < 6; ++q) tsum[1 + q][threadIdx.x] += to_f64(w[q]) + wa[q].d();
+      }
+      continue;
+    }
+    eatom_i += eatom_c.s;
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
-    ei += eatom_i;
+    if (want_acc) {
+      tsum[0][threadIdx.x] += to_f64(eatom_i);
+      for (int q = 0; q < 6; ++q) tsum[1 + q][threadIdx.x] += to_f64(w[q]);
+    }
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T>(ei, w, a.acc);
+  if (want_acc && __syncthreads_or(any)) {
+    double wd[6];
+    for (int q = 0; q < 6; ++q) wd[q] = tsum[1 + q][threadIdx.x];
+    block_reduce_store_d(tsum[0][threadIdx.x], wd, a.acc);
+  }
 }
 
 // ---------------------------------------------------------------- wide kernel
@@ -1051,8 +1114,13 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
   auto at = [&](int q, int f) -> T& {
     return sl[((size_t)q * WIDE_WORDS + f) * WIDE_BLOCK + threadIdx.x];
   };
-  T ei = 0;
-  T w[6] = {0, 0, 0, 0, 0, 0};
+  // the atom's own virial sums (float); energy and virial over the thread's
+  // atoms in double (only when the reduction is wanted)
+  T w[6];
+  __shared__ double tsum[7][WIDE_BLOCK];
+  const bool want_acc = a.acc != nullptr;
+  if (want_acc)
+    for (int q = 0; q < 7; ++q) tsum[q][threadIdx.x] = 0.0;
   bool any = false;
   for (int item = blockIdx.x * WIDE_BLOCK + threadIdx.x; item < n_items;
        item += gridDim.x * WIDE_BLOCK) {
@@ -1061,8 +1129,7 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
     if (!slots && !a.atomic_mode) clear_slots<T>(a, i);
     Shift<T, BATCH> sh;
     sh.load(a, i);
-    if (BATCH)
-      for (int q = 0; q < 6; ++q) w[q] = T(0);
+    for (int q = 0; q < 6; ++q) w[q] = T(0);
     using P = typename SelfPos<T>::type;
     const P pi = self_pos<T>(a, i);
     const int ti = a.types[i];
@@ -1187,11 +1254,18 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
         atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
     }
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
-    ei += eatom_i;
+    if (want_acc) {
+      tsum[0][threadIdx.x] += to_f64(eatom_i);
+      for (int q = 0; q < 6; ++q) tsum[1 + q][threadIdx.x] += to_f64(w[q]);
+    }
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (a.acc != nullptr && __syncthreads_or(any)) block_reduce_store<T, WIDE_BLOCK>(ei, w, a.acc);
+  if (want_acc && __syncthreads_or(any)) {
+    double wd[6];
+    for (int q = 0; q < 6; ++q) wd[q] = tsum[1 + q][threadIdx.x];
+    block_reduce_store_d<WIDE_BLOCK>(tsum[0][threadIdx.x], wd, a.acc);
+  }
 }
 
 // ---------------------------------------------------------------- fast-forward ablation
@@ -1220,8 +1294,8 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_ffwd(const __grid_constant__ 
   if (blockIdx.x == 0 && threadIdx.x == 0) a.flags[FLAG_EXTRA] = 1;
   using P = typename SelfPos<T>::type;
   const Shift<T, false> sh;
-  T ei = 0;
-  T w[6] = {0, 0, 0, 0, 0, 0};
+  T w[6];
+  double eid = 0.0, wd[6] = {0, 0, 0, 0, 0, 0};
   // block-uniform loop: every lane of a warp takes part in every vote
   for (int i0 = blockIdx.x * BLOCK; i0 < a.n; i0 += gridDim.x * BLOCK) {
     const int i = i0 + threadIdx.x;
@@ -1234,6 +1308,7 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_ffwd(const __grid_constant__ 
       if (!a.atomic_mode) clear_slots<T>(a, i);
     }
     T eatom_i = 0, fix = 0, fiy = 0, fiz = 0;
+    for (int q = 0; q < 6; ++q) w[q] = T(0);
     // bond to the entry in slot s: vector, length, exact residual near a cutoff
     auto bond = [&](int s, T& dx, T& dy, T& dz, T& r, T& rx, int& j, int& tj) {
       const uint32_t e = a.nbr[(size_t)s * a.n + i];
@@ -1357,9 +1432,10 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_ffwd(const __grid_constant__ 
       atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
       if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     }
-    ei += eatom_i;
+    eid += to_f64(eatom_i);
+    for (int q = 0; q < 6; ++q) wd[q] += to_f64(w[q]);
   }
-  if (a.acc != nullptr) block_reduce_store<T>(ei, w, a.acc);
+  if (a.acc != nullptr) block_reduce_store_d(eid, wd, a.acc);
 }
 
 }  // namespace fwd

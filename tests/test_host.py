@@ -33,7 +33,7 @@ def test_header_constants_match_binding():
     assert int(consts["TERSOFF_FP64"]) == T.FP64
     assert int(consts["TERSOFF_MIXED"]) == T.MIXED
     assert int(consts["TERSOFF_NOALLOC_MAX_ATOMS"]) == T.NOALLOC_MAX_ATOMS
-    for name in ("NO_SHORT", "GENERAL", "FP32_SUMS", "FASTFWD"):
+    for name in ("NO_SHORT", "GENERAL", "FP32_SUMS", "FASTFWD", "COMP_ATOM_SUMS"):
         assert int(consts["TERSOFF_ABLATE_" + name]) == getattr(T, "ABLATE_" + name)
     order = ["M", "GAMMA", "LAMBDA3", "C", "D", "H", "N", "BETA", "LAMBDA2", "B", "R", "D_CUT",
              "LAMBDA1", "A"]
