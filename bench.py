@@ -489,6 +489,11 @@ def run_ours(args):
         "measured_peaks": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")} if peaks else None,
         "pipe_peaks": pk,
     }
+    if world > 1 and not args.no_extra:
+        # the sharded fitting step needs every rank (collectives)
+        sf = sharded_fit(T, W, dev, flush, world, rank)
+        if rank == 0:
+            out["sharded_fit"] = sf
     if rank == 0 and not args.no_extra:
         out["backward"] = time_backward(T, ctxm, xdm, ctx64, xd64, flush)
     ctxm.close()
@@ -641,6 +646,95 @@ def batched_fit(T, W, dev, flush, cells, gen_seconds, reps=20):
            "forward_ms": fwd_ms, "backward_ms": bwd_ms, "autotune": tune,
            "loss": float(static_loss.item()),
            "grad_norm": float(tab.grad.norm().item())}
+    system.ctx.close()
+    return out
+
+
+def sharded_fit(T, W, dev, flush, world, rank, reps=20):
+    """The 256-cell fitting step sharded over the ranks (one GPU each): every
+    rank takes its cost-balanced share of the cells (shard.shard_cells),
+    generates only those, and runs the same fitting step as batched_fit on them
+    (forward, loss on energies and forces, parameter VJP; captured in one CUDA
+    graph); the loss and the table gradient are then summed over ranks with one
+    NCCL all-reduce each (shard.fit_step). The time of a step is the slowest
+    rank's; the work is all ranks' atoms."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_1607_02904_gb300 import shard
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    sizes, _ = W.batched_cell_sizes(256)
+    mine = shard.shard_cells(sizes, world, rank)
+    cells = W.batched_cells(n_cells=256, subset=mine)
+    gen_s = time.time() - t0
+    names = ["Si", "C"]
+    table = T.mix_tersoff89(*W.element_records(names))
+    off = np.cumsum([0] + [len(c[0]) for c in cells]).astype(np.int32)
+    x = np.concatenate([c[0] for c in cells])
+    t = np.concatenate([c[1] for c in cells]).astype(np.int32)
+    boxes = np.stack([c[2] for c in cells])
+    xd = torch.tensor(x, dtype=torch.float64, device=dev)
+    rng = np.random.Generator(np.random.Philox(1607029044))
+    pert = table.copy()
+    cont = np.arange(table.size) % T.NPARAM != 0
+    pert[cont] *= 1.0 + 0.01 * rng.normal(0.0, 1.0, size=int(cont.sum()))
+    ref = T.TersoffBatch(t, off, boxes, R_LIST, precision=T.FP64)
+    with torch.no_grad():
+        e0, f0 = T.energy_forces(ref, xd, torch.tensor(pert, dtype=torch.float64))
+    e0, f0 = e0.clone(), f0.clone()
+    ref.ctx.close()
+    system = T.TersoffBatch(t, off, boxes, R_LIST, precision=T.MIXED)
+    tab = torch.tensor(table, dtype=torch.float64, device=dev, requires_grad=True)
+    with torch.no_grad():
+        T.energy_forces(system, xd, tab)
+
+    def step():
+        E, F = T.energy_forces(system, xd, tab)
+        loss = ((E - e0) ** 2).sum() + ((F - f0) ** 2).sum()
+        loss.backward()
+        return loss
+
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            tab.grad = None
+            step()
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    tab.grad = None
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        static_loss = step()
+    loss_sum = static_loss.detach().reshape(1)
+    for _ in range(3):
+        graph.replay()
+        shard.fit_step(lambda: (loss_sum, tab.grad))
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(reps):
+        flush.zero_()
+        dist.barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        shard.fit_step(lambda: (loss_sum, tab.grad))
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    ms /= reps
+    atoms = float(len(x))
+    tmax, atoms_all = aggregate(ms, atoms, world)
+    out = {"workload": "256 periodic Si/C cells (the batched fitting workload) sharded over "
+                       f"{world} ranks by cost (atoms x 16); one NCCL all-reduce of the loss "
+                       "and of the table gradient per step",
+           "ranks": world, "cells_this_rank": len(mine), "atoms_this_rank": int(atoms),
+           "atoms_all_ranks": int(atoms_all), "fit_step_ms": tmax,
+           "atoms_per_s": atoms_all / (tmax * 1e-3), "cell_generation_s_this_rank": gen_s,
+           "loss": float(loss_sum.item()), "grad_norm": float(tab.grad.norm().item())}
     system.ctx.close()
     return out
 

@@ -259,7 +259,9 @@ int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int 
  *   - the block size of the pack, integrate and gather kernels (128/256/512).
  * One option at a time, the others fixed at their best so far (coordinate
  * descent); every trial is the median of 5 timed repetitions (CUDA events on
- * `stream`) after 2 untimed ones.
+ * `stream`) after 2 untimed ones. The winner then replaces the context's
+ * starting options only if a confirming pair of trials (9 repetitions each)
+ * finds it at least 1% faster.
  * With v != NULL the repetition is one tersoff_md_step call of `steps` steps
  * (list rebuilt after the last step) on internal copies of x and v (device,
  * N x 3, not modified), mass (host) and dt as for tersoff_md_step; afterwards

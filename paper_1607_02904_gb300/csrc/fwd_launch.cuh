@@ -47,12 +47,22 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
     launch_forward_cs(c, &a, ZC, grid, s);
     return;
   }
-  if (c->has_lam3)
+  // forces only (MD steps): the instance without energy and virial sums
+  const bool ev = BATCH || a.acc != nullptr || a.eatom != nullptr;
+  if (ZC == 4 && !BATCH && !ev) {
+    if (c->has_lam3)
+      k_tersoff<T, NS, ZC, 1, false, false, false><<<grid, BLOCK, 0, s>>>(a);
+    else if (c->sym_table)
+      k_tersoff<T, NS, ZC, 2, false, false, false><<<grid, BLOCK, 0, s>>>(a);
+    else
+      k_tersoff<T, NS, ZC, 0, false, false, false><<<grid, BLOCK, 0, s>>>(a);
+  } else if (c->has_lam3) {
     k_tersoff<T, NS, ZC, 1, BATCH><<<grid, BLOCK, 0, s>>>(a);
-  else if (c->sym_table)
+  } else if (c->sym_table) {
     k_tersoff<T, NS, ZC, 2, BATCH><<<grid, BLOCK, 0, s>>>(a);
-  else
+  } else {
     k_tersoff<T, NS, ZC, 0, BATCH><<<grid, BLOCK, 0, s>>>(a);
+  }
   c->launches++;
 }
 
@@ -70,7 +80,7 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
 inline int force_grid(const Ctx* c, int zc) {
   const int full = (c->n + BLOCK - 1) / BLOCK;
   if (c->opt_waves <= 0 || c->n_sm <= 0) return full;
-  const int resident = c->n_sm * (zc <= 4 ? 7 : 4);
+  const int resident = c->n_sm * (zc <= 4 ? 8 : 4);
   const int g = c->opt_waves * resident;
   return g < full ? g : full;
 }

@@ -221,19 +221,10 @@ __global__ void k_cell_pos(int n, const int* __restrict__ cell_atoms,
   posc[s] = make_float4(p.x, p.y, p.z, __int_as_float(4 * j + __float_as_int(p.w)));
 }
 
-// One thread per atom, threads taking the atoms in cell order (lanes of a
-// warp hold atoms of the same or adjacent cells, whose candidate sets
-// coincide or overlap). The 27 stencil cells are walked as 9 rows of three
-// cells along x: away from the periodic edge in x the three cells of a row
-// are consecutive in the cell numbering, so their atoms form one slot range,
-// and a candidate's cell offset in x follows from two slot comparisons. The
-// candidate loop has no data-dependent branch except the rare exact test:
-// list entries are written by predicated stores.
 template <bool BATCH>
 __global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
-    const int* __restrict__ cell_atoms,
     const float4* __restrict__ posc, const __grid_constant__ GridDev g1,
     const GridDev* __restrict__ geo,
     const int* __restrict__ atom_sys, double rc2, float lo2, float hi2, int cap,
@@ -241,9 +232,8 @@ __global__ void __launch_bounds__(128) k_neigh(
     const __grid_constant__ Radii core, int ns,
     uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
     uint8_t* __restrict__ zwa, int* __restrict__ flags) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = t < n;
-  const int i = active ? cell_atoms[t] : 0;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i < n;
   int count = 0;
   int z = 0;
   int zw = 0;  // entries inside the filter radii without the margin
@@ -255,66 +245,51 @@ __global__ void __launch_bounds__(128) k_neigh(
     const int cx = ci % g.nc[0];
     const int cy = (ci / g.nc[0]) % g.nc[1];
     const int cz = ci / (g.nc[0] * g.nc[1]);
-    // interior in x: the row's three cells are consecutive
-    const bool inner = cx > 0 && cx < g.nc[0] - 1;
-    const float hx = g.hf[0];
-    uint32_t* wn = nbr + i;     // next skin-list slot of atom i
-    uint32_t* ws = shortl + i;  // next short-list slot
-    for (int row = 0; row < 9; ++row) {
-      const int oy = row % 3 - 1, oz = row / 3 - 1;
-      int ay = cy + oy;
-      ay += (ay < 0) ? g.nc[1] : 0;
-      ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
+    for (int oz = -1; oz <= 1; ++oz) {
       int az = cz + oz;
       az += (az < 0) ? g.nc[2] : 0;
       az -= (az >= g.nc[2]) ? g.nc[2] : 0;
-      const int rbase = g.cell_base + (az * g.nc[1] + ay) * g.nc[0];
-      const float sy = oy * g.hf[1], sz = oz * g.hf[2];
-      const uint32_t rcode = ((uint32_t)(oy + 1) << 28) | ((uint32_t)(oz + 1) << 30);
-      // segments of the row: one (interior) or the three cells one by one
-      const int nseg = inner ? 1 : 3;
-      for (int sg = 0; sg < nseg; ++sg) {
-        int s0, e, b1, b2, oxb;
-        if (inner) {
-          const int c0 = rbase + cx - 1;
-          s0 = cell_start[c0];
-          b1 = cell_start[c0 + 1];
-          b2 = cell_start[c0 + 2];
-          e = cell_start[c0 + 3];
-          oxb = -1;
-        } else {
-          oxb = sg - 1;
-          int ax = cx + oxb;
+      for (int oy = -1; oy <= 1; ++oy) {
+        int ay = cy + oy;
+        ay += (ay < 0) ? g.nc[1] : 0;
+        ay -= (ay >= g.nc[1]) ? g.nc[1] : 0;
+        for (int ox = -1; ox <= 1; ++ox) {
+          int ax = cx + ox;
           ax += (ax < 0) ? g.nc[0] : 0;
           ax -= (ax >= g.nc[0]) ? g.nc[0] : 0;
-          s0 = cell_start[rbase + ax];
-          e = cell_start[rbase + ax + 1];
-          b1 = b2 = 0x7fffffff;
-        }
-        const float sxb = oxb * hx;
-        for (int s = s0; s < e; ++s) {
-          const float4 pj = posc[s];
-          const int jt = __float_as_int(pj.w);
-          const int j = jt >> 2, tj = jt & 3;
-          const int up = (s >= b1 ? 1 : 0) + (s >= b2 ? 1 : 0);  // ox - oxb
-          const float dx = (pj.x - pi.x) + (sxb + (float)up * hx);
-          const float dy = (pj.y - pi.y) + sy;
-          const float dz = (pj.z - pi.z) + sz;
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          bool in = r2 < lo2;
-          if (!in && r2 <= hi2)  // near r_list: the exact test (rare)
-            in = exact_member(x, i, j, g, rc2, dx, dy, dz);
-          in = in && j != i;
-          const uint32_t en = (uint32_t)j | rcode | ((uint32_t)(oxb + 1 + up) << 26);
-          if (in && count < cap) *wn = en;
-          wn += in ? n : 0;
-          count += in ? 1 : 0;
-          // short list: within the filter radius plus the margin
-          const bool sh = in && r2 <= lim.r2[ti * ns + tj];
-          if (sh && z < cap) *ws = en;
-          ws += sh ? n : 0;
-          z += sh ? 1 : 0;
-          zw += (sh && r2 <= core.r2[ti * ns + tj]) ? 1 : 0;
+          const int c = g.cell_base + (az * g.nc[1] + ay) * g.nc[0] + ax;
+          const float sx = ox * g.hf[0], sy = oy * g.hf[1], sz = oz * g.hf[2];
+          const uint32_t code = ((uint32_t)(ox + 1) << 26) | ((uint32_t)(oy + 1) << 28) |
+                                ((uint32_t)(oz + 1) << 30);
+          const int s1 = cell_start[c + 1];
+          for (int s = cell_start[c]; s < s1; ++s) {
+            const float4 pj = posc[s];
+            const int jt = __float_as_int(pj.w);
+            const int j = jt >> 2, tj = jt & 3;
+            if (j == i) continue;
+            const float dx = (pj.x - pi.x) + sx;
+            const float dy = (pj.y - pi.y) + sy;
+            const float dz = (pj.z - pi.z) + sz;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            bool in;
+            if (r2 < lo2)
+              in = true;
+            else if (r2 > hi2)
+              in = false;
+            else
+              in = exact_member(x, i, j, g, rc2, dx, dy, dz);
+            if (in) {
+              const uint32_t e = (uint32_t)j | code;
+              if (count < cap) nbr[(size_t)count * n + i] = e;
+              ++count;
+              // short list: within the filter radius plus the margin
+              if (r2 <= lim.r2[ti * ns + tj]) {
+                if (z < cap) shortl[(size_t)z * n + i] = e;
+                ++z;
+                zw += r2 <= core.r2[ti * ns + tj] ? 1 : 0;
+              }
+            }
+          }
         }
       }
     }
@@ -370,15 +345,13 @@ __global__ void __launch_bounds__(128) k_neigh(
 
 // Reverse slots: for each short-list entry (j -> i), the slot of j in i's
 // short list (255 if absent), used to gather forces without atomics.
-// Four threads per atom j, thread p0 taking the entries p0, p0 + 4, ...
 __global__ void k_rev(int n, const uint32_t* __restrict__ shortl, const int* __restrict__ zcnt,
                       int cap, uint8_t* __restrict__ rev, int* __restrict__ flags) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = (int)(t >> 2);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int z = zcnt[j];
   z = z < cap ? z : cap;
-  for (int p = (int)(t & 3); p < z; p += 4) {
+  for (int p = 0; p < z; ++p) {
     const int i = (int)(shortl[(size_t)p * n + j] & ENTRY_JMASK);
     int zi = zcnt[i];
     zi = zi < cap ? zi : cap;
@@ -499,17 +472,16 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   if (n > 0) {
     if (batch)
       k_neigh<true><<<(n + 127) / 128, 128, 0, s>>>(
-          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_cell_atoms, c->d_posc, g, c->d_geo,
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, c->d_geo,
           c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
           c->d_zcnt, c->d_bucket, c->d_zw, c->d_flags);
     else
       k_neigh<false><<<(n + 127) / 128, 128, 0, s>>>(
-          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_cell_atoms, c->d_posc, g, nullptr,
-          nullptr,
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
           c->d_bucket, c->d_zw, c->d_flags);
-    k_rev<<<(int)((4 * (long long)n + 255) / 256), 256, 0, s>>>(n, c->d_short, c->d_zcnt,
-                                                                c->zs_cap, c->d_rev, c->d_flags);
+    k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
+                                          c->d_flags);
     c->launches += 2;
   }
   TGB_CUDA(c, cudaGetLastError());

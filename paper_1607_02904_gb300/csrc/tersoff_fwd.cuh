@@ -665,9 +665,14 @@ template <class T> struct Acc<T, true> {
 // the terms of its atom -- the force on each neighbour and on the atom, its
 // energy and virial -- is compensated, carried into double, and forces are
 // scattered with FP64 atomics (the TERSOFF_ABLATE_COMP_ATOM_SUMS variant).
-template <class T, int NS, int ZC, int MODE, bool BATCH = false, bool CS = false>
-__global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __grid_constant__ FwdArgs<T> a) {
+// EV false: forces only (no energy, virial or per-atom energy requested, a
+// single system): the instance the MD steps launch, with no energy or virial
+// bookkeeping and room for one more block per SM.
+template <class T, int NS, int ZC, int MODE, bool BATCH = false, bool CS = false, bool EV = true>
+__global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
+    k_tersoff(const __grid_constant__ FwdArgs<T> a) {
   static_assert(!(CS && BATCH), "compensated per-atom sums: single systems only");
+  static_assert(EV || !BATCH, "batches need the per-atom energy and virial");
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
   __shared__ T srec_s[SREC];
@@ -903,7 +908,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             if (rr[qj] < p2[K_ROUT2]) {
               T V, dVdr, dz;
               pair_fc<T>(p2, rr[qj], zeta[qj], fc3[qj], dfc3[qj], V, dVdr, dz);
-              eatom_c.add(V);
+              if (EV) eatom_c.add(V);
               dzt[qj] = dz;
               fx[qj].add(-dVdr * ux[qj]);
               fy[qj].add(-dVdr * uy[qj]);
@@ -968,7 +973,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             }
             T V, dVdr, dz;
             pair<T>(p2, rij, zeta, V, dVdr, dz, rex[qj]);
-            eatom_c.add(V);
+            if (EV) eatom_c.add(V);
             fx[qj].add(-(dVdr * ux[qj] + dz * gjx));
             fy[qj].add(-(dVdr * uy[qj] + dz * gjy));
             fz[qj].add(-(dVdr * uz[qj] + dz * gjz));
@@ -1005,7 +1010,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
             wa[3].add(dx * fy[q].s + dx * fy[q].lo());
             wa[4].add(dx * fz[q].s + dx * fz[q].lo());
             wa[5].add(dy * fz[q].s + dy * fz[q].lo());
-          } else {
+          } else if (EV) {
             w[0] += dx * fx[q].s;
             w[1] += dy * fy[q].s;
             w[2] += dz * fz[q].s;
@@ -1053,6 +1058,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
       }
       continue;
     }
+    if (!EV) continue;
     eatom_i += eatom_c.s;
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     if (want_acc) {
@@ -1062,7 +1068,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? 7 : 4)) k_tersoff(const __gr
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (want_acc && __syncthreads_or(any)) {
+  if (EV && want_acc && __syncthreads_or(any)) {
     double wd[6];
     for (int q = 0; q < 6; ++q) wd[q] = tsum[1 + q][threadIdx.x];
     block_reduce_store_d(tsum[0][threadIdx.x], wd, a.acc);

@@ -39,3 +39,21 @@ def allreduce_sum(*tensors):
     for t in tensors:
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return tensors
+
+
+def shard_cells(sizes, world: int, rank: int, neighbours=4.0):
+    """Indices of the systems that ``rank`` evaluates: the rank's part of the
+    cost-balanced partition of all systems (every rank computes the same
+    partition from the same sizes, so no exchange is needed to agree on it)."""
+    return partition(system_cost(sizes, neighbours), world)[rank]
+
+
+def fit_step(local_step):
+    """One data-parallel fitting step: ``local_step()`` evaluates this rank's
+    systems and returns (loss, grad) as tensors (the loss of its systems and
+    its gradient with respect to the parameter table); both are then summed
+    over ranks in place, giving every rank the loss and gradient of the whole
+    batch."""
+    loss, grad = local_step()
+    allreduce_sum(grad, loss)
+    return loss, grad

@@ -90,3 +90,68 @@ def test_gradient_allreduce_two_ranks():
         g, loss = out[rank]
         assert g == [3.0 * k for k in range(8)]
         assert loss == 30.0
+
+
+# One data-parallel fitting step over a batch of independent cells: each rank
+# evaluates its cost-balanced share of the cells (here with the oracle as the
+# evaluation: energies and their complex-step parameter derivatives) and the
+# loss and table gradient are summed over ranks. Every rank must end with the
+# loss and gradient of the whole batch computed in one process.
+FIT_BATCH = dict(n_cells=5, nmin=40, nmax=90, seed_k=11)
+
+
+def _oracle_loss_grad(cells):
+    import numpy as np
+    import oracle
+    from tests import _systems as S
+    table = S.table_for(["Si", "C"], oracle.mix_tersoff89)
+    target = table * (1.0 + 0.01 * np.sin(np.arange(table.size)))  # a perturbed table
+    loss = torch.zeros(1, dtype=torch.float64)
+    grad = torch.zeros(table.size, dtype=torch.float64)
+    for x, t, box in cells:
+        nl = oracle.neighbors(x, box, 3.0)
+        e, _, _ = oracle.compute(x, t, box, table, nl)
+        e0, _, _ = oracle.compute(x, t, box, target, nl)
+        loss += (e - e0) ** 2
+        for p in range(table.size):
+            if p % 14 == 0:
+                continue
+            de, _ = oracle.cs_param(x, t, box, table, nl, p)
+            grad[p] += 2.0 * (e - e0) * de
+    return loss, grad
+
+
+def _fit_worker(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import workloads as W
+    from paper_1607_02904_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        sizes, _ = W.batched_cell_sizes(FIT_BATCH["n_cells"], FIT_BATCH["nmin"],
+                                        FIT_BATCH["nmax"], FIT_BATCH["seed_k"])
+        mine = shard.shard_cells(sizes, world, rank)
+        cells = W.batched_cells(**FIT_BATCH, subset=mine)
+        loss, grad = shard.fit_step(lambda: _oracle_loss_grad(cells))
+        out[rank] = (list(mine), loss.item(), grad.tolist())
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_fit_step_equals_whole_batch():
+    import numpy as np
+    import workloads as W
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_fit_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    loss_ref, grad_ref = _oracle_loss_grad(W.batched_cells(**FIT_BATCH))
+    parts = [out[r][0] for r in range(world)]
+    assert sorted(i for p in parts for i in p) == list(range(FIT_BATCH["n_cells"]))
+    assert all(len(p) > 0 for p in parts)
+    for r in range(world):
+        _, loss, grad = out[r]
+        assert abs(loss - loss_ref.item()) <= 1e-12 * abs(loss_ref.item())
+        g = np.asarray(grad)
+        assert np.abs(g - grad_ref.numpy()).max() <= 1e-12 * np.abs(grad_ref.numpy()).max()

@@ -21,6 +21,7 @@ from .synth import (  # noqa: F401
     maxwell_velocities,
     random_packing,
     batched_cells,
+    batched_cell_sizes,
     element_records,
     config_si_small,
     config_si_md,

@@ -147,20 +147,30 @@ def _batched_cell(args):
         k += 1
 
 
+def batched_cell_sizes(n_cells: int = 256, nmin: int = 64, nmax: int = 4096, seed_k: int = 4):
+    """Atom counts and C fractions of the batched workload's cells (the draws
+    that precede the packings), without generating the packings."""
+    rng = rng_for(seed_k)
+    sizes = rng.integers(nmin, nmax + 1, size=n_cells)
+    fracs = rng.random(n_cells)
+    return sizes, fracs
+
+
 def batched_cells(n_cells: int = 256, nmin: int = 64, nmax: int = 4096,
                   density_gcc: float = 2.3, min_sep: float = 1.8, seed_k: int = 4,
-                  map_fn=map):
+                  map_fn=map, subset=None):
     """Independent periodic Si/C cells of uneven size for the batched workload.
 
     Atom counts ~ U{nmin..nmax}, C fraction ~ U(0,1) per cell; each cell is a
     random packing at ``density_gcc`` with minimum separation ``min_sep``. A
     cell whose packing runs out of attempts is drawn again from the next seed.
-    Every cell has its own generator, so ``map_fn`` may be a process pool's map.
+    Every cell has its own generator, so ``map_fn`` may be a process pool's map
+    and ``subset`` (cell indices) generates only those cells, identical to
+    their counterparts in the whole batch.
     """
-    rng = rng_for(seed_k)
-    sizes = rng.integers(nmin, nmax + 1, size=n_cells)
-    fracs = rng.random(n_cells)
-    jobs = [(c, sizes[c], fracs[c], density_gcc, min_sep, seed_k) for c in range(n_cells)]
+    sizes, fracs = batched_cell_sizes(n_cells, nmin, nmax, seed_k)
+    cells = range(n_cells) if subset is None else subset
+    jobs = [(c, sizes[c], fracs[c], density_gcc, min_sep, seed_k) for c in cells]
     return list(map_fn(_batched_cell, jobs))
 
 
