@@ -112,6 +112,7 @@ def apply_options(ctx, T, opt):
     ctx.set_scatter(T.SCATTER_ATOMIC if opt["scatter"] == "atomic" else T.SCATTER_GATHER)
     split = {"auto": -1, "off": 0, "on": 1}[opt["split"]]
     ctx.set_launch(int(opt["waves"]), split, int(opt["block"]))
+    ctx.set_lanes({"auto": 0, "1": 1, "4": 4}[opt.get("lanes", "auto")])
 
 
 def base_config(n, world):

@@ -254,6 +254,7 @@ int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int 
  *   - the force scatter (tersoff_set_scatter);
  *   - the separate register-capacity-8 launch on a side stream
  *     (automatic / never / whenever needed);
+ *   - the lanes per atom of the main force launch (tersoff_set_lanes);
  *   - the force kernel's grid: one thread per atom, or 1, 2 or 4 waves of
  *     the blocks resident on all multiprocessors looping over the atoms;
  *   - the block size of the pack, integrate and gather kernels (128/256/512).
@@ -278,6 +279,17 @@ int tersoff_autotune(tersoff_ctx* ctx, const double* x, const double* v, int n,
  * non-empty) and block (pack / integrate / gather block size, a power of two
  * in [64, 512]). Results do not depend on them beyond rounding order. */
 int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
+
+/* Lanes per centre atom in the main force launch (mixed path, one or two
+ * species, single systems; the FP64 path and batches always use one thread
+ * per atom): 4 = one lane per bond, four lanes per atom, the neighbourhood
+ * shared by warp shuffles (the paper's scheme (a) of Sec. IV-B, bonds on
+ * vector lanes), atoms with more than four bonds inside the cutoffs finished
+ * by a per-thread launch; 1 = one thread per atom with the bonds in registers
+ * (scheme (c)); 0 (the default) = 4 when at most 1% of the atoms had more than
+ * four bonds inside the cutoffs at the last build, else 1. Results agree to
+ * rounding order; tersoff_autotune also chooses this option. */
+int tersoff_set_lanes(tersoff_ctx* ctx, int lanes);
 
 /* Ablations of the paper's design choices, for measurement (results are
  * unchanged up to rounding order; the default is 0):

@@ -61,6 +61,7 @@ _SIG = {
     "tersoff_autotune": ([_P, _P, _P, _I, _P, _D, _I, _P], _I),
     "tersoff_autotune_summary": ([_P], ctypes.c_char_p),
     "tersoff_set_launch": ([_P, _I, _I, _I], _I),
+    "tersoff_set_lanes": ([_P, _I], _I),
     "tersoff_set_ablation": ([_P, _I], _I),
     "tersoff_set_timing": ([_P, _I], _I),
     "tersoff_set_graphs": ([_P, _I], _I),
@@ -281,6 +282,10 @@ class Context:
 
     def set_launch(self, waves=0, split=-1, block=256):
         self._check(self.lib.tersoff_set_launch(self.h, int(waves), int(split), int(block)))
+
+    def set_lanes(self, lanes=0):
+        """Lanes per atom of the main force launch: 0 automatic, 1 or 4."""
+        self._check(self.lib.tersoff_set_lanes(self.h, int(lanes)))
 
     def set_ablation(self, flags):
         """ABLATE_NO_SHORT | ABLATE_GENERAL | ABLATE_FP32_SUMS | ABLATE_FASTFWD |

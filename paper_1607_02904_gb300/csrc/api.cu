@@ -132,6 +132,7 @@ int ensure_atoms(Ctx* c, int n) {
   if ((st = dev_alloc(c, &c->d_qref, m))) return st;
   if ((st = dev_alloc(c, &c->d_zcnt, m))) return st;
   if ((st = dev_alloc(c, &c->d_bucket, 3 * m))) return st;
+  if ((st = dev_alloc(c, &c->d_left, m))) return st;
   if ((st = dev_alloc(c, &c->d_extra, 3 * (m ? m : 1)))) return st;
   TGB_CUDA(c, cudaMemset(c->d_extra, 0, sizeof(double) * 3 * (m ? m : 1)));
   c->atoms_alloc = m;
@@ -309,7 +310,7 @@ int tersoff_destroy(tersoff_ctx* p) {
                   c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_kmask, c->d_zw, c->d_fine, c->d_zbins, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
-                  c->d_bucket, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
+                  c->d_bucket, c->d_left, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
                   c->d_extra, c->d_geo, c->d_sys, c->d_atom_sys, c->d_sys_off, c->d_vatom,
                   c->d_eatom, c->d_gf32};
   for (void* b : bufs)
@@ -1095,7 +1096,7 @@ int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
 // ---------------------------------------------------------------- autotuner
 namespace {
 struct TuneOpt {
-  int atomic, split, waves, block;
+  int atomic, split, waves, block, quad;
 };
 
 void apply_opt(Ctx* c, const TuneOpt& o) {
@@ -1103,14 +1104,16 @@ void apply_opt(Ctx* c, const TuneOpt& o) {
   c->opt_split = o.split;
   c->opt_waves = o.waves;
   c->opt_block = o.block;
+  c->opt_quad = o.quad;
   c->gen++;  // captured MD graphs hold the old launch shapes
 }
 
 std::string opt_text(const TuneOpt& o) {
-  char b[128];
-  std::snprintf(b, sizeof(b), "scatter=%s split=%s waves=%d block=%d",
+  char b[160];
+  std::snprintf(b, sizeof(b), "scatter=%s split=%s waves=%d block=%d lanes=%s",
                 o.atomic ? "atomic" : "gather",
-                o.split < 0 ? "auto" : (o.split ? "on" : "off"), o.waves, o.block);
+                o.split < 0 ? "auto" : (o.split ? "on" : "off"), o.waves, o.block,
+                o.quad < 0 ? "auto" : (o.quad ? "4" : "1"));
   return b;
 }
 }  // namespace
@@ -1167,7 +1170,8 @@ int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, co
     *ms_out = t[t.size() / 2];
     return TERSOFF_OK;
   };
-  const TuneOpt start{c->scatter_atomic ? 1 : 0, c->opt_split, c->opt_waves, c->opt_block};
+  const TuneOpt start{c->scatter_atomic ? 1 : 0, c->opt_split, c->opt_waves, c->opt_block,
+                      c->opt_quad};
   TuneOpt best = start;
   double best_ms = 0.0;
   std::string log;
@@ -1176,13 +1180,16 @@ int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, co
     log = opt_text(best) + ": " + std::to_string(best_ms) + " ms";
     // coordinate descent: one option at a time, the others at their best
     const std::vector<std::vector<int>> values = {
-        {0, 1}, {-1, 0, 1}, {0, 1, 2, 4}, {128, 256, 512}};
-    for (int k = 0; k < 4 && !st; ++k)
+        {0, 1, -1}, {0, 1}, {-1, 0, 1}, {0, 1, 2, 4}, {128, 256, 512}};
+    for (int k = 0; k < 5 && !st; ++k)
       for (int val : values[k]) {
         TuneOpt o = best;
-        int* field = k == 0 ? &o.atomic : k == 1 ? &o.split : k == 2 ? &o.waves : &o.block;
+        int* field = k == 0 ? &o.quad : k == 1 ? &o.atomic : k == 2 ? &o.split
+                   : k == 3 ? &o.waves : &o.block;
         if (*field == val) continue;
-        if (k == 1 && c->n_sys > 0) continue;  // batches run one launch
+        if ((k == 0 || k == 2) && c->n_sys > 0) continue;  // batches run one launch
+        if (k == 0 && (c->precision != TERSOFF_MIXED || c->ns > 2)) continue;
+        if (k == 2 && best.quad == 1) continue;  // the four-lane launch has no split
         *field = val;
         double ms = 0.0;
         if ((st = trial(o, &ms, 5))) break;
@@ -1196,7 +1203,8 @@ int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, co
     // each; the winner replaces them only when at least 1% faster (the
     // trials' spread is of that order, so a narrower win is noise)
     const bool same = best.atomic == start.atomic && best.split == start.split &&
-                      best.waves == start.waves && best.block == start.block;
+                      best.waves == start.waves && best.block == start.block &&
+                      best.quad == start.quad;
     if (!st && !same) {
       double ms_s = 0.0, ms_b = 0.0;
       if (!(st = trial(start, &ms_s, 9)) && !(st = trial(best, &ms_b, 9))) {
@@ -1232,7 +1240,18 @@ int tersoff_set_launch(tersoff_ctx* p, int waves, int split, int block) {
       !(block == 64 || block == 128 || block == 256 || block == 512))
     return tgb::fail(c, TERSOFF_E_INVALID_ARG,
                      "waves in [0, 64], split in {-1, 0, 1}, block a power of two in [64, 512]");
-  TuneOpt o{c->scatter_atomic ? 1 : 0, split, waves, block};
+  TuneOpt o{c->scatter_atomic ? 1 : 0, split, waves, block, c->opt_quad};
+  apply_opt(c, o);
+  return TERSOFF_OK;
+}
+
+int tersoff_set_lanes(tersoff_ctx* p, int lanes) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (!(lanes == 0 || lanes == 1 || lanes == 4))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "lanes is 0 (automatic), 1 or 4");
+  TuneOpt o{c->scatter_atomic ? 1 : 0, c->opt_split, c->opt_waves, c->opt_block,
+            lanes == 0 ? -1 : (lanes == 4 ? 1 : 0)};
   apply_opt(c, o);
   return TERSOFF_OK;
 }

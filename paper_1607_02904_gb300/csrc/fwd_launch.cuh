@@ -85,8 +85,38 @@ inline int force_grid(const Ctx* c, int zc) {
   return g < full ? g : full;
 }
 
+// The four-lane kernel takes the main launch when the context allows it
+// (launch option opt_quad; automatic: mixed path, one or two species, a
+// single system, and at most 1% of the atoms with more than four bonds
+// inside the cutoffs at the last build).
+template <class T, int NS, bool BATCH>
+bool use_quad(const Ctx* c) {
+  if (BATCH || sizeof(T) != 4 || NS < 1 || NS > 2 || comp_atom_sums(c) || c->n == 0) return false;
+  if (c->opt_quad >= 0) return c->opt_quad == 1;
+  return (long long)(c->nbucket[1] + c->nbucket[2]) * 100 <= (long long)c->n;
+}
+
 template <class T, int NS, bool BATCH = false>
 void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
+  if (use_quad<T, NS, BATCH>(c)) {
+    TimedRegion tr(c, 0, s);
+    const bool ev = a.acc != nullptr || a.eatom != nullptr;
+    FwdArgs<T> aq = a;
+    aq.identity = 1;
+    launch_forward_quad(c, &aq, ev, s);
+    // the atoms it left (more than four bonds inside the cutoffs, general
+    // path): the per-thread kernel over the leftover list, one block per SM
+    // looping over it; its last block zeroes the list's count
+    FwdArgs<T> bl = a;
+    bl.order = c->d_left;
+    bl.n_items = c->d_flags + FLAG_LEFT;
+    bl.order2 = bl.order3 = nullptr;
+    bl.n_items2 = bl.n_items3 = nullptr;
+    bl.identity = 0;
+    bl.left_reset = 1;
+    launch_t<T, NS, 8, BATCH>(c, bl, c->n_sm > 0 ? c->n_sm : 152, s);
+    return;
+  }
   const bool split1 = c->opt_split < 0 ? (long long)c->nbucket[1] * 20 > (long long)c->n
                                        : (c->opt_split > 0 && c->nbucket[1] > 0);
   const bool fork = split1 && c->side != nullptr;
@@ -173,6 +203,8 @@ FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
   a.order2 = a.order3 = nullptr;
   a.n_items2 = a.n_items3 = nullptr;
   a.identity = 1;
+  a.left = c->d_left;
+  a.left_reset = 0;
   return a;
 }
 

@@ -151,6 +151,7 @@ struct Ctx {
   uint32_t* d_short = nullptr;    // zs_cap * n, slot-major short list
   int* d_zcnt = nullptr;          // n
   int* d_bucket = nullptr;        // 3 x n: atom indices per bucket (entries inside the cutoffs)
+  int* d_left = nullptr;          // n: atoms the four-lane force kernel leaves to the per-thread one
   uint8_t* d_rev = nullptr;       // zs_cap x n: slot of j in the short list of its p-th neighbour
   void* d_contrib = nullptr;      // zs_cap x n force contributions (float4 or dpos4)
   void* d_own = nullptr;          // n: force of each atom's own terms on itself
@@ -187,6 +188,9 @@ struct Ctx {
                        // blocks resident on all SMs (the kernel loops over items)
   int opt_split = -1;  // capacity-8 side-stream launch: -1 automatic, 0 never, 1 when non-empty
   int opt_block = 256; // block size of the per-atom pack / integrate / gather kernels
+  int opt_quad = -1;   // four lanes per atom in the main force launch: -1 automatic (mixed
+                       // path, single system, at most 1% of atoms with more than 4 bonds
+                       // inside the cutoffs at the build), 0 never, 1 always
   int n_sm = 0;        // multiprocessors of the device
   int ablate = 0;      // tersoff_set_ablation flags
   std::string tune_summary;  // last tersoff_autotune: choice and trial times
@@ -270,6 +274,9 @@ enum : int {
   FLAG_EXTRA = 11 * FLAG_STRIDE,        // last force evaluation scattered through atomics
   FLAG_NREBUILD = 12 * FLAG_STRIDE,     // displacement-triggered rebuilds in this MD call
   FLAG_EXTRA_STICKY = 13 * FLAG_STRIDE, // some evaluation since the call began did
+  FLAG_LEFT = 14 * FLAG_STRIDE,         // atoms the four-lane force kernel left to the
+                                        // per-thread kernel (0 between evaluations)
+  FLAG_LEFT_TICKET = 15 * FLAG_STRIDE,  // blocks of that per-thread launch done (0 between)
   FLAG_COUNT = 16 * FLAG_STRIDE
 };
 __host__ __device__ constexpr int flag_bucket(int b) { return FLAG_BUCKET + b * FLAG_STRIDE; }
@@ -313,6 +320,10 @@ int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream
 // the force launches of the TERSOFF_ABLATE_COMP_ATOM_SUMS variant (fwd_f32_cs.cu),
 // register capacity 4 or 8; args is a fwd::FwdArgs<float>
 int launch_forward_cs(Ctx* c, const void* args, int zc, int grid, cudaStream_t s);
+// the four-lane force kernel (fwd_f32_quad.cu; mixed path, one or two species,
+// single systems) over all atoms; args is a fwd::FwdArgs<float> with
+// identity set; ev: energy, virial or per-atom energy wanted
+int launch_forward_quad(Ctx* c, const void* args, bool ev, cudaStream_t s);
 // Batch of systems: forces (slots or atomics into f, as launch_forward),
 // per-atom energy d_eatom and virial d_vatom.
 int launch_forward_batch(Ctx* c, double* f, cudaStream_t s);

@@ -176,6 +176,9 @@ template <class T> struct FwdArgs {
   const SysShift* sys;   // per system: periodic shift units
   const int* atom_sys;   // system of each atom
   double* vatom;         // per-atom virial (6), summed per system afterwards
+  int* left;             // four-lane kernel: atoms left to the per-thread kernel
+  int left_reset;        // per-thread kernel over that list: the last block zeroes the
+                         // list's count (FLAG_LEFT) and its own ticket
 };
 
 // position of atom j relative to its origin, in T, and its species
@@ -702,7 +705,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
   constexpr bool LAM3 = MODE == 1;
   const int n_first = uni[0];
   const int n_second = uni[0] + uni[3];
-  const int n_items = a.identity ? a.n : n_second + uni[4];
+  const int n_items = a.identity ? a.n : min(n_second + uni[4], a.n);
   // slots: contributions go to per-slot stores (needs the stored short list and
   // its reverse map); otherwise FP64 atomics into the fallback buffer
   const bool slots_ok = uni[1] == 0;
@@ -1072,6 +1075,14 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
     double wd[6];
     for (int q = 0; q < 6; ++q) wd[q] = tsum[1 + q][threadIdx.x];
     block_reduce_store_d(tsum[0][threadIdx.x], wd, a.acc);
+  }
+  if (a.left_reset) {
+    // every block read the leftover count (uni[0]) before taking its ticket
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&a.flags[FLAG_LEFT_TICKET], 1) == (int)gridDim.x - 1) {
+      a.flags[FLAG_LEFT] = 0;
+      a.flags[FLAG_LEFT_TICKET] = 0;
+    }
   }
 }
 
