@@ -176,6 +176,14 @@ __global__ void __launch_bounds__(QBLOCK) k_tersoff_quad(const __grid_constant__
     }
     const bool act = have && !left;   // the group computes this atom
     const bool mine = act && sl >= 0;  // this lane holds a bond
+    // forces through the fallback buffer while the gather still runs: the
+    // gather must see zero in the atom's own slot and in its column (the
+    // lanes take the slots q, q + 4, ...)
+    if (act && !slots && !a.atomic_mode) {
+      if (q == 0) store_slot<T>(a, a.own, (size_t)i, T(0), T(0), T(0));
+      const int zc = min(zl, a.zs_cap);
+      for (int p = q; p < zc; p += 4) store_slot<T>(a, a.contrib, (size_t)p * a.n + i, T(0), T(0), T(0));
+    }
     // 1. the lane's bond
     T ux = 0, uy = 0, uz = 0, r = 1, ri = 1, rx = 0, fc = 0, dfc = 0;
     int j = i, tj = 0, rv = 0;

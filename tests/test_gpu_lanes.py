@@ -141,6 +141,36 @@ def test_four_lanes_moved_beyond_half_margin(T, case):
         check((e, f, w), ref)
 
 
+def test_four_lanes_slots_then_fallback_on_one_context(T):
+    # the same context evaluates first at the build positions (per-slot force
+    # stores and the gather), then at positions moved beyond half the margin
+    # (FP64 atomics into the fallback buffer while the gather still runs): the
+    # slots written by the first evaluation must not leak into the second
+    _, x, t, box, table = CASES[0]
+    rng = np.random.Generator(np.random.Philox(206))
+    d = rng.normal(size=x.shape)
+    d *= 0.35 / np.linalg.norm(d, axis=1).max()
+    ctx = T.Context(T.MIXED)
+    ctx.set_lanes(4)
+    ctx.params(table)
+    xd = dev(x)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+    f = torch.zeros_like(xd)
+    ctx.compute(xd, None, f)
+    torch.cuda.synchronize()
+    _, fr0, _ = oracle.compute(x, t, box, table, oracle.neighbors(x, box, RC))
+    f0 = f.cpu().numpy()
+    assert np.sqrt(((f0 - fr0) ** 2).mean()) / np.sqrt((fr0 ** 2).mean()) <= TOL
+    xm = x + d
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    w = torch.zeros(6, dtype=torch.float64, device="cuda")
+    ctx.compute(dev(xm), e, f, w)
+    torch.cuda.synchronize()
+    ref = oracle.compute(xm, t, box, table, oracle.neighbors(xm, box, RC))
+    check((e.item(), f.cpu().numpy(), w.cpu().numpy()), ref)
+    ctx.close()
+
+
 def test_four_lanes_md_against_oracle(T):
     # MD with the four-lane kernel in the graph (rebuild every 10 steps): the
     # forces after 30 steps against the oracle's trajectory, to the mixed
