@@ -286,9 +286,9 @@ int tersoff_set_launch(tersoff_ctx* ctx, int waves, int split, int block);
  * shared by warp shuffles (the paper's scheme (a) of Sec. IV-B, bonds on
  * vector lanes), atoms with more than four bonds inside the cutoffs finished
  * by a per-thread launch; 1 = one thread per atom with the bonds in registers
- * (scheme (c)); 0 (the default) = 4 when at most 1% of the atoms had more than
- * four bonds inside the cutoffs at the last build, else 1. Results agree to
- * rounding order; tersoff_autotune also chooses this option. */
+ * (scheme (c)); 0 (the default) = automatic, which is 1 (measured faster on the
+ * Si benchmark). Results agree to rounding order; tersoff_autotune also tries
+ * 4 and keeps it when it is faster. */
 int tersoff_set_lanes(tersoff_ctx* ctx, int lanes);
 
 /* Ablations of the paper's design choices, for measurement (results are

@@ -85,15 +85,15 @@ inline int force_grid(const Ctx* c, int zc) {
   return g < full ? g : full;
 }
 
-// The four-lane kernel takes the main launch when the context allows it
-// (launch option opt_quad; automatic: mixed path, one or two species, a
-// single system, and at most 1% of the atoms with more than four bonds
-// inside the cutoffs at the last build).
+// The four-lane kernel takes the main launch when the launch option asks for
+// it (tersoff_set_lanes(4), or the autotuner's choice) and the context is
+// eligible (mixed path, one or two species, a single system). Automatic
+// means one thread per atom: on the 512,000-atom Si benchmark the four-lane
+// launch executes 43% more instructions at a 21% higher IPC and is slower.
 template <class T, int NS, bool BATCH>
 bool use_quad(const Ctx* c) {
   if (BATCH || sizeof(T) != 4 || NS < 1 || NS > 2 || comp_atom_sums(c) || c->n == 0) return false;
-  if (c->opt_quad >= 0) return c->opt_quad == 1;
-  return (long long)(c->nbucket[1] + c->nbucket[2]) * 100 <= (long long)c->n;
+  return c->opt_quad == 1;
 }
 
 template <class T, int NS, bool BATCH = false>

@@ -188,9 +188,9 @@ struct Ctx {
                        // blocks resident on all SMs (the kernel loops over items)
   int opt_split = -1;  // capacity-8 side-stream launch: -1 automatic, 0 never, 1 when non-empty
   int opt_block = 256; // block size of the per-atom pack / integrate / gather kernels
-  int opt_quad = -1;   // four lanes per atom in the main force launch: -1 automatic (mixed
-                       // path, single system, at most 1% of atoms with more than 4 bonds
-                       // inside the cutoffs at the build), 0 never, 1 always
+  int opt_quad = -1;   // four lanes per atom in the main force launch: 1 when eligible
+                       // (mixed path, one or two species, a single system), 0 or -1
+                       // (automatic: measured slower on the benchmark) one thread per atom
   int n_sm = 0;        // multiprocessors of the device
   int ablate = 0;      // tersoff_set_ablation flags
   std::string tune_summary;  // last tersoff_autotune: choice and trial times
