@@ -1180,13 +1180,14 @@ int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, co
     log = opt_text(best) + ": " + std::to_string(best_ms) + " ms";
     // coordinate descent: one option at a time, the others at their best
     const std::vector<std::vector<int>> values = {
-        {0, 1, -1}, {0, 1}, {-1, 0, 1}, {0, 1, 2, 4}, {128, 256, 512}};
+        {1, 0}, {0, 1}, {-1, 0, 1}, {0, 1, 2, 4}, {128, 256, 512}};
     for (int k = 0; k < 5 && !st; ++k)
       for (int val : values[k]) {
         TuneOpt o = best;
         int* field = k == 0 ? &o.quad : k == 1 ? &o.atomic : k == 2 ? &o.split
                    : k == 3 ? &o.waves : &o.block;
         if (*field == val) continue;
+        if (k == 0 && val == 0 && *field < 0) continue;  // automatic is one lane per atom
         if ((k == 0 || k == 2) && c->n_sys > 0) continue;  // batches run one launch
         if (k == 0 && (c->precision != TERSOFF_MIXED || c->ns > 2)) continue;
         if (k == 2 && best.quad == 1) continue;  // the four-lane launch has no split
