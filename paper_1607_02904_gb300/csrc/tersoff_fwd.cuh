@@ -52,6 +52,9 @@ __device__ __forceinline__ double to_f64(float v) { return f2d_bits(v); }
 __device__ __forceinline__ double to_f64(double v) { return v; }
 
 // ---------------------------------------------------------------- math per precision
+__device__ __forceinline__ float fmaf_t(float x, float y, float z) { return fmaf(x, y, z); }
+__device__ __forceinline__ double fmaf_t(double x, double y, double z) { return fma(x, y, z); }
+
 template <class T> struct M;
 
 template <> struct M<float> {
@@ -644,6 +647,8 @@ __device__ __forceinline__ void block_reduce_store_d(double ei, const double* w,
 template <class T, bool CS> struct Acc {
   T s = T(0);
   __device__ __forceinline__ void add(T x) { s += x; }
+  // s += c t + b u, as two fused multiply-adds
+  __device__ __forceinline__ void madd2(T c, T t, T b, T u) { s = fmaf_t(c, t, fmaf_t(b, u, s)); }
   __device__ __forceinline__ void sub(const Acc& o) { s -= o.s; }
   __device__ __forceinline__ T lo() const { return T(0); }
   __device__ __forceinline__ double d() const { return to_f64(s); }
@@ -656,6 +661,7 @@ template <class T> struct Acc<T, true> {
     e += (s - (t - bp)) + (x - bp);
     s = t;
   }
+  __device__ __forceinline__ void madd2(T c, T t, T b, T u) { add(fmaf_t(c, t, b * u)); }
   __device__ __forceinline__ void sub(const Acc& o) {
     add(-o.s);
     e -= o.e;
@@ -892,17 +898,18 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
 #pragma unroll
         for (int qj = 0; qj < ZC; ++qj)
 #pragma unroll
-          for (int qk = qj + 1; qk < ZC; ++qk)
-            if (qk < z) {
-              const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
-              const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
-              const T t = p3[K_H] - cs;
-              const T t2 = t * t;
-              const T q = M<T>::rcp_nr(p3[K_D2] + t2);
-              const T g = p3[K_GC2D2] * (t2 * q) + p3[K_GAMMA];
-              zeta[qj] += fc3[qk] * g;
-              zeta[qk] += fc3[qj] * g;
-            }
+          for (int qk = qj + 1; qk < ZC; ++qk) {
+            // (the test keeps the compiler from interleaving all six pairs:
+            // without it the kernel spills)
+            if (qk >= z) continue;
+            const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
+            const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
+            const T t = p3[K_H] - cs;
+            const T tq = t * M<T>::rcp_nr(p3[K_D2] + t * t);
+            const T g = p3[K_GC2D2] * (t * tq) + p3[K_GAMMA];
+            zeta[qj] += fc3[qk] * g;
+            zeta[qk] += fc3[qj] * g;
+          }
         // pair terms, b_ij and dV/dzeta
 #pragma unroll
         for (int qj = 0; qj < ZC; ++qj)
@@ -918,30 +925,33 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
               fz[qj].add(-dVdr * uz[qj]);
             }
           }
-        // pass 2: -dV/dzeta_ij d zeta_ij/dx - dV/dzeta_ik d zeta_ik/dx per pair {j,k}
+        // pass 2: -dV/dzeta_ij d zeta_ij/dx - dV/dzeta_ik d zeta_ik/dx per pair
+        // {j,k}; with q = 1/(d^2 + t^2): g = gamma + gamma c^2/d^2 t^2 q and
+        // dg/dcos = -2 gamma c^2 t q^2
 #pragma unroll
         for (int qj = 0; qj < ZC; ++qj)
 #pragma unroll
-          for (int qk = qj + 1; qk < ZC; ++qk)
-            if (qk < z) {
-              const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
-              const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
-              const T t = p3[K_H] - cs;
-              const T t2 = t * t;
-              const T q = M<T>::rcp_nr(p3[K_D2] + t2);
-              const T g = p3[K_GC2D2] * (t2 * q) + p3[K_GAMMA];
-              const T dg = -p3[K_G2C2] * t * q * q;
-              const T A = -(dzt[qj] * fc3[qk] + dzt[qk] * fc3[qj]) * dg;
-              const T cj = A * ri[qj], ck = A * ri[qk];
-              const T bj = -dzt[qk] * dfc3[qj] * g;
-              const T bk = -dzt[qj] * dfc3[qk] * g;
-              fx[qj].add(cj * (ux[qk] - cs * ux[qj]) + bj * ux[qj]);
-              fy[qj].add(cj * (uy[qk] - cs * uy[qj]) + bj * uy[qj]);
-              fz[qj].add(cj * (uz[qk] - cs * uz[qj]) + bj * uz[qj]);
-              fx[qk].add(ck * (ux[qj] - cs * ux[qk]) + bk * ux[qk]);
-              fy[qk].add(ck * (uy[qj] - cs * uy[qk]) + bk * uy[qk]);
-              fz[qk].add(ck * (uz[qj] - cs * uz[qk]) + bk * uz[qk]);
-            }
+          for (int qk = qj + 1; qk < ZC; ++qk) {
+            if (qk >= z) continue;
+            const T* p3 = srec + rec_off<NS>(ns, ti, tt[qj], tt[qk]);
+            const T cs = ux[qj] * ux[qk] + uy[qj] * uy[qk] + uz[qj] * uz[qk];
+            const T t = p3[K_H] - cs;
+            const T q = M<T>::rcp_nr(p3[K_D2] + t * t);
+            const T tq = t * q;
+            const T g = p3[K_GC2D2] * (t * tq) + p3[K_GAMMA];
+            const T dg = (-p3[K_G2C2] * q) * tq;
+            const T A = -(dzt[qj] * fc3[qk] + dzt[qk] * fc3[qj]) * dg;
+            const T cj = A * ri[qj], ck = A * ri[qk];
+            const T bj = -dzt[qk] * dfc3[qj] * g;
+            const T bk = -dzt[qj] * dfc3[qk] * g;
+            // F += c (u_k - cos u_j) + b u_j
+            fx[qj].madd2(cj, fmaf_t(-cs, ux[qj], ux[qk]), bj, ux[qj]);
+            fy[qj].madd2(cj, fmaf_t(-cs, uy[qj], uy[qk]), bj, uy[qj]);
+            fz[qj].madd2(cj, fmaf_t(-cs, uz[qj], uz[qk]), bj, uz[qj]);
+            fx[qk].madd2(ck, fmaf_t(-cs, ux[qk], ux[qj]), bk, ux[qk]);
+            fy[qk].madd2(ck, fmaf_t(-cs, uy[qk], uy[qj]), bk, uy[qk]);
+            fz[qk].madd2(ck, fmaf_t(-cs, uz[qk], uz[qj]), bk, uz[qk]);
+          }
       } else
 #pragma unroll
       for (int qj = 0; qj < ZC; ++qj) {

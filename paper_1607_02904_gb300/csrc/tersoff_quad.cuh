@@ -38,9 +38,6 @@ __device__ __forceinline__ T qsh(T v, int src) {
   return __shfl_sync(0xffffffffu, v, src);
 }
 
-__device__ __forceinline__ float fmaf_t(float x, float y, float z) { return fmaf(x, y, z); }
-__device__ __forceinline__ double fmaf_t(double x, double y, double z) { return fma(x, y, z); }
-
 // Sum over the four lanes of a group.
 template <class T>
 __device__ __forceinline__ T qsum(T v) {
