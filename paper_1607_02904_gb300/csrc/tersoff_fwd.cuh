@@ -595,12 +595,11 @@ __device__ __forceinline__ void clear_slots(const FwdArgs<T>& a, int i) {
 }
 
 // ---------------------------------------------------------------- reduction
-// Energy and virial: the 7 per-thread sums in double (padded to 8) are
-// reduce-scattered across the warp in double (halving
-// exchanges: 4, 2, 1 values), then summed over the remaining lanes; lanes 0,
-// 4, ..., 28 end with the 8 warp totals. Warp totals are summed in double over
-// the block and added to acc with one atomic each. Every sum across atoms is
-// thus in double.
+// Energy and virial of the double path: the 7 per-thread sums (padded to 8)
+// are reduce-scattered across the warp (halving exchanges: 4, 2, 1 values),
+// then summed over the remaining lanes; lanes 0, 4, ..., 28 end with the 8
+// warp totals. Warp totals are summed in double over the block and added to
+// acc with one atomic each.
 template <int NB = BLOCK>
 __device__ __forceinline__ void block_reduce_store_d(double ei, const double* w, double* acc) {
   __shared__ double part[NB / 32][8];
@@ -638,6 +637,89 @@ __device__ __forceinline__ void block_reduce_store_d(double ei, const double* w,
     for (int q = 0; q < NB / 32; ++q) s += part[q][threadIdx.x];
     atomicAdd(&acc[threadIdx.x * ACC_STRIDE], s);
   }
+}
+
+// ---------------------------------------------------------------- thread sums
+// Energy and virial (7 components) summed by one thread over the atoms it
+// handles, kept in the thread's column of a shared-memory table. Float path:
+// compensated pairs (s, e) (Knuth's TwoSum keeps each addition's rounding
+// error in e), reduced over the warp as pairs and carried into double at the
+// warp totals: exact to double rounding at a few float operations per value,
+// where double arithmetic would run on GB300's FP64 pipe at 1/62 of the FP32
+// rate. Double path: plain doubles.
+template <class T> struct SumT;
+template <> struct SumT<float> { using type = float2; };
+template <> struct SumT<double> { using type = double; };
+
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float t = a.x + b.x;
+  const float bp = t - a.x;
+  const float err = (a.x - (t - bp)) + (b.x - bp);
+  return make_float2(t, (a.y + b.y) + err);
+}
+__device__ __forceinline__ void sum_zero(float2& p) { p = make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ void sum_zero(double& p) { p = 0.0; }
+__device__ __forceinline__ void sum_add(float2& p, float x) { p = pair_add(p, make_float2(x, 0.0f)); }
+__device__ __forceinline__ void sum_add(double& p, double x) { p += x; }
+// a compensated per-atom value (s, e)
+__device__ __forceinline__ void sum_add2(float2& p, float s_, float e_) {
+  p = pair_add(p, make_float2(s_, e_));
+}
+__device__ __forceinline__ void sum_add2(double& p, double s_, double e_) { p += s_ + e_; }
+
+__device__ __forceinline__ float2 shfl_xor2(float2 v, int m) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
+// Block sum of the 7 per-thread values col[k * NB] (this thread's column),
+// added to acc with one double atomic per component and block: the same
+// halving reduce-scatter over the warp as block_reduce_store_d, on pairs.
+template <int NB = BLOCK>
+__device__ __forceinline__ void block_reduce_sums(const float2* col, double* acc) {
+  __shared__ double part[NB / 32][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float2 v[8];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) v[k] = col[k * NB];
+  v[7] = make_float2(0.0f, 0.0f);
+  const bool hi16 = lane & 16;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 send = hi16 ? v[q] : v[q + 4];
+    const float2 keep = hi16 ? v[q + 4] : v[q];
+    v[q] = pair_add(keep, shfl_xor2(send, 16));
+  }
+  const bool hi8 = lane & 8;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float2 send = hi8 ? v[q] : v[q + 2];
+    const float2 keep = hi8 ? v[q + 2] : v[q];
+    v[q] = pair_add(keep, shfl_xor2(send, 8));
+  }
+  const bool hi4 = lane & 4;
+  {
+    const float2 send = hi4 ? v[0] : v[1];
+    const float2 keep = hi4 ? v[1] : v[0];
+    v[0] = pair_add(keep, shfl_xor2(send, 4));
+  }
+  v[0] = pair_add(v[0], shfl_xor2(v[0], 2));
+  v[0] = pair_add(v[0], shfl_xor2(v[0], 1));
+  if ((lane & 3) == 0) {
+    const int idx = (hi16 ? 4 : 0) + (hi8 ? 2 : 0) + (hi4 ? 1 : 0);
+    part[wid][idx] = to_f64(v[0].x) + to_f64(v[0].y);
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double s = 0.0;
+    for (int q = 0; q < NB / 32; ++q) s += part[q][threadIdx.x];
+    atomicAdd(&acc[threadIdx.x * ACC_STRIDE], s);
+  }
+}
+template <int NB = BLOCK>
+__device__ __forceinline__ void block_reduce_sums(const double* col, double* acc) {
+  double wd[6];
+  for (int k = 0; k < 6; ++k) wd[k] = col[(1 + k) * NB];
+  block_reduce_store_d<NB>(col[0], wd, acc);
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -724,10 +806,10 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
   // over its atoms in double, kept in the thread's column of a shared-memory
   // table (not in registers) and formed only when the reduction is wanted
   T w[6];
-  __shared__ double tsum[7][BLOCK];
+  __shared__ typename SumT<T>::type tsum[7][BLOCK];
   const bool want_acc = a.acc != nullptr;
   if (want_acc)
-    for (int q = 0; q < 7; ++q) tsum[q][threadIdx.x] = 0.0;
+    for (int q = 0; q < 7; ++q) sum_zero(tsum[q][threadIdx.x]);
   bool any = false;
   for (int item = blockIdx.x * BLOCK + threadIdx.x; item < n_items;
        item += gridDim.x * BLOCK) {
@@ -1063,11 +1145,14 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
     if (CS) {
       // the general path's float sums (eatom_i, w) and the fast path's
       // compensated ones (eatom_c, wa), into the thread's double sums
-      const double e_at = to_f64(eatom_i) + eatom_c.d();
-      if (a.eatom) a.eatom[i] = e_at;
+      if (a.eatom) a.eatom[i] = to_f64(eatom_i) + eatom_c.d();
       if (want_acc) {
-        tsum[0][threadIdx.x] += e_at;
-        for (int q = 0; q < 6; ++q) tsum[1 + q][threadIdx.x] += to_f64(w[q]) + wa[q].d();
+        sum_add(tsum[0][threadIdx.x], eatom_i);
+        sum_add2(tsum[0][threadIdx.x], eatom_c.s, eatom_c.lo());
+        for (int q = 0; q < 6; ++q) {
+          sum_add(tsum[1 + q][threadIdx.x], w[q]);
+          sum_add2(tsum[1 + q][threadIdx.x], wa[q].s, wa[q].lo());
+        }
       }
       continue;
     }
@@ -1075,17 +1160,13 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
     eatom_i += eatom_c.s;
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     if (want_acc) {
-      tsum[0][threadIdx.x] += to_f64(eatom_i);
-      for (int q = 0; q < 6; ++q) tsum[1 + q][threadIdx.x] += to_f64(w[q]);
+      sum_add(tsum[0][threadIdx.x], eatom_i);
+      for (int q = 0; q < 6; ++q) sum_add(tsum[1 + q][threadIdx.x], w[q]);
     }
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (EV && want_acc && __syncthreads_or(any)) {
-    double wd[6];
-    for (int q = 0; q < 6; ++q) wd[q] = tsum[1 + q][threadIdx.x];
-    block_reduce_store_d(tsum[0][threadIdx.x], wd, a.acc);
-  }
+  if (EV && want_acc && __syncthreads_or(any)) block_reduce_sums(&tsum[0][threadIdx.x], a.acc);
   if (a.left_reset) {
     // every block read the leftover count (uni[0]) before taking its ticket
     __syncthreads();
@@ -1144,10 +1225,10 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
   // the atom's own virial sums (float); energy and virial over the thread's
   // atoms in double (only when the reduction is wanted)
   T w[6];
-  __shared__ double tsum[7][WIDE_BLOCK];
+  __shared__ typename SumT<T>::type tsum[7][WIDE_BLOCK];
   const bool want_acc = a.acc != nullptr;
   if (want_acc)
-    for (int q = 0; q < 7; ++q) tsum[q][threadIdx.x] = 0.0;
+    for (int q = 0; q < 7; ++q) sum_zero(tsum[q][threadIdx.x]);
   bool any = false;
   for (int item = blockIdx.x * WIDE_BLOCK + threadIdx.x; item < n_items;
        item += gridDim.x * WIDE_BLOCK) {
@@ -1282,17 +1363,14 @@ __global__ void __launch_bounds__(WIDE_BLOCK) k_tersoff_wide(const __grid_consta
     }
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     if (want_acc) {
-      tsum[0][threadIdx.x] += to_f64(eatom_i);
-      for (int q = 0; q < 6; ++q) tsum[1 + q][threadIdx.x] += to_f64(w[q]);
+      sum_add(tsum[0][threadIdx.x], eatom_i);
+      for (int q = 0; q < 6; ++q) sum_add(tsum[1 + q][threadIdx.x], w[q]);
     }
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (want_acc && __syncthreads_or(any)) {
-    double wd[6];
-    for (int q = 0; q < 6; ++q) wd[q] = tsum[1 + q][threadIdx.x];
-    block_reduce_store_d<WIDE_BLOCK>(tsum[0][threadIdx.x], wd, a.acc);
-  }
+  if (want_acc && __syncthreads_or(any))
+    block_reduce_sums<WIDE_BLOCK>(&tsum[0][threadIdx.x], a.acc);
 }
 
 // ---------------------------------------------------------------- fast-forward ablation
@@ -1322,7 +1400,8 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_ffwd(const __grid_constant__ 
   using P = typename SelfPos<T>::type;
   const Shift<T, false> sh;
   T w[6];
-  double eid = 0.0, wd[6] = {0, 0, 0, 0, 0, 0};
+  __shared__ typename SumT<T>::type tsum[7][BLOCK];
+  for (int q = 0; q < 7; ++q) sum_zero(tsum[q][threadIdx.x]);
   // block-uniform loop: every lane of a warp takes part in every vote
   for (int i0 = blockIdx.x * BLOCK; i0 < a.n; i0 += gridDim.x * BLOCK) {
     const int i = i0 + threadIdx.x;
@@ -1459,10 +1538,13 @@ __global__ void __launch_bounds__(BLOCK) k_tersoff_ffwd(const __grid_constant__ 
       atomic_add3(a.f, i, to_f64(fix), to_f64(fiy), to_f64(fiz));
       if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     }
-    eid += to_f64(eatom_i);
-    for (int q = 0; q < 6; ++q) wd[q] += to_f64(w[q]);
+    sum_add(tsum[0][threadIdx.x], eatom_i);
+    for (int q = 0; q < 6; ++q) sum_add(tsum[1 + q][threadIdx.x], w[q]);
   }
-  if (a.acc != nullptr) block_reduce_store_d(eid, wd, a.acc);
+  if (a.acc != nullptr) {
+    __syncthreads();
+    block_reduce_sums(&tsum[0][threadIdx.x], a.acc);
+  }
 }
 
 }  // namespace fwd

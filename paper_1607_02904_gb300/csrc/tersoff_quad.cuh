@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(QBLOCK) k_tersoff_quad(const __grid_constant__
   __shared__ T sfilt[SNS * SNS];
   __shared__ float snear[SNS * SNS];
   __shared__ int uni[3];
-  __shared__ double tsum[7][QBLOCK];
+  __shared__ typename SumT<T>::type tsum[7][QBLOCK];
   const int ns = NS > 0 ? NS : a.ns;
   if (NS != 1)
     for (int q = threadIdx.x; q < ns * ns * ns * RSTRIDE; q += QBLOCK) srec_s[q] = a.rec[q];
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(QBLOCK) k_tersoff_quad(const __grid_constant__
   }
   const bool want_acc = EV && a.acc != nullptr;
   if (want_acc)
-    for (int q = 0; q < 7; ++q) tsum[q][threadIdx.x] = 0.0;
+    for (int q = 0; q < 7; ++q) sum_zero(tsum[q][threadIdx.x]);
   __syncthreads();
   const T* srec = NS == 1 ? a.prm1 : srec_s;
   const bool use_short = __int_as_float(uni[1]) <= a.dlim2;
@@ -315,21 +315,19 @@ __global__ void __launch_bounds__(QBLOCK) k_tersoff_quad(const __grid_constant__
       if (a.eatom && act && q == 0) a.eatom[i] = to_f64(vsum);
       if (want_acc && mine) {
         const T dx = ux * r, dy = uy * r, dzz = uz * r;
-        tsum[0][threadIdx.x] += to_f64(V);
-        tsum[1][threadIdx.x] += to_f64(dx * fx);
-        tsum[2][threadIdx.x] += to_f64(dy * fy);
-        tsum[3][threadIdx.x] += to_f64(dzz * fz);
-        tsum[4][threadIdx.x] += to_f64(dx * fy);
-        tsum[5][threadIdx.x] += to_f64(dx * fz);
-        tsum[6][threadIdx.x] += to_f64(dy * fz);
+        sum_add(tsum[0][threadIdx.x], V);
+        sum_add(tsum[1][threadIdx.x], dx * fx);
+        sum_add(tsum[2][threadIdx.x], dy * fy);
+        sum_add(tsum[3][threadIdx.x], dzz * fz);
+        sum_add(tsum[4][threadIdx.x], dx * fy);
+        sum_add(tsum[5][threadIdx.x], dx * fz);
+        sum_add(tsum[6][threadIdx.x], dy * fz);
       }
     }
   }
   if (want_acc) {
     __syncthreads();
-    double wd[6];
-    for (int k = 0; k < 6; ++k) wd[k] = tsum[1 + k][threadIdx.x];
-    block_reduce_store_d(tsum[0][threadIdx.x], wd, a.acc);
+    block_reduce_sums<QBLOCK>(&tsum[0][threadIdx.x], a.acc);
   }
 }
 
