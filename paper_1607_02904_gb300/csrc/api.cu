@@ -882,7 +882,8 @@ static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
         c->launches -= bk;  // counted per rebuild that runs
       }
     }
-    if ((st = tgb::launch_forward(c, c->d_extra, acc, nullptr, s))) return st;
+    // the thermo rows take the potential energy only: no virial
+    if ((st = tgb::launch_forward(c, c->d_extra, acc, nullptr, s, false))) return st;
   }
   {
     tgb::TimedRegion tr(c, 2, s);
@@ -923,6 +924,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     c->coef.cf[t] = (float)hc[t];
     c->coef.c2f[t] = (float)(2.0 * hc[t]);
     c->coef.m[t] = hc[TERSOFF_MAX_SPECIES + t];
+    c->coef.hmf[t] = (float)(0.5 * hc[TERSOFF_MAX_SPECIES + t]);
   }
   if ((st = tgb::ensure_nbr(c))) return st;
   double* rows = nullptr;

@@ -2,8 +2,9 @@
 #include "fwd_launch.cuh"
 
 namespace tgb {
-int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
-  return fwd::launch_prec<double>(c, f, acc, eatom, s);
+int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s,
+                       bool virial) {
+  return fwd::launch_prec<double>(c, f, acc, eatom, s, virial);
 }
 
 int launch_forward_batch(Ctx* c, double* f, cudaStream_t s) {
@@ -12,9 +13,9 @@ int launch_forward_batch(Ctx* c, double* f, cudaStream_t s) {
   return fwd::launch_batch<double>(c, f, s);
 }
 
-int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
+int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s, bool virial) {
   if (c->n == 0) return TERSOFF_OK;
-  if (c->precision == TERSOFF_MIXED) return launch_forward_f32(c, f, acc, eatom, s);
-  return launch_forward_f64(c, f, acc, eatom, s);
+  if (c->precision == TERSOFF_MIXED) return launch_forward_f32(c, f, acc, eatom, s, virial);
+  return launch_forward_f64(c, f, acc, eatom, s, virial);
 }
 }  // namespace tgb

@@ -38,6 +38,14 @@ void launch_wide(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
   c->launches++;
 }
 
+// Energy/virial mode of a force launch (the EV parameter of k_tersoff).
+template <class T, bool BATCH>
+int ev_mode(const FwdArgs<T>& a) {
+  if (BATCH) return 2;
+  if (a.acc != nullptr) return a.virial ? 2 : 1;
+  return a.eatom != nullptr ? 1 : 0;
+}
+
 // Grids are fixed by the atom count (the bucket sizes live on the device), so
 // the launches can be captured in a CUDA graph and replayed across builds.
 template <class T, int NS, int ZC, bool BATCH = false>
@@ -47,15 +55,23 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
     launch_forward_cs(c, &a, ZC, grid, s);
     return;
   }
-  // forces only (MD steps): the instance without energy and virial sums
-  const bool ev = BATCH || a.acc != nullptr || a.eatom != nullptr;
-  if (ZC == 4 && !BATCH && !ev) {
+  // forces only, or energy without the virial (MD steps, with or without
+  // thermo): the instances with less bookkeeping
+  const int evm = ev_mode<T, BATCH>(a);
+  if (ZC == 4 && !BATCH && evm == 0) {
     if (c->has_lam3)
-      k_tersoff<T, NS, ZC, 1, false, false, false><<<grid, BLOCK, 0, s>>>(a);
+      k_tersoff<T, NS, ZC, 1, false, false, 0><<<grid, BLOCK, 0, s>>>(a);
     else if (c->sym_table)
-      k_tersoff<T, NS, ZC, 2, false, false, false><<<grid, BLOCK, 0, s>>>(a);
+      k_tersoff<T, NS, ZC, 2, false, false, 0><<<grid, BLOCK, 0, s>>>(a);
     else
-      k_tersoff<T, NS, ZC, 0, false, false, false><<<grid, BLOCK, 0, s>>>(a);
+      k_tersoff<T, NS, ZC, 0, false, false, 0><<<grid, BLOCK, 0, s>>>(a);
+  } else if (ZC == 4 && !BATCH && evm == 1) {
+    if (c->has_lam3)
+      k_tersoff<T, NS, ZC, 1, false, false, 1><<<grid, BLOCK, 0, s>>>(a);
+    else if (c->sym_table)
+      k_tersoff<T, NS, ZC, 2, false, false, 1><<<grid, BLOCK, 0, s>>>(a);
+    else
+      k_tersoff<T, NS, ZC, 0, false, false, 1><<<grid, BLOCK, 0, s>>>(a);
   } else if (c->has_lam3) {
     k_tersoff<T, NS, ZC, 1, BATCH><<<grid, BLOCK, 0, s>>>(a);
   } else if (c->sym_table) {
@@ -77,10 +93,11 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
 // Grid of a force launch: one thread per item, or (launch option) a number of
 // waves of the blocks that fit on all SMs at once (resident blocks per SM from
 // the kernel's launch bounds), the kernel looping over the items.
-inline int force_grid(const Ctx* c, int zc) {
+inline int force_grid(const Ctx* c, int zc, int evm) {
   const int full = (c->n + BLOCK - 1) / BLOCK;
   if (c->opt_waves <= 0 || c->n_sm <= 0) return full;
-  const int resident = c->n_sm * (zc <= 4 ? 8 : 4);
+  // the blocks of this instance resident on one SM (its launch bound)
+  const int resident = c->n_sm * fwd_min_blocks(zc <= 4 ? 4 : 8, zc <= 4 ? evm : 2);
   const int g = c->opt_waves * resident;
   return g < full ? g : full;
 }
@@ -133,7 +150,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
     b1.order2 = b1.order3 = nullptr;
     b1.n_items2 = b1.n_items3 = nullptr;
     b1.identity = 0;
-    launch_t<T, NS, 8, BATCH>(c, b1, force_grid(c, 8), s2);
+    launch_t<T, NS, 8, BATCH>(c, b1, force_grid(c, 8, ev_mode<T, BATCH>(a)), s2);
   }
   // bucket 0, then bucket 1 (unless split off), then bucket 2 (general path)
   const bool wide = (long long)c->nbucket[2] * 200 > (long long)c->n;
@@ -149,7 +166,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
   b0.identity = (split1 || wide) ? 0 : 1;
   {
     TimedRegion tr(c, 0, s);
-    launch_t<T, NS, 4, BATCH>(c, b0, force_grid(c, 4), s);
+    launch_t<T, NS, 4, BATCH>(c, b0, force_grid(c, 4, ev_mode<T, BATCH>(a)), s);
     if (wide) launch_wide<T, NS, BATCH>(c, a, s);
   }
   if (fork) {
@@ -159,8 +176,9 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
 }
 
 template <class T>
-FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom) {
+FwdArgs<T> make_args(Ctx* c, double* f, double* acc, double* eatom, bool virial = true) {
   FwdArgs<T> a;
+  a.virial = virial ? 1 : 0;
   a.n = c->n;
   a.cap = c->cap;
   a.ns = c->ns;
@@ -222,8 +240,9 @@ void launch_ffwd(Ctx* c, const FwdArgs<T>& a, cudaStream_t s) {
 }
 
 template <class T>
-int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s) {
-  FwdArgs<T> a = make_args<T>(c, f, acc, eatom);
+int launch_prec(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s,
+                bool virial = true) {
+  FwdArgs<T> a = make_args<T>(c, f, acc, eatom, virial);
   if (c->ablate & TERSOFF_ABLATE_FASTFWD) {
     switch (c->ns) {
       case 1: launch_ffwd<T, 1>(c, a, s); break;

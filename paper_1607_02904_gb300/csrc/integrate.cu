@@ -89,6 +89,42 @@ __global__ void k_pack(PackArgs a, const double* __restrict__ x) {
   track_max(a, d2);
 }
 
+// double -> float rounded to nearest (ties away from zero) through the IEEE-754
+// bit layouts, for values in float's normal range (velocities, forces); below
+// it gives signed zero. Integer operations only: conversions involving double
+// run on GB300's FP64 pipe at 1/62 of the FP32 rate.
+__device__ __forceinline__ float d2f_bits(double d) {
+  const unsigned long long u = __double_as_longlong(d);
+  const unsigned long long mag = (u & 0x7fffffffffffffffull) + 0x10000000ull;  // + half ulp
+  const int e = (int)(mag >> 52) - 1023 + 127;
+  uint32_t f = ((uint32_t)e << 23) | (uint32_t)((mag >> 29) & 0x7fffffu);
+  f = e <= 0 ? 0u : (e >= 255 ? 0x7f800000u : f);
+  return __uint_as_float(f | (uint32_t)(u >> 32 & 0x80000000ull));
+}
+
+// Block sum of one float per thread, added to dst: compensated float pairs
+// over the warp (TwoSum), warp totals carried into double.
+__device__ __forceinline__ void block_sum_add_f(float x, double* dst) {
+  float s = x, e = 0.0f;
+  for (int o = 16; o > 0; o >>= 1) {
+    const float os = __shfl_xor_sync(0xffffffffu, s, o);
+    const float oe = __shfl_xor_sync(0xffffffffu, e, o);
+    const float t = s + os;
+    const float bp = t - s;
+    e = (e + oe) + ((s - (t - bp)) + (os - bp));
+    s = t;
+  }
+  __shared__ double ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) ws[wid] = gather_f2d(s) + gather_f2d(e);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    atomicAdd(dst, t);
+  }
+}
+
 __device__ __forceinline__ void block_sum_add(double v, double* dst) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __shared__ double ws[32];
@@ -112,7 +148,8 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (acc_zero && i < 8) acc_zero[i * ACC_STRIDE] = 0.0;
   float d2 = 0.0f;
-  double ke = 0.0;
+  double ke = 0.0;   // FP64 path
+  float kef = 0.0f;  // mixed path: in float (m v^2 / 2 in amu A^2/ps^2, ~1e1 per atom)
   if (i < pk.n) {
     const int t = pk.types[i];
     const size_t b = 3 * (size_t)i;
@@ -141,16 +178,18 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
       const float d2v = kf * sc[2] + kf * sc[5];
       const bool extra = ga.flags[FLAG_EXTRA] | ga.flags[FLAG_EXTRA_STICKY];
       if (ke_row) {
+        // the previous step's full velocity in float (the kinetic energy is a
+        // thermo output; it does not feed the dynamics)
         const float hf = cf.cf[t];
-        double w0 = v0 + gather_f2d(hf * sc[0] + hf * sc[3]);
-        double w1 = v1 + gather_f2d(hf * sc[1] + hf * sc[4]);
-        double w2 = v2 + gather_f2d(hf * sc[2] + hf * sc[5]);
+        float w0 = d2f_bits(v0) + (hf * sc[0] + hf * sc[3]);
+        float w1 = d2f_bits(v1) + (hf * sc[1] + hf * sc[4]);
+        float w2 = d2f_bits(v2) + (hf * sc[2] + hf * sc[5]);
         if (extra) {  // forces scattered through the fallback buffer
-          w0 = fma(cu, F0, w0);
-          w1 = fma(cu, F1, w1);
-          w2 = fma(cu, F2, w2);
+          w0 = fmaf(hf, d2f_bits(F0), w0);
+          w1 = fmaf(hf, d2f_bits(F1), w1);
+          w2 = fmaf(hf, d2f_bits(F2), w2);
         }
-        ke = 0.5 * cf.m[t] * fma(w0, w0, fma(w1, w1, w2 * w2));
+        kef = cf.hmf[t] * fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
       }
       vn0 = v0 + gather_f2d(d0);
       vn1 = v1 + gather_f2d(d1);
@@ -180,7 +219,12 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
     if (do_pack) d2 = pack_one(pk, i, t, xn0, xn1, xn2);
   }
   if (do_pack) track_max(pk, d2);
-  if (ke_row) block_sum_add(ke, ke_row);
+  if (ke_row) {
+    if (gather && !ga.fp64 && !ga.atomic_mode)
+      block_sum_add_f(kef, ke_row);
+    else
+      block_sum_add(ke, ke_row);
+  }
 }
 
 // closing half kick with gathered forces, which are also written to f

@@ -76,6 +76,7 @@ struct Coef {
   double m[TERSOFF_MAX_SPECIES];
   float cf[TERSOFF_MAX_SPECIES];   // c and 2c rounded to float (mixed-path increments)
   float c2f[TERSOFF_MAX_SPECIES];
+  float hmf[TERSOFF_MAX_SPECIES];  // m / 2 in float (mixed-path kinetic energy)
 };
 
 // Cell grid of one periodic system on the device (the launch-wide grid, or one
@@ -314,9 +315,13 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s);
 
 // Forces (fwd_f32.cu / fwd_f64.cu). Accumulates into f (zeroed by the caller),
 // energy and virial into acc components 0..6 (zeroed by the caller); eatom optional.
-int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
-int launch_forward_f32(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
-int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s);
+// virial false: acc receives the energy only (its virial components stay 0).
+int launch_forward(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s,
+                   bool virial = true);
+int launch_forward_f32(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s,
+                       bool virial);
+int launch_forward_f64(Ctx* c, double* f, double* acc, double* eatom, cudaStream_t s,
+                       bool virial);
 // the force launches of the TERSOFF_ABLATE_COMP_ATOM_SUMS variant (fwd_f32_cs.cu),
 // register capacity 4 or 8; args is a fwd::FwdArgs<float>
 int launch_forward_cs(Ctx* c, const void* args, int zc, int grid, cudaStream_t s);

@@ -179,6 +179,7 @@ template <class T> struct FwdArgs {
   const SysShift* sys;   // per system: periodic shift units
   const int* atom_sys;   // system of each atom
   double* vatom;         // per-atom virial (6), summed per system afterwards
+  int virial;            // the virial is wanted (with acc): 0 for the MD steps' thermo
   int* left;             // four-lane kernel: atoms left to the per-thread kernel
   int left_reset;        // per-thread kernel over that list: the last block zeroes the
                          // list's count (FLAG_LEFT) and its own ticket
@@ -756,14 +757,21 @@ template <class T> struct Acc<T, true> {
 // the terms of its atom -- the force on each neighbour and on the atom, its
 // energy and virial -- is compensated, carried into double, and forces are
 // scattered with FP64 atomics (the TERSOFF_ABLATE_COMP_ATOM_SUMS variant).
-// EV false: forces only (no energy, virial or per-atom energy requested, a
-// single system): the instance the MD steps launch, with no energy or virial
-// bookkeeping and room for one more block per SM.
-template <class T, int NS, int ZC, int MODE, bool BATCH = false, bool CS = false, bool EV = true>
-__global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
+// Resident blocks per SM that the force kernel's launch bound asks for: the
+// register budget, and the grid of the "waves" launch option.
+__host__ __device__ constexpr int fwd_min_blocks(int zc, int ev) {
+  return zc <= 4 ? (ev == 2 ? 7 : 8) : 4;
+}
+
+// EV: 2 energy and virial (and per-atom energy) as requested; 1 energy and
+// per-atom energy only (the MD steps' thermo); 0 forces only (the MD steps
+// without thermo). Instances 0 and 1 carry less bookkeeping and fit one more
+// block per SM.
+template <class T, int NS, int ZC, int MODE, bool BATCH = false, bool CS = false, int EV = 2>
+__global__ void __launch_bounds__(BLOCK, fwd_min_blocks(ZC, EV))
     k_tersoff(const __grid_constant__ FwdArgs<T> a) {
   static_assert(!(CS && BATCH), "compensated per-atom sums: single systems only");
-  static_assert(EV || !BATCH, "batches need the per-atom energy and virial");
+  static_assert(EV == 2 || !BATCH, "batches need the per-atom energy and virial");
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
   __shared__ T srec_s[SREC];
@@ -1000,7 +1008,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
             if (rr[qj] < p2[K_ROUT2]) {
               T V, dVdr, dz;
               pair_fc<T>(p2, rr[qj], zeta[qj], fc3[qj], dfc3[qj], V, dVdr, dz);
-              if (EV) eatom_c.add(V);
+              if (EV >= 1) eatom_c.add(V);
               dzt[qj] = dz;
               fx[qj].add(-dVdr * ux[qj]);
               fy[qj].add(-dVdr * uy[qj]);
@@ -1068,7 +1076,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
             }
             T V, dVdr, dz;
             pair<T>(p2, rij, zeta, V, dVdr, dz, rex[qj]);
-            if (EV) eatom_c.add(V);
+            if (EV >= 1) eatom_c.add(V);
             fx[qj].add(-(dVdr * ux[qj] + dz * gjx));
             fy[qj].add(-(dVdr * uy[qj] + dz * gjy));
             fz[qj].add(-(dVdr * uz[qj] + dz * gjz));
@@ -1105,7 +1113,7 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
             wa[3].add(dx * fy[q].s + dx * fy[q].lo());
             wa[4].add(dx * fz[q].s + dx * fz[q].lo());
             wa[5].add(dy * fz[q].s + dy * fz[q].lo());
-          } else if (EV) {
+          } else if (EV == 2) {
             w[0] += dx * fx[q].s;
             w[1] += dy * fy[q].s;
             w[2] += dz * fz[q].s;
@@ -1156,17 +1164,18 @@ __global__ void __launch_bounds__(BLOCK, (ZC <= 4 ? (EV ? 7 : 8) : 4))
       }
       continue;
     }
-    if (!EV) continue;
+    if (EV == 0) continue;
     eatom_i += eatom_c.s;
     if (a.eatom) a.eatom[i] = to_f64(eatom_i);
     if (want_acc) {
       sum_add(tsum[0][threadIdx.x], eatom_i);
-      for (int q = 0; q < 6; ++q) sum_add(tsum[1 + q][threadIdx.x], w[q]);
+      if (EV == 2)
+        for (int q = 0; q < 6; ++q) sum_add(tsum[1 + q][threadIdx.x], w[q]);
     }
     if (BATCH)
       for (int q = 0; q < 6; ++q) a.vatom[6 * (size_t)i + q] = to_f64(w[q]);
   }
-  if (EV && want_acc && __syncthreads_or(any)) block_reduce_sums(&tsum[0][threadIdx.x], a.acc);
+  if (EV >= 1 && want_acc && __syncthreads_or(any)) block_reduce_sums(&tsum[0][threadIdx.x], a.acc);
   if (a.left_reset) {
     // every block read the leftover count (uni[0]) before taking its ticket
     __syncthreads();
