@@ -142,10 +142,17 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst) {
 // previous step ; clear the accumulator for the coming force evaluation.
 // F: from f on the first step of a call, gathered from the last force
 // evaluation afterwards. All loads of an atom are issued before its stores.
-__global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restrict__ x,
+// MG: the instance for the mixed path's gathered steps (gather set, float
+// slots with compensated sums), KE its kinetic-energy row; with MG false the
+// kernel decides both at run time. The specialised instances carry fewer
+// registers.
+template <bool MG, bool KE>
+__global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restrict__ x,
                        double* __restrict__ v, const double* __restrict__ f, const __grid_constant__ Coef cf,
-                       double dt, int kick, int do_pack, double* ke_row, double* acc_zero) {
+                       double dt, int kick, int do_pack, double* ke_row_, double* acc_zero) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gather = MG ? 1 : gather_;
+  double* const ke_row = MG ? (KE ? ke_row_ : nullptr) : ke_row_;
   if (acc_zero && i < 8) acc_zero[i * ACC_STRIDE] = 0.0;
   float d2 = 0.0f;
   double ke = 0.0;   // FP64 path
@@ -157,7 +164,7 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
     const double v0 = v[b], v1 = v[b + 1], v2 = v[b + 2];
     double F0, F1, F2;
     float sc[6] = {0, 0, 0, 0, 0, 0};
-    const bool mixed = gather && !ga.fp64 && !ga.atomic_mode;
+    const bool mixed = MG || (gather && !ga.fp64 && !ga.atomic_mode);
     if (gather) {
       gather_force(ga, i, F0, F1, F2, mixed ? sc : nullptr);
     } else {
@@ -220,7 +227,7 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather, double* __restric
   }
   if (do_pack) track_max(pk, d2);
   if (ke_row) {
-    if (gather && !ga.fp64 && !ga.atomic_mode)
+    if (MG || (gather && !ga.fp64 && !ga.atomic_mode))
       block_sum_add_f(kef, ke_row);
     else
       block_sum_add(ke, ke_row);
@@ -345,9 +352,19 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s) {
 int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick, bool pack,
                    double* ke_row, double* acc_zero, cudaStream_t s) {
   const int B = c->opt_block;
-  k_step<<<(c->n + B - 1) / B, B, 0, s>>>(make_pack(c, true), make_gather(c), kick == 2 ? 1 : 0,
-                                            x, v, f, c->coef, dt, kick, pack ? 1 : 0, ke_row,
-                                            acc_zero);
+  const GatherArgs ga = make_gather(c);
+  const int grid = (c->n + B - 1) / B;
+  if (kick == 2 && !ga.fp64 && !ga.atomic_mode) {
+    if (ke_row)
+      k_step<true, true><<<grid, B, 0, s>>>(make_pack(c, true), ga, 1, x, v, f, c->coef, dt, kick,
+                                            pack ? 1 : 0, ke_row, acc_zero);
+    else
+      k_step<true, false><<<grid, B, 0, s>>>(make_pack(c, true), ga, 1, x, v, f, c->coef, dt, kick,
+                                             pack ? 1 : 0, nullptr, acc_zero);
+  } else {
+    k_step<false, false><<<grid, B, 0, s>>>(make_pack(c, true), ga, kick == 2 ? 1 : 0, x, v, f,
+                                            c->coef, dt, kick, pack ? 1 : 0, ke_row, acc_zero);
+  }
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;
