@@ -391,6 +391,38 @@ int tersoff_timing(tersoff_ctx* ctx, int kind, double* total_ms, long long* laun
  * `stream`. Returns TERSOFF_E_CUDA when no device is usable. */
 int tersoff_pipe_peaks(double* out, void* stream);
 
+/* Ghost-shell packing for a slab decomposition of one periodic cell over
+ * ranks (the data-parallel layout of the paper's multi-node runs, Sec. V):
+ * one rank's owned atoms in; its local frame and the two face sets it sends
+ * to its neighbours out, each already in the receiver's local frame, so that
+ * a halo exchange sends the buffers as they are and the receiver appends
+ * them after its own atoms.
+ *   x (n x 3), types (n, int32), ids (n, int64): the rank's owned atoms.
+ *   axis: the cut axis (0, 1 or 2).
+ *   geo: HOST array of 9 doubles: L (the box edge along the axis), lo, hi
+ *     (the rank's slab [lo, hi)), r_ghost (the ghost width), frame (the
+ *     origin of the rank's local frame along the axis), shift_lower,
+ *     frame_lower, shift_upper, frame_upper (for the lower / upper face set:
+ *     the periodic shift it takes across the boundary, and the frame origin
+ *     of the neighbour that receives it).
+ * With u the axis coordinate wrapped into [0, L) (the remainder of the
+ * division by L, moved up by L when negative; +0 for a zero remainder):
+ *   x_local (n x 3): the owned atoms with the axis coordinate u - frame;
+ *   set 0 (lower face: u - lo < r_ghost) and set 1 (upper face:
+ *   hi - u <= r_ghost), each in ascending owned index, into send_x
+ *   (2 x cap x 3, set-major), send_t (2 x cap) and send_id (2 x cap), the
+ *   axis coordinate (u + shift) - frame of the receiver (two roundings, in
+ *   that order), the other two coordinates unchanged;
+ *   counts (2 ints): the sizes of the two sets (atoms beyond cap are counted,
+ *   not written: compare counts with cap).
+ * Needs no parameters or lists on ctx (it serves error reporting and the
+ * launch count). Allocates a scratch buffer of 8 bytes per 1024 atoms
+ * (stream-ordered); does not synchronise. */
+int tersoff_halo_pack(tersoff_ctx* ctx, const double* x, const int* types, const long long* ids,
+                      int n, int axis, const double* geo, int cap, double* x_local,
+                      double* send_x, int* send_t, long long* send_id, int* counts,
+                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ _SIG = {
     "tersoff_set_scatter": ([_P, _I], _I),
     "tersoff_timing": ([_P, _I, _P, _P], _I),
     "tersoff_pipe_peaks": ([_P, _P], _I),
+    "tersoff_halo_pack": ([_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _P, _P, _P, _P], _I),
 }
 
 
@@ -203,6 +204,17 @@ class Context:
 
     def set_neighbor_capacity(self, cap):
         self._check(self.lib.tersoff_set_neighbor_capacity(self.h, int(cap)))
+
+    def halo_pack(self, x, types, ids, axis, geo, cap, x_local, send_x, send_t, send_id,
+                  counts, stream=None):
+        """tersoff_halo_pack: geo holds the 9 host doubles (L, lo, hi, r_ghost,
+        frame, shift_lower, frame_lower, shift_upper, frame_upper); the output
+        tensors are the caller's."""
+        g = (_D * 9)(*[float(v) for v in geo])
+        self._check(self.lib.tersoff_halo_pack(
+            self.h, _ptr(x), _ptr(types), _ptr(ids), int(x.shape[0]), int(axis), g, int(cap),
+            _ptr(x_local), _ptr(send_x), _ptr(send_t), _ptr(send_id), _ptr(counts),
+            _stream(stream)))
 
     def neighbor_export(self, cap, stream=None):
         import torch

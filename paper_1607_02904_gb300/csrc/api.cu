@@ -1259,6 +1259,27 @@ int tersoff_set_lanes(tersoff_ctx* p, int lanes) {
   return TERSOFF_OK;
 }
 
+int tersoff_halo_pack(tersoff_ctx* p, const double* x, const int* types, const long long* ids,
+                      int n, int axis, const double* geo, int cap, double* x_local,
+                      double* send_x, int* send_t, long long* send_id, int* counts,
+                      void* stream) {
+  Ctx* c = C(p);
+  if (!c) return TERSOFF_E_INVALID_ARG;
+  if (n < 0 || cap < 0 || axis < 0 || axis > 2 || !geo || !counts)
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "n >= 0, cap >= 0, axis in {0, 1, 2}, geo and counts set");
+  if (n > 0 && (!x || !types || !ids || !x_local))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "x, types, ids and x_local must be set when n > 0");
+  if (cap > 0 && (!send_x || !send_t || !send_id))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "send buffers must be set when cap > 0");
+  for (int q = 0; q < 9; ++q)
+    if (!std::isfinite(geo[q]))
+      return tgb::fail(c, TERSOFF_E_INVALID_ARG, "geo values must be finite");
+  if (!(geo[0] > 0.0) || !(geo[3] >= 0.0))
+    return tgb::fail(c, TERSOFF_E_INVALID_ARG, "L > 0 and r_ghost >= 0");
+  return tgb::launch_halo_pack(c, x, types, ids, n, axis, geo, cap, x_local, send_x, send_t,
+                               send_id, counts, (cudaStream_t)stream);
+}
+
 int tersoff_set_ablation(tersoff_ctx* p, int flags) {
   Ctx* c = C(p);
   if (!c) return TERSOFF_E_INVALID_ARG;

@@ -359,6 +359,13 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
 // displacement since the last build exceeds lim2 (and counts it), else 0.
 int launch_decide_rebuild(Ctx* c, float lim2, cudaGraphConditionalHandle h, cudaStream_t s);
 // thermo (nsteps x 3: potential, kinetic [eV], total) from the accumulator rows
+// Ghost-shell packing of a slab decomposition (halo.cu); geo: 9 host doubles
+// (L, lo, hi, r_ghost, frame, shift_lower, frame_lower, shift_upper,
+// frame_upper).
+int launch_halo_pack(Ctx* c, const double* x, const int* types, const long long* ids, int n,
+                     int axis, const double* geo, int cap, double* x_local, double* send_x,
+                     int* send_t, long long* send_id, int* counts, cudaStream_t s);
+
 int launch_thermo_rows(Ctx* c, const double* rows, int nsteps, double mvv2e, double* thermo,
                        cudaStream_t s);
 // Parameter adjoint (tersoff_bwd.cu): adds d/dtheta [gE E + sum gF . F] to

@@ -221,7 +221,8 @@ __global__ void k_cell_pos(int n, const int* __restrict__ cell_atoms,
   posc[s] = make_float4(p.x, p.y, p.z, __int_as_float(4 * j + __float_as_int(p.w)));
 }
 
-template <bool BATCH>
+// NS1: one species (the short-list radii are single values)
+template <bool BATCH, bool NS1>
 __global__ void __launch_bounds__(128) k_neigh(
     int n, const double* __restrict__ x, const float4* __restrict__ pos32,
     const int* __restrict__ cell_of, const int* __restrict__ cell_start,
@@ -266,27 +267,26 @@ __global__ void __launch_bounds__(128) k_neigh(
             const float4 pj = posc[s];
             const int jt = __float_as_int(pj.w);
             const int j = jt >> 2, tj = jt & 3;
-            if (j == i) continue;
             const float dx = (pj.x - pi.x) + sx;
             const float dy = (pj.y - pi.y) + sy;
             const float dz = (pj.z - pi.z) + sz;
             const float r2 = dx * dx + dy * dy + dz * dz;
-            bool in;
-            if (r2 < lo2)
-              in = true;
-            else if (r2 > hi2)
-              in = false;
-            else
-              in = exact_member(x, i, j, g, rc2, dx, dy, dz);
+            // FP32 classification; candidates in the band around the list
+            // radius take the exact test (rare)
+            bool in = r2 < lo2;
+            if (r2 >= lo2 && r2 <= hi2) in = exact_member(x, i, j, g, rc2, dx, dy, dz);
+            in = in && j != i;
             if (in) {
               const uint32_t e = (uint32_t)j | code;
               if (count < cap) nbr[(size_t)count * n + i] = e;
               ++count;
               // short list: within the filter radius plus the margin
-              if (r2 <= lim.r2[ti * ns + tj]) {
+              const float l2 = NS1 ? lim.r2[0] : lim.r2[ti * ns + tj];
+              const float c2 = NS1 ? core.r2[0] : core.r2[ti * ns + tj];
+              if (r2 <= l2) {
                 if (z < cap) shortl[(size_t)z * n + i] = e;
                 ++z;
-                zw += r2 <= core.r2[ti * ns + tj] ? 1 : 0;
+                zw += r2 <= c2 ? 1 : 0;
               }
             }
           }
@@ -471,12 +471,17 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
     }
   if (n > 0) {
     if (batch)
-      k_neigh<true><<<(n + 127) / 128, 128, 0, s>>>(
+      k_neigh<true, false><<<(n + 127) / 128, 128, 0, s>>>(
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, c->d_geo,
           c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
           c->d_zcnt, c->d_bucket, c->d_zw, c->d_flags);
+    else if (c->ns == 1)
+      k_neigh<false, true><<<(n + 127) / 128, 128, 0, s>>>(
+          n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
+          rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
+          c->d_bucket, c->d_zw, c->d_flags);
     else
-      k_neigh<false><<<(n + 127) / 128, 128, 0, s>>>(
+      k_neigh<false, false><<<(n + 127) / 128, 128, 0, s>>>(
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
           c->d_bucket, c->d_zw, c->d_flags);

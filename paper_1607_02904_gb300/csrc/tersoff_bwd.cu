@@ -65,6 +65,8 @@ template <> struct BM<float> {
     sincospif(x, s, c);
   }
   static __device__ __forceinline__ float sq(float x) { return sqrtf(x); }
+  // reciprocal: hardware approximation and one Newton step (~1 ulp)
+  static __device__ __forceinline__ float rcp(float x) { return fwd::M<float>::rcp_nr(x); }
 };
 template <> struct BM<double> {
   static __device__ __forceinline__ double ex(double x) { return exp(x); }
@@ -75,6 +77,7 @@ template <> struct BM<double> {
     sincospi(x, s, c);
   }
   static __device__ __forceinline__ double sq(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 };
 
 // f_C(r; R, D), its r-derivative, and the R- and D-derivatives of both.
@@ -96,19 +99,21 @@ __device__ __forceinline__ Cut<T> cutoff_ad(T r, T R, T D) {
   // x = pi (r - R) / (2 D) = pi/2 - pi delta/(2D), delta = R + D - r: with
   // sh, ch = sin, cos(pi delta/(4D)), sin x = 1 - 2 sh^2 and cos x = 2 sh ch,
   // and f_C = 1/2 - 1/2 sin x = sh^2 without cancellation near R + D
+  // (one reciprocal of D; products in place of the divisions)
   const T delta = (R + D) - r;
+  const T iD = BM<T>::rcp(D);
   T sh, ch;
-  BM<T>::scpi(delta / (T(4) * D), &sh, &ch);
+  BM<T>::scpi(delta * (T(0.25) * iD), &sh, &ch);
   const T s = T(1) - T(2) * sh * sh, c = T(2) * sh * ch;
   const T PI = T(3.14159265358979323846);
-  const T x = PI * (r - R) / (T(2) * D);
-  const T k = PI / (T(4) * D);  // pi / (4 D)
+  const T x = PI * (r - R) * (T(0.5) * iD);
+  const T k = PI * (T(0.25) * iD);  // pi / (4 D)
   o.fc = sh * sh;
   o.dfc = -k * c;
   o.fc_R = k * c;
-  o.fc_D = T(0.5) * c * x / D;
-  o.dfc_R = -k * PI / (T(2) * D) * s;
-  o.dfc_D = k / D * (c - x * s);
+  o.fc_D = T(0.5) * c * x * iD;
+  o.dfc_R = -k * PI * (T(0.5) * iD) * s;
+  o.dfc_D = k * iD * (c - x * s);
   return o;
 }
 
@@ -121,18 +126,21 @@ template <class T> struct Ang {
 template <class T>
 __device__ __forceinline__ Ang<T> angular_ad(T cs, T ga, T c, T d, T h) {
   Ang<T> o;
+  // (reciprocals of d and Den; products in place of the divisions)
   const T t = h - cs;
   const T t2 = t * t;
   const T d2 = d * d;
   const T den = d2 + t2;
-  const T iden = T(1) / den;
+  const T iden = BM<T>::rcp(den);
   const T iden2 = iden * iden;
+  const T id = BM<T>::rcp(d);
+  const T id2 = id * id;
   const T c2 = c * c;
-  const T r = t2 / (d2 * den);  // (1/d^2 - 1/Den)
+  const T r = t2 * id2 * iden;  // (1/d^2 - 1/Den)
   o.g_ga = T(1) + c2 * r;
   o.g = ga * o.g_ga;
   o.g_c = T(2) * ga * c * r;
-  o.g_d = -T(2) * ga * c2 * t2 * (T(2) * d2 + t2) / (d2 * d * den * den);
+  o.g_d = -T(2) * ga * c2 * t2 * (T(2) * d2 + t2) * (id2 * id) * iden2;
   o.dg = -T(2) * ga * c2 * t * iden2;
   o.g_h = -o.dg;
   o.dg_ga = -T(2) * c2 * t * iden2;

@@ -215,6 +215,116 @@ def distributed_energy_forces(dec: SlabDecomposition, x_own, types_own, ids_own,
     return e, f
 
 
+def pack_geometry(dec: SlabDecomposition, rank: int):
+    """The 9 values that tersoff_halo_pack takes for ``rank``: the box edge
+    along the cut axis, the slab [lo, hi), the ghost width, the rank's frame
+    origin (lo - r_ghost: ``to_local``), and for the lower and upper face sets
+    the periodic shift each takes (as in ``face_sets``) and the frame origin
+    of the neighbour that receives it."""
+    L = float(dec.box[dec.axis])
+    lo, hi = dec.bounds(rank)
+    rg = dec.r_ghost
+    world = dec.world
+    frame = lo - rg
+    shift_lower = L if rank == 0 else 0.0
+    shift_upper = -L if rank == world - 1 else 0.0
+    frame_lower = dec.bounds((rank - 1) % world)[0] - rg
+    frame_upper = dec.bounds((rank + 1) % world)[0] - rg
+    return [L, lo, hi, rg, frame, shift_lower, frame_lower, shift_upper, frame_upper]
+
+
+def device_pack(ctx):
+    """The face-set packing of ``halo_exchange_device`` on the GPU: one call
+    of tersoff_halo_pack through ``ctx`` (a library Context). Returns
+    (x_local, send_x, send_t, send_id, counts on the host)."""
+    import torch
+
+    def pack(dec, x_own, types_own, ids_own, rank):
+        n = x_own.shape[0]
+        cap = max(n, 1)
+        dev = x_own.device
+        x_local = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        send_x = torch.empty((2, cap, 3), dtype=torch.float64, device=dev)
+        send_t = torch.empty((2, cap), dtype=torch.int32, device=dev)
+        send_id = torch.empty((2, cap), dtype=torch.int64, device=dev)
+        counts = torch.zeros(2, dtype=torch.int32, device=dev)
+        ctx.halo_pack(x_own, types_own, ids_own, dec.axis, pack_geometry(dec, rank), cap,
+                      x_local, send_x, send_t, send_id, counts)
+        return x_local, send_x, send_t, send_id, [int(v) for v in counts.cpu()]
+
+    return pack
+
+
+def halo_exchange_device(dec: SlabDecomposition, x_own, types_own, ids_own, rank: int, pack,
+                         group=None):
+    """The halo exchange on device buffers. ``pack`` (``device_pack(ctx)`` on
+    a GPU) writes the rank's owned atoms in its local frame and its two face
+    sets, already in the receivers' frames; the upper set goes to rank + 1 and
+    the lower set to rank - 1 (periodic) over torch.distributed point-to-point
+    messages (NCCL between GPUs), counts first, and the received sets land
+    after the owned atoms: first the set travelling down (from rank + 1), then
+    the set travelling up (from rank - 1), the order of ``ghosts_from_global``.
+    Returns the local system (positions, species, global indices; owned atoms
+    first) on the device of x_own, and the owned count."""
+    import torch
+    import torch.distributed as dist
+    n = x_own.shape[0]
+    x_local, send_x, send_t, send_id, cnt = pack(dec, x_own, types_own, ids_own, rank)
+    dev = x_own.device
+    world = dec.world
+    if world == 1:  # periodic images of its own faces, no messages
+        m = [cnt[0], cnt[1]]
+        parts = [(send_x[0, :m[0]], send_t[0, :m[0]], send_id[0, :m[0]]),
+                 (send_x[1, :m[1]], send_t[1, :m[1]], send_id[1, :m[1]])]
+        xs = torch.cat([x_local] + [p[0] for p in parts])
+        ts = torch.cat([types_own.to(torch.int32)] + [p[1] for p in parts])
+        ids = torch.cat([ids_own.to(torch.int64)] + [p[2] for p in parts])
+        return xs, ts, ids, n
+    # counts: set 1 (upper) travels up to rank + 1, set 0 (lower) down to rank - 1
+    up, down = (rank + 1) % world, (rank - 1) % world
+    c_up = torch.tensor([cnt[1]], dtype=torch.int64, device=dev)
+    c_down = torch.tensor([cnt[0]], dtype=torch.int64, device=dev)
+    r_from_below = torch.zeros(1, dtype=torch.int64, device=dev)  # rank - 1's upper set
+    r_from_above = torch.zeros(1, dtype=torch.int64, device=dev)  # rank + 1's lower set
+    # one group of point-to-point operations per phase (with NCCL a send
+    # posted alone could wait for its peer's receive behind the peer's send)
+    _p2p([dist.P2POp(dist.isend, c_up, up, group, 0),
+          dist.P2POp(dist.irecv, r_from_below, down, group, 0),
+          dist.P2POp(dist.isend, c_down, down, group, 1),
+          dist.P2POp(dist.irecv, r_from_above, up, group, 1)])
+    m_above, m_below = int(r_from_above.item()), int(r_from_below.item())
+    tot = n + m_above + m_below
+    xs = torch.empty((tot, 3), dtype=torch.float64, device=dev)
+    ts = torch.empty(tot, dtype=torch.int32, device=dev)
+    ids = torch.empty(tot, dtype=torch.int64, device=dev)
+    xs[:n].copy_(x_local)
+    ts[:n].copy_(types_own)
+    ids[:n].copy_(ids_own)
+    a0, a1 = n, n + m_above        # from rank + 1 (travelling down)
+    b0, b1 = a1, tot               # from rank - 1 (travelling up)
+    ops = []
+    for k, (buf, dst_a, dst_b) in enumerate(((send_x, xs[a0:a1], xs[b0:b1]),
+                                             (send_t, ts[a0:a1], ts[b0:b1]),
+                                             (send_id, ids[a0:a1], ids[b0:b1]))):
+        if cnt[1]:
+            ops.append(dist.P2POp(dist.isend, buf[1, :cnt[1]].contiguous(), up, group, 2 + 2 * k))
+        if m_below:
+            ops.append(dist.P2POp(dist.irecv, dst_b, down, group, 2 + 2 * k))
+        if cnt[0]:
+            ops.append(dist.P2POp(dist.isend, buf[0, :cnt[0]].contiguous(), down, group, 3 + 2 * k))
+        if m_above:
+            ops.append(dist.P2POp(dist.irecv, dst_a, up, group, 3 + 2 * k))
+    _p2p(ops)
+    return xs, ts, ids, n
+
+
+def _p2p(ops):
+    import torch.distributed as dist
+    if ops:
+        for r in dist.batch_isend_irecv(ops):
+            r.wait()
+
+
 class LibraryCompute:
     """The callback for a GPU: one library context, rebuilt for each local
     system (its atom count changes from call to call)."""

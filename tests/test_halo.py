@@ -156,3 +156,76 @@ def test_single_cutoff_shell_is_not_enough():
         xg, tg, _ = halo.ghosts_from_global(dec, X, T, r)
         _, f[sel] = halo.owned_energy_forces(dec, X[sel], T[sel], xg, tg, r, oracle_compute(TABLE))
     assert np.abs(f - f_ref).max() > 1e-3 * np.abs(f_ref).max()
+
+
+def host_pack(dec, x_own, types_own, ids_own, rank):
+    """The packing contract of tersoff_halo_pack restated on CPU tensors (the
+    GPU tests check the kernel against the host path itself): owned atoms in
+    the rank's frame, the two face sets in the receivers' frames."""
+    x = x_own.numpy()
+    u = dec.wrapped(x)
+    L, lo, hi, rg, frame, s_lo, f_lo, s_up, f_up = halo.pack_geometry(dec, rank)
+    x_local = x.copy()
+    x_local[:, dec.axis] = u - frame
+    n = len(x)
+    cap = max(n, 1)
+    send_x = np.zeros((2, cap, 3))
+    send_t = np.zeros((2, cap), dtype=np.int32)
+    send_id = np.zeros((2, cap), dtype=np.int64)
+    cnt = []
+    for k, (sel, shift, fr) in enumerate(((u - lo < rg, s_lo, f_lo), (hi - u <= rg, s_up, f_up))):
+        idx = np.nonzero(sel)[0]
+        y = x[idx].copy()
+        y[:, dec.axis] = (u[idx] + shift) - fr
+        send_x[k, :len(idx)] = y
+        send_t[k, :len(idx)] = types_own.numpy()[idx]
+        send_id[k, :len(idx)] = ids_own.numpy()[idx]
+        cnt.append(len(idx))
+    return (torch.from_numpy(x_local), torch.from_numpy(send_x), torch.from_numpy(send_t),
+            torch.from_numpy(send_id), cnt)
+
+
+def _expected_local(dec, rank):
+    sel = np.nonzero(dec.owner(X) == rank)[0]
+    xg, tg, idg = halo.ghosts_from_global(dec, X, T, rank)
+    xl, tl, _ = halo.local_system(dec, X[sel], T[sel], xg, tg, rank)
+    return sel, xl, tl, np.concatenate([sel, idg])
+
+
+def _device_worker(rank, world, port, out):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dec = halo.SlabDecomposition(BOX, world, RC, RC + 0.5)
+        sel, xl, tl, il = _expected_local(dec, rank)
+        xs, ts, ids, n = halo.halo_exchange_device(
+            dec, torch.from_numpy(X[sel]), torch.from_numpy(T[sel]),
+            torch.from_numpy(sel.astype(np.int64)), rank, host_pack)
+        out[rank] = (n == len(sel) and np.array_equal(xs.numpy(), xl)
+                     and np.array_equal(ts.numpy(), tl) and np.array_equal(ids.numpy(), il))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3, 4])
+def test_device_buffer_exchange_gloo_ranks(world):
+    # the exchange of packed buffers (halo_exchange_device) delivers, on every
+    # rank, exactly the host path's local system: owned atoms first, then the
+    # ghosts, bit for bit, in the local frame
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_device_worker, args=(world, port, out), nprocs=world, join=True,
+                       start_method="spawn")
+    assert all(out[r] for r in range(world))
+
+
+def test_device_buffer_exchange_one_rank():
+    dec = halo.SlabDecomposition(BOX, 1, RC, RC + 0.5)
+    sel, xl, tl, il = _expected_local(dec, 0)
+    xs, ts, ids, n = halo.halo_exchange_device(
+        dec, torch.from_numpy(X[sel]), torch.from_numpy(T[sel]),
+        torch.from_numpy(sel.astype(np.int64)), 0, host_pack)
+    assert n == len(sel)
+    assert np.array_equal(xs.numpy(), xl) and np.array_equal(ts.numpy(), tl)
+    assert np.array_equal(ids.numpy(), il)
