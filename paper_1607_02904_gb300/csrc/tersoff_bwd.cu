@@ -161,7 +161,7 @@ __device__ __forceinline__ Expo<T> expo_ad(T delta, T l3, int m) {
   T am1 = T(1);
   for (int s = 1; s < m; ++s) am1 *= a;
   const T am = am1 * a;
-  o.x = BM<T>::ex(am);
+  o.x = am == T(0) ? T(1) : BM<T>::ex(am);  // lambda3 = 0 (most tables): no exponential
   o.dx = T(m) * l3 * am1 * o.x;
   o.x_l = T(m) * am1 * delta * o.x;
   o.dx_l = T(m) * T(m) * am1 * (T(1) + am) * o.x;
@@ -181,17 +181,20 @@ __device__ __forceinline__ Bo<T> bond_ad(T zeta, T be, T n) {
     o.db = o.ddb = o.b_be = o.b_n = o.db_be = o.db_n = T(0);
     return o;
   }
+  // (reciprocals of 1 + u, zeta, n and beta; products in place of the divisions)
   const T L = BM<T>::ln(be * zeta);
   const T u = BM<T>::ex(n * L);
-  const T w = u / (T(1) + u);
+  const T w = u * BM<T>::rcp(T(1) + u);
   const T l1u = BM<T>::ln1p(u);
-  const T iz = T(1) / zeta;
-  o.b = BM<T>::ex(-l1u / (T(2) * n));
+  const T iz = BM<T>::rcp(zeta);
+  const T ih = T(0.5) * BM<T>::rcp(n);  // 1 / (2 n)
+  const T ibe = BM<T>::rcp(be);
+  o.b = BM<T>::ex(-l1u * ih);
   o.db = -T(0.5) * o.b * w * iz;
   o.ddb = -T(0.5) * (o.db * w + o.b * w * (n * (T(1) - w) - T(1)) * iz) * iz;
-  o.b_be = -o.b * w / (T(2) * be);
-  o.b_n = o.b * (l1u / (T(2) * n * n) - w * L / (T(2) * n));
-  const T w_be = n * w * (T(1) - w) / be;
+  o.b_be = -o.b * w * (T(0.5) * ibe);
+  o.b_n = o.b * (l1u * (T(2) * ih * ih) - w * L * ih);
+  const T w_be = n * w * (T(1) - w) * ibe;
   const T w_n = w * (T(1) - w) * L;
   o.db_be = -T(0.5) * (o.b_be * w + o.b * w_be) * iz;
   o.db_n = -T(0.5) * (o.b_n * w + o.b * w_n) * iz;
