@@ -45,7 +45,7 @@ PEAK_FP32_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x F
 PEAK_ISSUE_WARP_INST = 152 * 4 * 2.07e9  # SMs x schedulers (one warp instruction each) x clock
 # warp instructions of one force launch on this workload (ncu smsp__inst_executed.sum, the same
 # capture as the traffic); like the traffic, valid only for the sources it was taken with
-FORCE_WARP_INST = 28_019_987
+FORCE_WARP_INST = 25_185_239
 
 # Algorithmic FP32 operations of the force evaluation per unit of work
 # (additions and multiplications, an FMA counting 2; special-function ops
@@ -60,9 +60,9 @@ MUFU_SHORT, MUFU_PAIR, MUFU_TRIPLET = 1, 7, 1
 # workload, from an ncu capture (profiles/k_tersoff_si512k_mixed.md). Valid only
 # for the kernel sources it was taken with, identified by their SHA-256; once
 # those change the traffic is reported as null until it is measured again.
-FORCE_TRAFFIC_BYTES = 23_627_008 + 3_176_960
+FORCE_TRAFFIC_BYTES = 23_688_960 + 3_132_416
 FORCE_TRAFFIC_SOURCES = ("tersoff_fwd.cuh", "fwd_launch.cuh", "fwd_f32.cu")
-FORCE_TRAFFIC_SHA256 = "df2924a7a5a74c8556af056a8f8d92987ba177303853cb57d948c5f69c36bb16"
+FORCE_TRAFFIC_SHA256 = "372058d3f510b8d7b632a97c19e9fcafe683e6133f341a464f2e86400da5bb5c"
 
 
 def mufu_peak(pk):

@@ -178,11 +178,12 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restri
     if (mixed) {
       // the velocity increment from the float force pair in float (the forces
       // are float-accurate), accumulated into the double velocity; F0..2 hold
-      // the (rare) fallback-buffer forces
+      // the (rare) fallback-buffer forces, whose share of the increment is
+      // also formed in float (no FP64 operation on the common path)
       const float kf = kick == 2 ? cf.c2f[t] : cf.cf[t];
-      const float d0 = kf * sc[0] + kf * sc[3];
-      const float d1 = kf * sc[1] + kf * sc[4];
-      const float d2v = kf * sc[2] + kf * sc[5];
+      float d0 = kf * sc[0] + kf * sc[3];
+      float d1 = kf * sc[1] + kf * sc[4];
+      float d2v = kf * sc[2] + kf * sc[5];
       const bool extra = ga.flags[FLAG_EXTRA] | ga.flags[FLAG_EXTRA_STICKY];
       if (ke_row) {
         // the previous step's full velocity in float (the kinetic energy is a
@@ -198,14 +199,14 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restri
         }
         kef = cf.hmf[t] * fmaf(w0, w0, fmaf(w1, w1, w2 * w2));
       }
+      if (extra) {
+        d0 = fmaf(kf, d2f_bits(F0), d0);
+        d1 = fmaf(kf, d2f_bits(F1), d1);
+        d2v = fmaf(kf, d2f_bits(F2), d2v);
+      }
       vn0 = v0 + gather_f2d(d0);
       vn1 = v1 + gather_f2d(d1);
       vn2 = v2 + gather_f2d(d2v);
-      if (extra) {
-        vn0 = fma(kcu, F0, vn0);
-        vn1 = fma(kcu, F1, vn1);
-        vn2 = fma(kcu, F2, vn2);
-      }
     } else {
       if (ke_row) {
         // full-step velocity of the previous step
