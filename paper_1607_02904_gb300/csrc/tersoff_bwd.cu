@@ -217,6 +217,7 @@ template <class T> struct Acc<1, T> {
     for (int q = 0; q < NP; ++q) v[q] = T(0);
   }
   __device__ __forceinline__ void add(double*, int, int f, T x) { v[f] += x; }
+  __device__ __forceinline__ void add_pair(double*, int, int, int f, T x) { v[f] += x; }
   __device__ __forceinline__ void flush(double* sh, int) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -241,6 +242,20 @@ template <class T> struct Acc<2, T> {
     else if (r == 2) v[2][f] += x;
     else v[3][f] += x;
   }
+  // pair terms: record (ti, tj, tj), at [3 tj]; the mixed records (1 and 2)
+  // never receive a pair field, so their pair-only sums are never live
+  __device__ __forceinline__ void add_pair(double*, int, int tj, int f, T x) {
+    if (tj == 0) v[0][f] += x;
+    else v[3][f] += x;
+  }
+  // fields a record position can receive: m never; A, lambda1, B, lambda2,
+  // beta and n only at the pair records 0 and 3
+  static __device__ __forceinline__ constexpr bool used(int r, int f) {
+    return f != TERSOFF_P_M &&
+           (r == 0 || r == 3 || f == TERSOFF_P_GAMMA || f == TERSOFF_P_LAMBDA3 ||
+            f == TERSOFF_P_C || f == TERSOFF_P_D || f == TERSOFF_P_H || f == TERSOFF_P_R ||
+            f == TERSOFF_P_D_CUT);
+  }
   // all lanes; lanes without an atom hold zeros (ti 0)
   __device__ __forceinline__ void flush(double* sh, int ti) {
 #pragma unroll
@@ -249,6 +264,7 @@ template <class T> struct Acc<2, T> {
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
+          if (!used(r, q)) continue;
           T s = ti == tt ? v[r][q] : T(0);
           for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
           if ((threadIdx.x & 31) == 0 && s != T(0))
@@ -261,6 +277,9 @@ template <class T> struct Acc<0, T> {
   __device__ __forceinline__ void add(double* sh, int rec, int f, T x) {
     const double d = to_f64(x);
     if (d != 0.0) atomicAdd(&sh[rec * NP + f], d);
+  }
+  __device__ __forceinline__ void add_pair(double* sh, int rec, int, int f, T x) {
+    add(sh, rec, f, x);
   }
   __device__ __forceinline__ void flush(double*, int) {}
 };
@@ -384,16 +403,16 @@ __device__ __forceinline__ void atom_adjoint(const T* sraw, int ns, int ti, T hE
     const T Qdbar = -T(0.5) * bo.b * rdj;
     const T bbar = hE * Qv - T(0.5) * Qd * rdj;
     const T dbbar = -T(0.5) * Qv * zd;
-    acc.add(sgrad, p, TERSOFF_P_A, (Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
-    acc.add(sgrad, p, TERSOFF_P_LAMBDA1, (Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
-    acc.add(sgrad, p, TERSOFF_P_B, (Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
-    acc.add(sgrad, p, TERSOFF_P_LAMBDA2, (Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
-    acc.add(sgrad, p, TERSOFF_P_R, ((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_A, (Pbar * fj.fc * e1 + Pdbar * (fj.dfc - l1 * fj.fc) * e1));
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_LAMBDA1, (Pbar * (-rj * Pv) + Pdbar * (-fj.fc * Ae1 - rj * Pd)));
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_B, (Qbar * (-fj.fc * e2) + Qdbar * (-(fj.dfc - l2 * fj.fc) * e2)));
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_LAMBDA2, (Qbar * (-rj * Qv) + Qdbar * (fj.fc * Be2 - rj * Qd)));
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_R, ((Pbar * fj.fc_R + Pdbar * (fj.dfc_R - l1 * fj.fc_R)) * Ae1 -
                    (Qbar * fj.fc_R + Qdbar * (fj.dfc_R - l2 * fj.fc_R)) * Be2));
-    acc.add(sgrad, p, TERSOFF_P_D_CUT, ((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_D_CUT, ((Pbar * fj.fc_D + Pdbar * (fj.dfc_D - l1 * fj.fc_D)) * Ae1 -
                    (Qbar * fj.fc_D + Qdbar * (fj.dfc_D - l2 * fj.fc_D)) * Be2));
-    acc.add(sgrad, p, TERSOFF_P_BETA, (bbar * bo.b_be + dbbar * bo.db_be));
-    acc.add(sgrad, p, TERSOFF_P_N, (bbar * bo.b_n + dbbar * bo.db_n));
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_BETA, (bbar * bo.b_be + dbbar * bo.db_be));
+    acc.add_pair(sgrad, p, tj, TERSOFF_P_N, (bbar * bo.b_n + dbbar * bo.db_n));
     const T zbar = bbar * bo.db + dbbar * bo.ddb;
     const T zdbar = -T(0.5) * Qv * bo.db;
     if (zbar == T(0) && zdbar == T(0)) continue;
