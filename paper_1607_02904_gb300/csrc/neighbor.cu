@@ -345,13 +345,45 @@ __global__ void __launch_bounds__(128) k_neigh(
 
 // Reverse slots: for each short-list entry (j -> i), the slot of j in i's
 // short list (255 if absent), used to gather forces without atomics.
+// The first RU entries of j's list, and the first RU entries of each of those
+// neighbours' lists, are requested together (every column has at least 8
+// slots, so the loads are in bounds; entries at or beyond a count are only
+// compared, never followed); longer lists finish with the loop below.
+constexpr int RU = 4;
 __global__ void k_rev(int n, const uint32_t* __restrict__ shortl, const int* __restrict__ zcnt,
                       int cap, uint8_t* __restrict__ rev, int* __restrict__ flags) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int z = zcnt[j];
   z = z < cap ? z : cap;
-  for (int p = 0; p < z; ++p) {
+  int ii[RU], zi[RU];
+  uint32_t ent[RU][RU];
+#pragma unroll
+  for (int p = 0; p < RU; ++p) {
+    const uint32_t e = shortl[(size_t)p * n + j];
+    ii[p] = p < z ? (int)(e & ENTRY_JMASK) : j;
+  }
+#pragma unroll
+  for (int p = 0; p < RU; ++p) {
+    zi[p] = zcnt[ii[p]];
+#pragma unroll
+    for (int s = 0; s < RU; ++s) ent[p][s] = shortl[(size_t)s * n + ii[p]];
+  }
+#pragma unroll
+  for (int p = 0; p < RU; ++p) {
+    if (p >= z) break;
+    const int i = ii[p];
+    const int zz = zi[p] < cap ? zi[p] : cap;
+    int q = 255;
+#pragma unroll
+    for (int s = RU - 1; s >= 0; --s)
+      if (s < zz && (int)(ent[p][s] & ENTRY_JMASK) == j) q = s;
+    for (int s = RU; q == 255 && s < zz; ++s)
+      if ((int)(shortl[(size_t)s * n + i] & ENTRY_JMASK) == j) q = s;
+    if (q == 255) atomicOr(&flags[FLAG_REV_MISS], 1);
+    rev[(size_t)p * n + j] = (uint8_t)q;
+  }
+  for (int p = RU; p < z; ++p) {
     const int i = (int)(shortl[(size_t)p * n + j] & ENTRY_JMASK);
     int zi = zcnt[i];
     zi = zi < cap ? zi : cap;

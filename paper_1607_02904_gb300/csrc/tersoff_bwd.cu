@@ -209,6 +209,17 @@ __device__ __forceinline__ Bo<T> bond_ad(T zeta, T be, T n) {
 // NS == 1: one record. NS == 2 (mixed path): the 4 records (ti, *, *) of the
 // thread's centre species, summed once per centre species. Otherwise:
 // per-block shared accumulators with shared-memory atomics.
+// the fields a three-body term adds to, in the order of Acc::add_triplet
+__host__ __device__ constexpr int triplet_field(int k) {
+  return k == 0   ? TERSOFF_P_R
+         : k == 1 ? TERSOFF_P_D_CUT
+         : k == 2 ? TERSOFF_P_GAMMA
+         : k == 3 ? TERSOFF_P_C
+         : k == 4 ? TERSOFF_P_D
+         : k == 5 ? TERSOFF_P_H
+                  : TERSOFF_P_LAMBDA3;
+}
+
 template <int NS, class T> struct Acc;
 template <class T> struct Acc<1, T> {
   T v[NP];
@@ -218,6 +229,10 @@ template <class T> struct Acc<1, T> {
   }
   __device__ __forceinline__ void add(double*, int, int f, T x) { v[f] += x; }
   __device__ __forceinline__ void add_pair(double*, int, int, int f, T x) { v[f] += x; }
+  __device__ __forceinline__ void add_triplet(double*, int, const T (&x)[7]) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) v[triplet_field(k)] += x[k];
+  }
   __device__ __forceinline__ void flush(double* sh, int) {
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -241,6 +256,24 @@ template <class T> struct Acc<2, T> {
     else if (r == 1) v[1][f] += x;
     else if (r == 2) v[2][f] += x;
     else v[3][f] += x;
+  }
+  // one three-body term's seven fields: one choice of the record position
+  // for all of them
+  __device__ __forceinline__ void add_triplet(double*, int rec, const T (&x)[7]) {
+    const int r = rec & 3;
+    if (r == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[0][triplet_field(k)] += x[k];
+    } else if (r == 1) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[1][triplet_field(k)] += x[k];
+    } else if (r == 2) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[2][triplet_field(k)] += x[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) v[3][triplet_field(k)] += x[k];
+    }
   }
   // pair terms: record (ti, tj, tj), at [3 tj]; the mixed records (1 and 2)
   // never receive a pair field, so their pair-only sums are never live
@@ -280,6 +313,10 @@ template <class T> struct Acc<0, T> {
   }
   __device__ __forceinline__ void add_pair(double* sh, int rec, int, int f, T x) {
     add(sh, rec, f, x);
+  }
+  __device__ __forceinline__ void add_triplet(double* sh, int rec, const T (&x)[7]) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) add(sh, rec, triplet_field(k), x[k]);
   }
   __device__ __forceinline__ void flush(double*, int) {}
 };
@@ -443,13 +480,14 @@ __device__ __forceinline__ void atom_adjoint(const T* sraw, int ns, int ti, T hE
       const T Gdbar = zdbar * fk.fc * csd * ex.x;
       const T Xbar = zbar * fk.fc * an.g + zdbar * (fk.dfc * rdk * an.g + fk.fc * an.dg * csd);
       const T Xdbar = zdbar * fk.fc * an.g * dld;
-      acc.add(sgrad, q, TERSOFF_P_R, (F3bar * fk.fc_R + F3dbar * fk.dfc_R));
-      acc.add(sgrad, q, TERSOFF_P_D_CUT, (F3bar * fk.fc_D + F3dbar * fk.dfc_D));
-      acc.add(sgrad, q, TERSOFF_P_GAMMA, (Gbar * an.g_ga + Gdbar * an.dg_ga));
-      acc.add(sgrad, q, TERSOFF_P_C, (Gbar * an.g_c + Gdbar * an.dg_c));
-      acc.add(sgrad, q, TERSOFF_P_D, (Gbar * an.g_d + Gdbar * an.dg_d));
-      acc.add(sgrad, q, TERSOFF_P_H, (Gbar * an.g_h + Gdbar * an.dg_h));
-      acc.add(sgrad, q, TERSOFF_P_LAMBDA3, (Xbar * ex.x_l + Xdbar * ex.dx_l));
+      const T tb[7] = {F3bar * fk.fc_R + F3dbar * fk.dfc_R,  // R
+                       F3bar * fk.fc_D + F3dbar * fk.dfc_D,  // D
+                       Gbar * an.g_ga + Gdbar * an.dg_ga,    // gamma
+                       Gbar * an.g_c + Gdbar * an.dg_c,      // c
+                       Gbar * an.g_d + Gdbar * an.dg_d,      // d
+                       Gbar * an.g_h + Gdbar * an.dg_h,      // h
+                       Xbar * ex.x_l + Xdbar * ex.dx_l};     // lambda3
+      acc.add_triplet(sgrad, q, tb);
     }
   }
 }
