@@ -565,13 +565,16 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
       b.pz = (wz - b.uz * b.rd) * ir;
       return true;
     };
-    // cache the bonds inside the filter radius when they fit
+    // cache the bonds inside the filter radius when they fit; mark them in a
+    // bit mask over the list (its first 64 entries)
     constexpr int ZB = BwdBlock<T>::slots;
     int z = 0;
-    for (int s = 0; s < c && z <= ZB; ++s) {
+    unsigned long long kept = 0ull;
+    for (int s = 0; s < c; ++s) {
       BondD<T> b;
       if (!from_list(s, b)) continue;
       if (z < ZB) put_slot<T>(slots, z, b);
+      if (s < 64) kept |= 1ull << s;
       ++z;
     }
     if (z <= ZB) {
@@ -579,6 +582,17 @@ __global__ void __launch_bounds__(BwdBlock<T>::size) k_tersoff_bwd(const __grid_
                           [&](int q, BondD<T>& b) -> bool {
                             get_slot<T>(slots, q, b);
                             return true;
+                          },
+                          acc, sgrad);
+    } else if (c <= 64) {
+      // more bonds than slots: the q-th marked entry, formed again from the list
+      const unsigned lo = (unsigned)kept, hi = (unsigned)(kept >> 32);
+      const int nlo = __popc(lo);
+      atom_adjoint<T, NS>(sraw, ns, ti, hE, z,
+                          [&](int q, BondD<T>& b) -> bool {
+                            const int s = q < nlo ? (int)__fns(lo, 0, q + 1)
+                                                  : 32 + (int)__fns(hi, 0, q - nlo + 1);
+                            return from_list(s, b);
                           },
                           acc, sgrad);
     } else {
