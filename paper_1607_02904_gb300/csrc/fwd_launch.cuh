@@ -97,7 +97,8 @@ inline int force_grid(const Ctx* c, int zc, int evm) {
   const int full = (c->n + BLOCK - 1) / BLOCK;
   if (c->opt_waves <= 0 || c->n_sm <= 0) return full;
   // the blocks of this instance resident on one SM (its launch bound)
-  const int resident = c->n_sm * fwd_min_blocks(zc <= 4 ? 4 : 8, zc <= 4 ? evm : 2);
+  const int resident = c->n_sm * fwd_min_blocks(zc <= 4 ? 4 : 8, zc <= 4 ? evm : 2,
+                                                c->precision == TERSOFF_FP64);
   const int g = c->opt_waves * resident;
   return g < full ? g : full;
 }
