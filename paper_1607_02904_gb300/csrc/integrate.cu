@@ -235,11 +235,56 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restri
   }
 }
 
-// closing half kick with gathered forces, which are also written to f
+// closing half kick with gathered forces, which are also written to f.
+// MG: the mixed path's gathered forces (float slots, compensated sums): the
+// force is the float pair carried into double (one rounding), the velocity
+// increment is formed in float as in k_step, and the kinetic energy in float
+// with a compensated block sum; otherwise all in double.
+template <bool MG>
 __global__ void k_final_kick(GatherArgs ga, const int* __restrict__ types,
                              double* __restrict__ v, double* __restrict__ f, const __grid_constant__ Coef cf,
                              double* ke_row) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (MG) {
+    float kef = 0.0f;
+    if (i < ga.n) {
+      const int t = types[i];
+      const size_t b = 3 * (size_t)i;
+      const double v0 = v[b], v1 = v[b + 1], v2 = v[b + 2];
+      double E0, E1, E2;  // fallback-buffer forces (zero unless flagged)
+      float sc[6];
+      gather_force(ga, i, E0, E1, E2, sc);
+      const bool extra = ga.flags[FLAG_EXTRA] | ga.flags[FLAG_EXTRA_STICKY];
+      const float kf = cf.cf[t];
+      float d0 = kf * sc[0] + kf * sc[3];
+      float d1 = kf * sc[1] + kf * sc[4];
+      float d2 = kf * sc[2] + kf * sc[5];
+      double F0 = gather_f2d(sc[0]) + gather_f2d(sc[3]);
+      double F1 = gather_f2d(sc[1]) + gather_f2d(sc[4]);
+      double F2 = gather_f2d(sc[2]) + gather_f2d(sc[5]);
+      if (extra) {
+        d0 = fmaf(kf, d2f_bits(E0), d0);
+        d1 = fmaf(kf, d2f_bits(E1), d1);
+        d2 = fmaf(kf, d2f_bits(E2), d2);
+        F0 += E0;
+        F1 += E1;
+        F2 += E2;
+      }
+      const double w0 = v0 + gather_f2d(d0), w1 = v1 + gather_f2d(d1), w2 = v2 + gather_f2d(d2);
+      f[b] = F0;
+      f[b + 1] = F1;
+      f[b + 2] = F2;
+      v[b] = w0;
+      v[b + 1] = w1;
+      v[b + 2] = w2;
+      if (ke_row) {
+        const float u0 = d2f_bits(w0), u1 = d2f_bits(w1), u2 = d2f_bits(w2);
+        kef = cf.hmf[t] * fmaf(u0, u0, fmaf(u1, u1, u2 * u2));
+      }
+    }
+    if (ke_row) block_sum_add_f(kef, ke_row);
+    return;
+  }
   double ke = 0.0;
   if (i < ga.n) {
     const int t = types[i];
@@ -373,8 +418,11 @@ int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick,
 
 int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t s) {
   const int B = c->opt_block;
-  k_final_kick<<<(c->n + B - 1) / B, B, 0, s>>>(make_gather(c), c->d_types, v, f, c->coef,
-                                                  ke_row);
+  const GatherArgs ga = make_gather(c);
+  if (!ga.fp64 && !ga.atomic_mode)
+    k_final_kick<true><<<(c->n + B - 1) / B, B, 0, s>>>(ga, c->d_types, v, f, c->coef, ke_row);
+  else
+    k_final_kick<false><<<(c->n + B - 1) / B, B, 0, s>>>(ga, c->d_types, v, f, c->coef, ke_row);
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

@@ -66,12 +66,25 @@ __global__ void k_bin(int n, const double* __restrict__ x, const __grid_constant
       finite = false;
       xa = 0.0;
     }
-    const double k = floor(xa * g.invL[a]);  // periodic image
-    const double w = xa - g.L[a] * k;
-    int c = (int)(w * g.invh[a]);
-    c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-    // origin = image corner of the cell; offsets x - o start inside the cell
-    const double o = fma(k, g.L[a], c * g.h[a]);
+    // periodic image k = floor(x / L) and the wrapped coordinate w; inside
+    // the box (0 <= x/L < 1, tested on the bits of the double: no FP64
+    // operation) k = 0 and w = x, the values the general formulas give there
+    const double u = xa * g.invL[a];
+    const long long ub = __double_as_longlong(u);
+    // origin o = image corner of the cell; offsets x - o start inside the cell
+    int c;
+    double o;
+    if (ub >= 0 && ub < 0x3FF0000000000000ll) {
+      c = (int)(xa * g.invh[a]);
+      c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+      o = c * g.h[a];  // = fma(0, L, c h)
+    } else {
+      const double k = floor(u);
+      const double w = xa - g.L[a] * k;
+      c = (int)(w * g.invh[a]);
+      c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+      o = fma(k, g.L[a], c * g.h[a]);
+    }
     origin[3 * (size_t)i + a] = o;
     qorg[3 * (size_t)i + a] = 6755399441055744.0 - o * scale;
     c3[a] = c;
