@@ -337,6 +337,38 @@ def test_md_mixed_energy_conservation_and_host_api(T):
     ctx2.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_md_host_buffers_pinned_and_pageable_equal_device(T, prec):
+    # the host-buffer call with page-locked and with pageable host arrays
+    # gives the device call's state bit for bit (the copies are exact, and
+    # gather mode sums in a fixed order)
+    x, v, t, box = _md_inputs(ncell=4, seed=53)
+    table = si_table()
+    mass = [W.MASS_AMU["Si"]]
+    runs = []
+    for mode in ("device", "pinned", "pageable"):
+        ctx = T.Context(prec)
+        ctx.params(table)
+        xd, vd = dev(x), dev(v)
+        ctx.neighbor_build(xd, dev(t, torch.int32), box, RC + 1.0)
+        fd = torch.zeros_like(xd)
+        ctx.compute(xd, None, fd)
+        if mode == "device":
+            ctx.md_step(xd, vd, fd, mass, 0.001, 20, 10)
+            torch.cuda.synchronize()
+            runs.append([a.cpu().numpy() for a in (xd, vd, fd)])
+        else:
+            hs = [a.cpu() for a in (xd, vd, fd)]
+            if mode == "pinned":
+                hs = [a.pin_memory() for a in hs]
+            ctx.md_step_host(hs[0], hs[1], hs[2], mass, 0.001, 20, 10)
+            runs.append([a.numpy().copy() for a in hs])
+        ctx.close()
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b)
+
+
 def test_md_graph_replay_matches_eager(T):
     # the same FP64 MD through direct launches and through a replayed CUDA graph
     x, v, t, box = _md_inputs(ncell=4, seed=52)
