@@ -60,24 +60,24 @@ void launch_t(Ctx* c, const FwdArgs<T>& a, int grid, cudaStream_t s) {
   const int evm = ev_mode<T, BATCH>(a);
   if (ZC == 4 && !BATCH && evm == 0) {
     if (c->has_lam3)
-      k_tersoff<T, NS, ZC, 1, false, false, 0><<<grid, BLOCK, 0, s>>>(a);
+      launch_pdl(k_tersoff<T, NS, ZC, 1, false, false, 0>, grid, BLOCK, 0, s, a);
     else if (c->sym_table)
-      k_tersoff<T, NS, ZC, 2, false, false, 0><<<grid, BLOCK, 0, s>>>(a);
+      launch_pdl(k_tersoff<T, NS, ZC, 2, false, false, 0>, grid, BLOCK, 0, s, a);
     else
-      k_tersoff<T, NS, ZC, 0, false, false, 0><<<grid, BLOCK, 0, s>>>(a);
+      launch_pdl(k_tersoff<T, NS, ZC, 0, false, false, 0>, grid, BLOCK, 0, s, a);
   } else if (ZC == 4 && !BATCH && evm == 1) {
     if (c->has_lam3)
-      k_tersoff<T, NS, ZC, 1, false, false, 1><<<grid, BLOCK, 0, s>>>(a);
+      launch_pdl(k_tersoff<T, NS, ZC, 1, false, false, 1>, grid, BLOCK, 0, s, a);
     else if (c->sym_table)
-      k_tersoff<T, NS, ZC, 2, false, false, 1><<<grid, BLOCK, 0, s>>>(a);
+      launch_pdl(k_tersoff<T, NS, ZC, 2, false, false, 1>, grid, BLOCK, 0, s, a);
     else
-      k_tersoff<T, NS, ZC, 0, false, false, 1><<<grid, BLOCK, 0, s>>>(a);
+      launch_pdl(k_tersoff<T, NS, ZC, 0, false, false, 1>, grid, BLOCK, 0, s, a);
   } else if (c->has_lam3) {
-    k_tersoff<T, NS, ZC, 1, BATCH><<<grid, BLOCK, 0, s>>>(a);
+    launch_pdl(k_tersoff<T, NS, ZC, 1, BATCH>, grid, BLOCK, 0, s, a);
   } else if (c->sym_table) {
-    k_tersoff<T, NS, ZC, 2, BATCH><<<grid, BLOCK, 0, s>>>(a);
+    launch_pdl(k_tersoff<T, NS, ZC, 2, BATCH>, grid, BLOCK, 0, s, a);
   } else {
-    k_tersoff<T, NS, ZC, 0, BATCH><<<grid, BLOCK, 0, s>>>(a);
+    launch_pdl(k_tersoff<T, NS, ZC, 0, BATCH>, grid, BLOCK, 0, s, a);
   }
   c->launches++;
 }

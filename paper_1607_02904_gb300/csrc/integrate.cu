@@ -150,6 +150,7 @@ template <bool MG, bool KE>
 __global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restrict__ x,
                        double* __restrict__ v, const double* __restrict__ f, const __grid_constant__ Coef cf,
                        double dt, int kick, int do_pack, double* ke_row_, double* acc_zero) {
+  pdl_wait();  // the previous kernel's writes (a launch with launch_pdl)
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int gather = MG ? 1 : gather_;
   double* const ke_row = MG ? (KE ? ke_row_ : nullptr) : ke_row_;
@@ -402,14 +403,15 @@ int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick,
   const int grid = (c->n + B - 1) / B;
   if (kick == 2 && !ga.fp64 && !ga.atomic_mode) {
     if (ke_row)
-      k_step<true, true><<<grid, B, 0, s>>>(make_pack(c, true), ga, 1, x, v, f, c->coef, dt, kick,
-                                            pack ? 1 : 0, ke_row, acc_zero);
+      TGB_CUDA(c, launch_pdl(k_step<true, true>, grid, B, 0, s, make_pack(c, true), ga, 1, x, v,
+                             f, c->coef, dt, kick, pack ? 1 : 0, ke_row, acc_zero));
     else
-      k_step<true, false><<<grid, B, 0, s>>>(make_pack(c, true), ga, 1, x, v, f, c->coef, dt, kick,
-                                             pack ? 1 : 0, nullptr, acc_zero);
+      TGB_CUDA(c, launch_pdl(k_step<true, false>, grid, B, 0, s, make_pack(c, true), ga, 1, x, v,
+                             f, c->coef, dt, kick, pack ? 1 : 0, (double*)nullptr, acc_zero));
   } else {
-    k_step<false, false><<<grid, B, 0, s>>>(make_pack(c, true), ga, kick == 2 ? 1 : 0, x, v, f,
-                                            c->coef, dt, kick, pack ? 1 : 0, ke_row, acc_zero);
+    TGB_CUDA(c, launch_pdl(k_step<false, false>, grid, B, 0, s, make_pack(c, true), ga,
+                           kick == 2 ? 1 : 0, x, v, f, c->coef, dt, kick, pack ? 1 : 0, ke_row,
+                           acc_zero));
   }
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());

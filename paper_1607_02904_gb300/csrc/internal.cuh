@@ -288,6 +288,30 @@ constexpr int ACC_LEN = 8 * ACC_STRIDE;   // one accumulator row
 
 // The TERSOFF_ABLATE_COMP_ATOM_SUMS variant is active: mixed path, one
 // species, a single system. Its force kernel scatters with FP64 atomics.
+// Programmatic dependent launch: a kernel launched with launch_pdl may be
+// scheduled while the previous kernel on its stream drains; it calls
+// pdl_wait() before touching any memory, which returns once that kernel has
+// completed and its writes are visible (at once when there is no such
+// dependency). The launch latency between the two kernels overlaps the first
+// one's last blocks.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 inline bool comp_atom_sums(const Ctx* c) {
   return (c->ablate & TERSOFF_ABLATE_COMP_ATOM_SUMS) && c->precision == TERSOFF_MIXED &&
          c->ns == 1 && c->n_sys == 0;

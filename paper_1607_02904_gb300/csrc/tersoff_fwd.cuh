@@ -783,6 +783,7 @@ __global__ void __launch_bounds__(BLOCK, fwd_min_blocks(ZC, EV, sizeof(T) == 8))
     k_tersoff(const __grid_constant__ FwdArgs<T> a) {
   static_assert(!(CS && BATCH), "compensated per-atom sums: single systems only");
   static_assert(EV == 2 || !BATCH, "batches need the per-atom energy and virial");
+  pdl_wait();  // the previous kernel's writes (a launch with launch_pdl)
   constexpr int SNS = NS > 1 ? NS : (NS == 1 ? 1 : TERSOFF_MAX_SPECIES);
   constexpr int SREC = NS == 1 ? 1 : SNS * SNS * SNS * RSTRIDE;
   __shared__ T srec_s[SREC];
