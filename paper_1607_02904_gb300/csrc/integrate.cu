@@ -80,6 +80,7 @@ __device__ __forceinline__ void track_max(const PackArgs& a, float d2) {
 }
 
 __global__ void k_pack(PackArgs a, const double* __restrict__ x) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float d2 = 0.0f;
   if (i < a.n) {
@@ -245,6 +246,7 @@ template <bool MG>
 __global__ void k_final_kick(GatherArgs ga, const int* __restrict__ types,
                              double* __restrict__ v, double* __restrict__ f, const __grid_constant__ Coef cf,
                              double* ke_row) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (MG) {
     float kef = 0.0f;
@@ -390,7 +392,7 @@ PackArgs make_pack(Ctx* c, bool track, bool build = false) {
 int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s) {
   if (c->n == 0) return TERSOFF_OK;
   const int B = c->opt_block;
-  k_pack<<<(c->n + B - 1) / B, B, 0, s>>>(make_pack(c, !build, build), x);
+  TGB_CUDA(c, launch_pdl(k_pack, (c->n + B - 1) / B, B, 0, s, make_pack(c, !build, build), x));
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;
@@ -422,9 +424,9 @@ int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t
   const int B = c->opt_block;
   const GatherArgs ga = make_gather(c);
   if (!ga.fp64 && !ga.atomic_mode)
-    k_final_kick<true><<<(c->n + B - 1) / B, B, 0, s>>>(ga, c->d_types, v, f, c->coef, ke_row);
+    TGB_CUDA(c, launch_pdl(k_final_kick<true>, (c->n + B - 1) / B, B, 0, s, ga, c->d_types, v, f, c->coef, ke_row));
   else
-    k_final_kick<false><<<(c->n + B - 1) / B, B, 0, s>>>(ga, c->d_types, v, f, c->coef, ke_row);
+    TGB_CUDA(c, launch_pdl(k_final_kick<false>, (c->n + B - 1) / B, B, 0, s, ga, c->d_types, v, f, c->coef, ke_row));
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());
   return TERSOFF_OK;

@@ -55,6 +55,7 @@ __global__ void k_bin(int n, const double* __restrict__ x, const __grid_constant
                       double scale, int* __restrict__ cell_of, int* __restrict__ cell_count,
                       double* __restrict__ origin, double* __restrict__ qorg,
                       int* __restrict__ flags) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const GridDev& g = grid_of<BATCH>(g1, geo, atom_sys, i);
@@ -128,6 +129,7 @@ __device__ int block_excl_scan(int v, int* total) {
 
 __global__ void k_scan_tiles(const int* __restrict__ in, int m, int* __restrict__ out,
                              int* __restrict__ tile_sums) {
+  pdl_wait();
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
   int v[SCAN_ITEMS];
   int s = 0;
@@ -146,6 +148,7 @@ __global__ void k_scan_tiles(const int* __restrict__ in, int m, int* __restrict_
 
 // single block: exclusive scan of the tile sums in place
 __global__ void k_scan_sums(int* __restrict__ sums, int nt) {
+  pdl_wait();
   int carry = 0;
   for (int base = 0; base < nt; base += SCAN_BLOCK) {
     int idx = base + threadIdx.x;
@@ -159,6 +162,7 @@ __global__ void k_scan_sums(int* __restrict__ sums, int nt) {
 
 __global__ void k_scan_add(int* __restrict__ out, int m, const int* __restrict__ tile_off,
                            int* __restrict__ fill) {
+  pdl_wait();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= m) return;
   int v = out[idx] + tile_off[idx / SCAN_TILE];
@@ -168,6 +172,7 @@ __global__ void k_scan_add(int* __restrict__ out, int m, const int* __restrict__
 
 __global__ void k_scatter(int n, const int* __restrict__ cell_of, int* __restrict__ fill,
                           int* __restrict__ cell_atoms) {
+  pdl_wait();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   int slot = atomicAdd(&fill[cell_of[i]], 1);
@@ -208,6 +213,7 @@ struct Radii {
 // order, then cell order) does not depend on the scatter's atomic order.
 __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
                             int* __restrict__ cell_atoms) {
+  pdl_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const int s0 = cell_start[c], s1 = cell_start[c + 1];
@@ -227,6 +233,7 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
 // the bits of 4 j + species (j < 2^26, at most 4 species).
 __global__ void k_cell_pos(int n, const int* __restrict__ cell_atoms,
                            const float4* __restrict__ pos32, float4* __restrict__ posc) {
+  pdl_wait();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int j = cell_atoms[s];
@@ -246,6 +253,7 @@ __global__ void __launch_bounds__(128) k_neigh(
     const __grid_constant__ Radii core, int ns,
     uint32_t* __restrict__ shortl, int* __restrict__ zcnt, int* __restrict__ bucket,
     uint8_t* __restrict__ zwa, int* __restrict__ flags) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = i < n;
   int count = 0;
@@ -365,6 +373,7 @@ __global__ void __launch_bounds__(128) k_neigh(
 constexpr int RU = 4;
 __global__ void k_rev(int n, const uint32_t* __restrict__ shortl, const int* __restrict__ zcnt,
                       int cap, uint8_t* __restrict__ rev, int* __restrict__ flags) {
+  pdl_wait();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   int z = zcnt[j];
@@ -475,26 +484,26 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   if (n > 0) TGB_CUDA(c, cudaMemsetAsync(c->d_kmask, 0xff, sizeof(unsigned long long) * n, s));
   if (n > 0) {
     if (batch)
-      k_bin<true><<<nb, B, 0, s>>>(n, x, g, c->d_geo, c->d_atom_sys, scale, c->d_cell_of,
-                                   c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags);
+      TGB_CUDA(c, launch_pdl(k_bin<true>, nb, B, 0, s, n, x, g, c->d_geo, c->d_atom_sys, scale, c->d_cell_of,
+                                   c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags));
     else
-      k_bin<false><<<nb, B, 0, s>>>(n, x, g, nullptr, nullptr, scale, c->d_cell_of,
-                                    c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags);
+      TGB_CUDA(c, launch_pdl(k_bin<false>, nb, B, 0, s, n, x, g, nullptr, nullptr, scale, c->d_cell_of,
+                                    c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags));
     c->launches++;
     int st = launch_pack_positions(c, x, true, s);
     if (st) return st;
   }
   const int m = (int)ncell + 1;
   const int ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
-  k_scan_tiles<<<ntiles, SCAN_BLOCK, 0, s>>>(c->d_cell_count, m, c->d_cell_start, c->d_scan_tmp);
-  k_scan_sums<<<1, SCAN_BLOCK, 0, s>>>(c->d_scan_tmp, ntiles);
-  k_scan_add<<<(m + 255) / 256, 256, 0, s>>>(c->d_cell_start, m, c->d_scan_tmp, c->d_cell_fill);
+  TGB_CUDA(c, launch_pdl(k_scan_tiles, ntiles, SCAN_BLOCK, 0, s, c->d_cell_count, m, c->d_cell_start, c->d_scan_tmp));
+  TGB_CUDA(c, launch_pdl(k_scan_sums, 1, SCAN_BLOCK, 0, s, c->d_scan_tmp, ntiles));
+  TGB_CUDA(c, launch_pdl(k_scan_add, (m + 255) / 256, 256, 0, s, c->d_cell_start, m, c->d_scan_tmp, c->d_cell_fill));
   c->launches += 3;
   if (n > 0) {
-    k_scatter<<<nb, B, 0, s>>>(n, c->d_cell_of, c->d_cell_fill, c->d_cell_atoms);
-    k_cell_sort<<<(int)((ncell + 255) / 256), 256, 0, s>>>((int)ncell, c->d_cell_start,
-                                                           c->d_cell_atoms);
-    k_cell_pos<<<nb, B, 0, s>>>(n, c->d_cell_atoms, c->d_pos32, c->d_posc);
+    TGB_CUDA(c, launch_pdl(k_scatter, nb, B, 0, s, n, c->d_cell_of, c->d_cell_fill, c->d_cell_atoms));
+    TGB_CUDA(c, launch_pdl(k_cell_sort, (int)((ncell + 255) / 256), 256, 0, s, (int)ncell, c->d_cell_start,
+                                                           c->d_cell_atoms));
+    TGB_CUDA(c, launch_pdl(k_cell_pos, nb, B, 0, s, n, c->d_cell_atoms, c->d_pos32, c->d_posc));
     c->launches += 3;
   }
   const double rc2 = c->r_list * c->r_list;
@@ -516,22 +525,22 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
     }
   if (n > 0) {
     if (batch)
-      k_neigh<true, false><<<(n + 127) / 128, 128, 0, s>>>(
+      TGB_CUDA(c, launch_pdl(k_neigh<true, false>, (n + 127) / 128, 128, 0, s,
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, c->d_geo,
           c->d_atom_sys, rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short,
-          c->d_zcnt, c->d_bucket, c->d_zw, c->d_flags);
+          c->d_zcnt, c->d_bucket, c->d_zw, c->d_flags));
     else if (c->ns == 1)
-      k_neigh<false, true><<<(n + 127) / 128, 128, 0, s>>>(
+      TGB_CUDA(c, launch_pdl(k_neigh<false, true>, (n + 127) / 128, 128, 0, s,
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
-          c->d_bucket, c->d_zw, c->d_flags);
+          c->d_bucket, c->d_zw, c->d_flags));
     else
-      k_neigh<false, false><<<(n + 127) / 128, 128, 0, s>>>(
+      TGB_CUDA(c, launch_pdl(k_neigh<false, false>, (n + 127) / 128, 128, 0, s,
           n, x, c->d_pos32, c->d_cell_of, c->d_cell_start, c->d_posc, g, nullptr, nullptr,
           rc2, lo2, hi2, c->cap, c->d_nbr, c->d_cnt, lim, core, c->ns, c->d_short, c->d_zcnt,
-          c->d_bucket, c->d_zw, c->d_flags);
-    k_rev<<<(n + 255) / 256, 256, 0, s>>>(n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
-                                          c->d_flags);
+          c->d_bucket, c->d_zw, c->d_flags));
+    TGB_CUDA(c, launch_pdl(k_rev, (n + 255) / 256, 256, 0, s, n, c->d_short, c->d_zcnt, c->zs_cap, c->d_rev,
+                                          c->d_flags));
     c->launches += 2;
   }
   TGB_CUDA(c, cudaGetLastError());
