@@ -45,7 +45,7 @@ PEAK_FP32_TFLOPS_DERIVED = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x F
 PEAK_ISSUE_WARP_INST = 152 * 4 * 2.07e9  # SMs x schedulers (one warp instruction each) x clock
 # warp instructions of one force launch on this workload (ncu smsp__inst_executed.sum, the same
 # capture as the traffic); like the traffic, valid only for the sources it was taken with
-FORCE_WARP_INST = 25_185_239
+FORCE_WARP_INST = 25_201_239
 
 # Algorithmic FP32 operations of the force evaluation per unit of work
 # (additions and multiplications, an FMA counting 2; special-function ops
@@ -60,9 +60,9 @@ MUFU_SHORT, MUFU_PAIR, MUFU_TRIPLET = 1, 7, 1
 # workload, from an ncu capture (profiles/k_tersoff_si512k_mixed.md). Valid only
 # for the kernel sources it was taken with, identified by their SHA-256; once
 # those change the traffic is reported as null until it is measured again.
-FORCE_TRAFFIC_BYTES = 23_713_536 + 3_090_176
+FORCE_TRAFFIC_BYTES = 23_685_888 + 3_094_272
 FORCE_TRAFFIC_SOURCES = ("tersoff_fwd.cuh", "fwd_launch.cuh", "fwd_f32.cu")
-FORCE_TRAFFIC_SHA256 = "34f8607007828506fa189b5090bffe6e0de5c47e35ac9af8bb3e8e7fad1b9de8"
+FORCE_TRAFFIC_SHA256 = "6c884a64f42132bb11d2fe16641560969ee2f821eed259812eec5981debc44d5"
 
 
 def mufu_peak(pk):
