@@ -253,10 +253,6 @@ int check_ctx(Ctx* c) {
 
 using tgb::Ctx;
 
-struct tersoff_ctx {
-  Ctx impl;
-};
-
 static Ctx* C(tersoff_ctx* p) { return p ? &p->impl : nullptr; }
 
 extern "C" {
@@ -307,7 +303,7 @@ int tersoff_destroy(tersoff_ctx* p) {
   cudaDeviceSynchronize();
   void* bufs[] = {c->d_rec64, c->d_rec32, c->d_raw64, c->d_raw32, c->d_filt64, c->d_filt32, c->d_near32,
                   c->d_types, c->d_cnt, c->d_nbr, c->d_origin, c->d_cell_of, c->d_cell_count, c->d_cell_start,
-                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_pos32, c->d_posc, c->d_kmask, c->d_zw, c->d_fine, c->d_zbins, c->d_posq,
+                  c->d_cell_fill, c->d_cell_atoms, c->d_scan_tmp, c->d_bintab, c->d_pos32, c->d_posc, c->d_kmask, c->d_zw, c->d_fine, c->d_zbins, c->d_posq,
                   c->d_pos64, c->d_flags, c->d_acc, c->d_fbuf, c->d_stage, c->d_thermo,
                   c->d_coef, c->d_qorg, c->d_qref, c->d_short, c->d_zcnt, c->d_trow,
                   c->d_bucket, c->d_left, c->d_snap, c->d_rev, c->d_contrib, c->d_own,
@@ -494,6 +490,7 @@ int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, in
     return tgb::fail(c, TERSOFF_E_INVALID_ARG, "r_list is below the potential's cutoff");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = tgb::setup_grid(c, box, r_list))) return st;
+  if ((st = tgb::upload_bin_tables(c, s))) return st;
   c->n_sys = 0;
   c->n = n;
   c->r_list = r_list;

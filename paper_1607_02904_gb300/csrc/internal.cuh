@@ -144,6 +144,8 @@ struct Ctx {
   int* d_cell_fill = nullptr;     // ncell
   int* d_cell_atoms = nullptr;    // n
   int* d_scan_tmp = nullptr;
+  long long* d_bintab = nullptr;  // binning tables of the single-system grid (neighbor.cu)
+  std::vector<long long> h_bintab;
   size_t cells_alloc = 0;
   size_t atoms_alloc = 0;
   size_t nbr_alloc = 0;
@@ -329,6 +331,10 @@ int cuda_fail(Ctx* c, cudaError_t e, const char* where);
 // ------------------------------------------------------------------ launchers
 // Neighbour build (neighbor.cu). Fills d_nbr, d_cnt, d_origin; does not sync.
 int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s);
+// Per-axis binning tables of the single-system grid c->grid (cell thresholds,
+// origins and fixed-point origins), uploaded on s; called whenever that grid
+// is set up, before any build on it.
+int upload_bin_tables(Ctx* c, cudaStream_t s);
 int launch_neighbor_export(Ctx* c, int* cnt, int* nbr, int cap, cudaStream_t s);
 
 // Position packs for the force kernels (integrate.cu): fixed-point offsets
@@ -405,3 +411,8 @@ int launch_noalloc_out(Ctx* c, const double* scr, int n, double* forces, double*
                        double* virial, cudaStream_t s);
 
 }  // namespace tgb
+
+// The opaque handle of the C ABI.
+struct tersoff_ctx {
+  tgb::Ctx impl;
+};

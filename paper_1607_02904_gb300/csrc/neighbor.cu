@@ -12,6 +12,7 @@
 // An entry stores j and the stencil cell offset; with u_i = x_i - o_i the bond
 // vector is  x_j(image) - x_i = (u_j - u_i) + off * h.
 #include <cmath>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -96,7 +97,104 @@ __global__ void k_bin(int n, const double* __restrict__ x, const __grid_constant
   atomicAdd(&cell_count[cell], 1);
 }
 
-// --- exclusive scan over m ints (three passes) ---
+// Binning of a single system by table lookups. Per axis a, with C(x) the cell
+// index (int)(x / h) of k_bin and U(x) = x / L (both rounded double products,
+// non-decreasing in x), the host tabulates
+//   t[0]        the smallest double x >= 0 with U(x) >= 1: an atom is inside
+//               the box (the test of k_bin) when 0 <= bits(x) < bits(t[0]);
+//   t[c]        for 1 <= c < nc, the smallest double x with C(x) >= c: inside
+//               the box the cell is the c with t[c] <= x < t[c + 1];
+//   t[BT_O + c] the origin c h, and t[BT_Q + c] the fixed-point origin
+//               1.5 2^52 - c h 2^S, by the double operations of k_bin (c h 2^S
+//               is exact, so the fused and unfused forms agree).
+// Non-negative doubles order like their bit patterns, so the tests are
+// integer comparisons; k_bin's FP64 arithmetic remains for atoms outside the
+// box. The build's position pack (fixed-point, float and FP64 offsets,
+// displacement references) is fused in.
+constexpr int BT_O = 1024;
+constexpr int BT_Q = 2048;
+constexpr int BT_AXIS = 3072;  // 64-bit words per axis (nc <= 1024)
+
+struct BinPack {
+  const long long* tab;  // 3 x BT_AXIS words
+  float invhf[3];        // float(1 / h): the estimate the thresholds correct
+  double scale;          // 2^S
+  float inv_scale;       // 2^-S
+  const int* types;
+  int4* posq;
+  float4* pos32;
+  int4* qref;
+  dpos4* pos64;  // FP64 path only, else null
+  unsigned long long* kmask;  // set to all ones (every slot may hold a stale force)
+};
+
+__global__ void k_bin_pack(int n, const double* __restrict__ x, const __grid_constant__ GridDev g,
+                           const __grid_constant__ BinPack bp, int* __restrict__ cell_of,
+                           int* __restrict__ cell_count, double* __restrict__ origin,
+                           double* __restrict__ qorg, int* __restrict__ flags) {
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int t = bp.types[i];
+  int c3[3], q3[3];
+  double xr[3], o3[3];
+  bool finite = true;
+  const long long mb = __double_as_longlong(6755399441055744.0);
+  for (int a = 0; a < 3; ++a) {
+    const double x_in = x[3 * (size_t)i + a];
+    xr[a] = x_in;
+    double xa = x_in;
+    long long xb = __double_as_longlong(xa);
+    if ((xb & 0x7ff0000000000000ll) == 0x7ff0000000000000ll) {
+      finite = false;
+      xa = 0.0;
+      xb = 0;
+    }
+    const long long* tb = bp.tab + a * BT_AXIS;
+    int c;
+    double o, qo;
+    if (xb >= 0 && xb < __ldg(&tb[0])) {
+      // float estimate of the cell from the bits of x (truncated), then the
+      // exact cell from the thresholds
+      const int e = (int)(xb >> 52) - 1023 + 127;
+      const float xf = __uint_as_float(
+          e <= 0 ? 0u : (((uint32_t)e << 23) | (uint32_t)((xb >> 29) & 0x7fffff)));
+      c = (int)(xf * bp.invhf[a]);
+      c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+      while (c < g.nc[a] - 1 && xb >= __ldg(&tb[c + 1])) ++c;
+      while (c > 0 && xb < __ldg(&tb[c])) --c;
+      o = __longlong_as_double(__ldg(&tb[BT_O + c]));
+      qo = __longlong_as_double(__ldg(&tb[BT_Q + c]));
+    } else {
+      // k_bin's general path: periodic image and wrapped coordinate
+      const double k = floor(xa * g.invL[a]);
+      const double w = xa - g.L[a] * k;
+      c = (int)(w * g.invh[a]);
+      c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+      o = fma(k, g.L[a], c * g.h[a]);
+      qo = 6755399441055744.0 - o * bp.scale;
+    }
+    origin[3 * (size_t)i + a] = o;
+    qorg[3 * (size_t)i + a] = qo;
+    c3[a] = c;
+    o3[a] = o;
+    // the pack of k_pack at a build: q = round((x - o) 2^S) with one rounding
+    q3[a] = (int)(__double_as_longlong(fma(x_in, bp.scale, qo)) - mb);
+  }
+  if (!finite) atomicOr(&flags[FLAG_NONFINITE], 1);
+  const int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
+  cell_of[i] = cell;
+  atomicAdd(&cell_count[cell], 1);
+  const int4 pq = make_int4(q3[0], q3[1], q3[2], t);
+  bp.posq[i] = pq;
+  bp.qref[i] = pq;
+  bp.pos32[i] = make_float4((float)q3[0] * bp.inv_scale, (float)q3[1] * bp.inv_scale,
+                            (float)q3[2] * bp.inv_scale, __int_as_float(t));
+  if (bp.pos64) bp.pos64[i] = dpos4{xr[0] - o3[0], xr[1] - o3[1], xr[2] - o3[2], (double)t};
+  bp.kmask[i] = ~0ull;
+}
+
+// --- exclusive scan over m ints (tile scans, then tile offsets) ---
 __device__ __forceinline__ int warp_incl_scan(int v) {
   for (int o = 1; o < 32; o <<= 1) {
     int t = __shfl_up_sync(0xffffffffu, v, o);
@@ -127,7 +225,7 @@ __device__ int block_excl_scan(int v, int* total) {
   return res;
 }
 
-__global__ void k_scan_tiles(const int* __restrict__ in, int m, int* __restrict__ out,
+__global__ void k_scan_tiles(int* __restrict__ in, int m, int* __restrict__ out,
                              int* __restrict__ tile_sums) {
   pdl_wait();
   int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
@@ -137,6 +235,9 @@ __global__ void k_scan_tiles(const int* __restrict__ in, int m, int* __restrict_
     v[q] = (base + q < m) ? in[base + q] : 0;
     s += v[q];
   }
+  // the counts are read once: clear them for the next build's binning
+  for (int q = 0; q < SCAN_ITEMS; ++q)
+    if (base + q < m) in[base + q] = 0;
   int total;
   int pre = block_excl_scan(s, &total);
   for (int q = 0; q < SCAN_ITEMS; ++q) {
@@ -146,7 +247,7 @@ __global__ void k_scan_tiles(const int* __restrict__ in, int m, int* __restrict_
   if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
-// single block: exclusive scan of the tile sums in place
+// single block: exclusive scan of the tile sums in place (grids of many tiles)
 __global__ void k_scan_sums(int* __restrict__ sums, int nt) {
   pdl_wait();
   int carry = 0;
@@ -160,12 +261,34 @@ __global__ void k_scan_sums(int* __restrict__ sums, int nt) {
   }
 }
 
-__global__ void k_scan_add(int* __restrict__ out, int m, const int* __restrict__ tile_off,
-                           int* __restrict__ fill) {
+// Adds to each count's tile-local prefix the offset of its tile: tile_sums
+// holds either the scanned offsets (scanned = 1, after k_scan_sums) or the
+// tile totals, which the block's first warp then sums up to its tile (grids of
+// at most SCAN_SUM_TILES tiles: no separate pass). A block lies inside one
+// tile (SCAN_TILE is a multiple of the block).
+constexpr int SCAN_ADD_BLOCK = 256;
+constexpr int SCAN_SUM_TILES = 1024;
+static_assert(SCAN_TILE % SCAN_ADD_BLOCK == 0, "a scan-add block must lie inside one tile");
+__global__ void __launch_bounds__(SCAN_ADD_BLOCK) k_scan_add(int* __restrict__ out, int m,
+                                                             const int* __restrict__ tile_sums,
+                                                             int scanned, int* __restrict__ fill) {
   pdl_wait();
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ int s_off;
+  const int tile = (int)(((size_t)blockIdx.x * SCAN_ADD_BLOCK) / SCAN_TILE);
+  if (threadIdx.x < 32) {
+    int v = 0;
+    if (scanned) {
+      v = threadIdx.x == 0 ? tile_sums[tile] : 0;
+    } else {
+      for (int t = threadIdx.x; t < tile; t += 32) v += tile_sums[t];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    if (threadIdx.x == 0) s_off = v;
+  }
+  __syncthreads();
+  const int idx = blockIdx.x * SCAN_ADD_BLOCK + threadIdx.x;
   if (idx >= m) return;
-  int v = out[idx] + tile_off[idx / SCAN_TILE];
+  const int v = out[idx] + s_off;
   out[idx] = v;
   if (fill) fill[idx] = v;
 }
@@ -198,12 +321,6 @@ __device__ __forceinline__ bool exact_member(const double* __restrict__ x, int i
   return r2 <= rc2;
 }
 
-__device__ __forceinline__ void warp_atomic_max(int* dst, int v, bool active) {
-  v = active ? v : 0;
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(dst, v);
-}
-
 // squared short-list radii per (type i, type j): filter radius plus margin
 struct Radii {
   float r2[TERSOFF_MAX_SPECIES * TERSOFF_MAX_SPECIES];
@@ -211,8 +328,13 @@ struct Radii {
 
 // Atoms of each cell in ascending index order, so that list order (stencil
 // order, then cell order) does not depend on the scatter's atomic order.
+// Sorts each cell's atoms by index (insertion sort: cells hold a few atoms)
+// and writes the positions in cell order for the candidate scan: slot s of the
+// cell arrays holds the float offsets of atom j = cell_atoms[s] and, in the
+// fourth word, the bits of 4 j + species (j < 2^26, at most 4 species).
 __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
-                            int* __restrict__ cell_atoms) {
+                            int* __restrict__ cell_atoms, const float4* __restrict__ pos32,
+                            float4* __restrict__ posc) {
   pdl_wait();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
@@ -226,19 +348,11 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
     }
     cell_atoms[b + 1] = key;
   }
-}
-
-// Positions in cell order for the candidate scan: slot s of the cell arrays
-// holds the float offsets of atom j = cell_atoms[s] and, in the fourth word,
-// the bits of 4 j + species (j < 2^26, at most 4 species).
-__global__ void k_cell_pos(int n, const int* __restrict__ cell_atoms,
-                           const float4* __restrict__ pos32, float4* __restrict__ posc) {
-  pdl_wait();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int j = cell_atoms[s];
-  const float4 p = pos32[j];
-  posc[s] = make_float4(p.x, p.y, p.z, __int_as_float(4 * j + __float_as_int(p.w)));
+  for (int a = s0; a < s1; ++a) {
+    const int j = cell_atoms[a];
+    const float4 p = pos32[j];
+    posc[a] = make_float4(p.x, p.y, p.z, __int_as_float(4 * j + __float_as_int(p.w)));
+  }
 }
 
 // NS1: one species (the short-list radii are single values)
@@ -453,7 +567,54 @@ int grow(Ctx* c, T** p, size_t* have, size_t need) {
   return TERSOFF_OK;
 }
 
+// smallest double x >= 0 whose rounded product x * m is at least v (m > 0,
+// v > 0): a binary search over the bit patterns of the non-negative doubles,
+// which order like the values
+double first_at_least(double m, double v) {
+  long long lo = 0, hi = 0x7ff0000000000000ll;  // P(+0) false, P(+inf) true
+  while (hi - lo > 1) {
+    const long long mid = lo + (hi - lo) / 2;
+    double xm;
+    std::memcpy(&xm, &mid, sizeof xm);
+    if (xm * m >= v)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  double r;
+  std::memcpy(&r, &hi, sizeof r);
+  return r;
+}
+
+long long bits_of(double d) {
+  long long b;
+  std::memcpy(&b, &d, sizeof b);
+  return b;
+}
+
 }  // namespace
+
+int upload_bin_tables(Ctx* c, cudaStream_t s) {
+  const Grid& G = c->grid;
+  const double scale = ldexp(1.0, G.fix_shift);
+  std::vector<long long>& t = c->h_bintab;
+  t.assign((size_t)3 * BT_AXIS, 0);
+  for (int a = 0; a < 3; ++a) {
+    if (G.nc[a] > BT_O) return fail(c, TERSOFF_E_INVALID_ARG, "more than 1024 cells per axis");
+    long long* ta = t.data() + (size_t)a * BT_AXIS;
+    ta[0] = bits_of(first_at_least(G.invL[a], 1.0));
+    for (int q = 1; q < G.nc[a]; ++q) ta[q] = bits_of(first_at_least(G.invh[a], (double)q));
+    for (int q = 0; q < G.nc[a]; ++q) {
+      const double o = q * G.h[a];
+      ta[BT_O + q] = bits_of(o);
+      ta[BT_Q + q] = bits_of(6755399441055744.0 - o * scale);
+    }
+  }
+  if (!c->d_bintab) TGB_CUDA(c, cudaMalloc(&c->d_bintab, sizeof(long long) * t.size()));
+  TGB_CUDA(c, cudaMemcpyAsync(c->d_bintab, t.data(), sizeof(long long) * t.size(),
+                              cudaMemcpyHostToDevice, s));
+  return TERSOFF_OK;
+}
 
 int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
   const int n = c->n;
@@ -473,38 +634,58 @@ int launch_neighbor_build(Ctx* c, const double* x, cudaStream_t s) {
     TGB_CUDA(c, cudaMalloc(&c->d_cell_start, sizeof(int) * m));
     TGB_CUDA(c, cudaMalloc(&c->d_cell_fill, sizeof(int) * m));
     TGB_CUDA(c, cudaMalloc(&c->d_scan_tmp, sizeof(int) * (m / SCAN_TILE + 2)));
+    // zero once: every build's first scan pass clears the counts it read
+    TGB_CUDA(c, cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * m, s));
     c->cells_alloc = m;
   }
   GridDev g = to_dev(G);
   const int B = 256;
   const int nb = (n + B - 1) / B;
   const double scale = ldexp(1.0, G.fix_shift);
-  TGB_CUDA(c, cudaMemsetAsync(c->d_cell_count, 0, sizeof(int) * (ncell + 1), s));
   // new slots hold stale forces: every entry of every atom may be nonzero
-  if (n > 0) TGB_CUDA(c, cudaMemsetAsync(c->d_kmask, 0xff, sizeof(unsigned long long) * n, s));
+  // (k_bin_pack sets the masks of single systems)
+  if (n > 0 && batch)
+    TGB_CUDA(c, cudaMemsetAsync(c->d_kmask, 0xff, sizeof(unsigned long long) * n, s));
   if (n > 0) {
-    if (batch)
-      TGB_CUDA(c, launch_pdl(k_bin<true>, nb, B, 0, s, n, x, g, c->d_geo, c->d_atom_sys, scale, c->d_cell_of,
-                                   c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags));
-    else
-      TGB_CUDA(c, launch_pdl(k_bin<false>, nb, B, 0, s, n, x, g, nullptr, nullptr, scale, c->d_cell_of,
-                                    c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags));
     c->launches++;
-    int st = launch_pack_positions(c, x, true, s);
-    if (st) return st;
+    if (batch) {
+      // per-system grids: k_bin's arithmetic, then the build's pack
+      TGB_CUDA(c, launch_pdl(k_bin<true>, nb, B, 0, s, n, x, g, c->d_geo, c->d_atom_sys, scale,
+                             c->d_cell_of, c->d_cell_count, c->d_origin, c->d_qorg, c->d_flags));
+      int st = launch_pack_positions(c, x, true, s);
+      if (st) return st;
+    } else {
+      BinPack bp;
+      bp.tab = c->d_bintab;
+      for (int a = 0; a < 3; ++a) bp.invhf[a] = (float)G.invh[a];
+      bp.scale = scale;
+      bp.inv_scale = ldexpf(1.0f, -G.fix_shift);
+      bp.types = c->d_types;
+      bp.posq = c->d_posq;
+      bp.pos32 = c->d_pos32;
+      bp.qref = c->d_qref;
+      bp.pos64 = c->precision == TERSOFF_FP64 ? c->d_pos64 : nullptr;
+      bp.kmask = c->d_kmask;
+      TGB_CUDA(c, launch_pdl(k_bin_pack, nb, B, 0, s, n, x, g, bp, c->d_cell_of, c->d_cell_count,
+                             c->d_origin, c->d_qorg, c->d_flags));
+    }
   }
   const int m = (int)ncell + 1;
   const int ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
   TGB_CUDA(c, launch_pdl(k_scan_tiles, ntiles, SCAN_BLOCK, 0, s, c->d_cell_count, m, c->d_cell_start, c->d_scan_tmp));
-  TGB_CUDA(c, launch_pdl(k_scan_sums, 1, SCAN_BLOCK, 0, s, c->d_scan_tmp, ntiles));
-  TGB_CUDA(c, launch_pdl(k_scan_add, (m + 255) / 256, 256, 0, s, c->d_cell_start, m, c->d_scan_tmp, c->d_cell_fill));
-  c->launches += 3;
+  const int scanned = ntiles > SCAN_SUM_TILES ? 1 : 0;
+  if (scanned) {
+    TGB_CUDA(c, launch_pdl(k_scan_sums, 1, SCAN_BLOCK, 0, s, c->d_scan_tmp, ntiles));
+    c->launches++;
+  }
+  TGB_CUDA(c, launch_pdl(k_scan_add, (m + SCAN_ADD_BLOCK - 1) / SCAN_ADD_BLOCK, SCAN_ADD_BLOCK, 0, s,
+                         c->d_cell_start, m, c->d_scan_tmp, scanned, c->d_cell_fill));
+  c->launches += 2;
   if (n > 0) {
     TGB_CUDA(c, launch_pdl(k_scatter, nb, B, 0, s, n, c->d_cell_of, c->d_cell_fill, c->d_cell_atoms));
     TGB_CUDA(c, launch_pdl(k_cell_sort, (int)((ncell + 255) / 256), 256, 0, s, (int)ncell, c->d_cell_start,
-                                                           c->d_cell_atoms));
-    TGB_CUDA(c, launch_pdl(k_cell_pos, nb, B, 0, s, n, c->d_cell_atoms, c->d_pos32, c->d_posc));
-    c->launches += 3;
+                           c->d_cell_atoms, c->d_pos32, c->d_posc));
+    c->launches += 2;
   }
   const double rc2 = c->r_list * c->r_list;
   // FP32 classification band: the FP32 r^2 of a stencil candidate differs from

@@ -438,3 +438,75 @@ def test_forces_bitwise_reproducible(T, prec):
     torch.cuda.synchronize()
     assert torch.equal(f1, f2)
     ctx.close()
+
+
+def _boundary_cell():
+    """A jittered Si cell whose atoms sit on the list-cell edges of the build's
+    grid (exactly, or one ulp to either side), on the box faces (0, -0.0, L and
+    one ulp below L) and in other periodic images (shifted by -L, +L, +2L)."""
+    x, t, box = S.si_cell(n=4, amp=0.1, seed=41)
+    r_list = RC + 1.0
+    x = x.copy()
+    for a in range(3):
+        L = box[a]
+        nc = max(2, int(np.floor(L / r_list)))
+        h = L / nc
+        edges = np.array([c * h for c in range(nc + 1)])
+        for i in range(len(x)):
+            d = np.abs(edges - x[i, a])
+            k = int(np.argmin(d))
+            if d[k] < 0.15:
+                x[i, a] = edges[k]
+                sel = (i + a) % 3  # exact, one ulp below, one ulp above
+                if sel == 1:
+                    x[i, a] = np.nextafter(x[i, a], -np.inf)
+                elif sel == 2:
+                    x[i, a] = np.nextafter(x[i, a], np.inf)
+                if k == nc and (i % 2 == 0):
+                    x[i, a] = np.nextafter(L, -np.inf)
+                if k == 0 and x[i, a] == 0.0 and (i % 2 == 1):
+                    x[i, a] = -0.0
+    shifts = (-1.0, 1.0, 2.0)
+    for q, i in enumerate(range(0, len(x), 37)):
+        x[i] += shifts[q % 3] * box
+    return x, t, box, r_list
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_atoms_on_cell_edges_and_box_faces(T, prec):
+    x, t, box, r_list = _boundary_cell()
+    assert (x < 0).any() and (x >= box).any() and (np.signbit(x) & (x == 0)).any()
+    table = si_table()
+    cnt_ref, nbr_ref = oracle.neighbors(x, box, r_list)
+    ctx = T.Context(prec)
+    ctx.params(table)
+    ctx.neighbor_build(dev(x), dev(t, torch.int32), box, r_list)
+    cap = int(cnt_ref.max())
+    cnt, nbr, st = ctx.neighbor_export(cap)
+    assert st == 0
+    assert np.array_equal(cnt.cpu().numpy(), cnt_ref)
+    assert np.array_equal(nbr.cpu().numpy(), nbr_ref[:, :cap])
+    ctx.close()
+    ref = oracle.compute(x, t, box, table, oracle.neighbors(x, box, RC), nthreads=4)
+    check(prec, gpu_eval(T, prec, x, t, box, table, r_list), ref)
+
+
+def test_md_fp64_from_cell_edges_matches_oracle(T):
+    x, t, box, r_list = _boundary_cell()
+    table = si_table()
+    mass = [W.MASS_AMU["Si"]]
+    rng = np.random.Generator(np.random.Philox(42))
+    v = W.maxwell_velocities(t, np.array(mass), 1000.0, rng)
+    nsteps, every = 12, 4
+    xo, vo, _, fo = oracle.md_run(x, v, t, box, table, mass, 0.001, nsteps, r_list, every)
+    ctx = T.Context(T.FP64)
+    ctx.params(table)
+    xd, vd = dev(x), dev(v)
+    ctx.neighbor_build(xd, dev(t, torch.int32), box, r_list)
+    fd = torch.zeros_like(xd)
+    ctx.compute(xd, None, fd)
+    ctx.md_step(xd, vd, fd, mass, 0.001, nsteps, every)
+    torch.cuda.synchronize()
+    assert np.abs(xd.cpu().numpy() - xo).max() < 1e-9
+    assert np.abs(fd.cpu().numpy() - fo).max() < 1e-8 * np.abs(fo).max()
+    ctx.close()
