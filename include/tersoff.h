@@ -248,6 +248,49 @@ int tersoff_md_step_host(tersoff_ctx* ctx, double* x, double* v, double* f, int 
                          const double* mass, double dt, int nsteps, int rebuild_every,
                          double* thermo, void* stream);
 
+/* MD checkpoints (the paper has no counterpart: its runs use LAMMPS, whose
+ * restart files it does not discuss; a facility of this library for long
+ * runs such as the 10^6-step accuracy experiment of Sec. V-D).
+ *
+ * tersoff_checkpoint_save writes to the host file `path` (created or
+ * truncated) one line of JSON text, then raw little-endian arrays in this
+ * order: the species (int32, n), the parameter table (double,
+ * n_species^3 x TERSOFF_NPARAM, as given to tersoff_params), x, v and f
+ * (double, n x 3 each). The header holds the format name and version, n,
+ * n_species, the precision, the box, the list radius, the caller's step
+ * counter `step`, the number of MD steps since the last neighbour build (the
+ * phase of tersoff_md_step's fixed rebuild period), the neighbour-list
+ * capacity per atom and the context's launch
+ * options (scatter mode, tersoff_set_launch's waves, split and block, lanes,
+ * ablation flags, graphs), which decide the order of the sums. x, v, f: device,
+ * N x 3 (f = F(x), as tersoff_md_step leaves it). Requires tersoff_params and
+ * a single-system tersoff_neighbor_build on these n atoms (TERSOFF_E_STATE
+ * otherwise); TERSOFF_E_INVALID_ARG when the file cannot be written.
+ * Synchronises `stream`. */
+int tersoff_checkpoint_save(tersoff_ctx* ctx, const char* path, const double* x, const double* v,
+                            const double* f, int n, long long step, void* stream);
+
+/* Atom and species counts of the checkpoint file `path` (host outputs, either
+ * may be NULL); TERSOFF_E_INVALID_ARG when the file is missing or is not a
+ * checkpoint of this format and version. Needs no context. */
+int tersoff_checkpoint_info(const char* path, int* n, int* n_species);
+
+/* Restores a checkpoint into ctx and the caller's device arrays x, v, f
+ * (N x 3 double) and types (N int32): sets the saved precision, parameter
+ * table, launch options and list capacity, copies the state, builds the neighbour list of the saved positions
+ * with the saved box and list radius, and restores the phase of the rebuild
+ * period, so that tersoff_md_step continues the saved run. When the
+ * checkpoint was taken right after a list rebuild (zero steps since the
+ * build, as after md_step calls whose step count is a multiple of
+ * rebuild_every) the list is the one the uninterrupted run built at that
+ * step, and with the gather scatter the continued trajectory equals the
+ * uninterrupted one (the same sequence of calls) bit for bit; otherwise it
+ * agrees to rounding. *step (host, may be NULL) receives the saved step
+ * counter. n must equal the saved count; TERSOFF_E_INVALID_ARG for another
+ * count, a missing, truncated or foreign file. Synchronises `stream`. */
+int tersoff_checkpoint_load(tersoff_ctx* ctx, const char* path, double* x, double* v, double* f,
+                            int* types, int n, long long* step, void* stream);
+
 /* Autotuner (the paper has no counterpart; its launch choices are made for
  * CPUs). Times the context's launch options on its current system and keeps
  * the fastest:

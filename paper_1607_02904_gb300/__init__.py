@@ -25,6 +25,7 @@ from ._lib import (  # noqa: F401
     library_path,
     declared_symbols,
     pipe_peaks,
+    checkpoint_info,
 )
 from .params import mix_tersoff89, FIELDS  # noqa: F401
 from .autograd import TersoffSystem, TersoffBatch, TersoffFunction, energy_forces  # noqa: F401

@@ -69,6 +69,9 @@ _SIG = {
     "tersoff_timing": ([_P, _I, _P, _P], _I),
     "tersoff_pipe_peaks": ([_P, _P], _I),
     "tersoff_halo_pack": ([_P, _P, _P, _P, _I, _I, _P, _I, _P, _P, _P, _P, _P, _P], _I),
+    "tersoff_checkpoint_save": ([_P, ctypes.c_char_p, _P, _P, _P, _I, ctypes.c_longlong, _P], _I),
+    "tersoff_checkpoint_info": ([ctypes.c_char_p, _P, _P], _I),
+    "tersoff_checkpoint_load": ([_P, ctypes.c_char_p, _P, _P, _P, _P, _I, _P, _P], _I),
 }
 
 
@@ -116,6 +119,16 @@ def pipe_peaks(stream=None):
         raise TersoffError(st, "tersoff_pipe_peaks failed")
     keys = ("fp32_tflops", "fp64_tflops", "rsqrt_tops", "ex2_tops", "lg2_tops", "sms")
     return dict(zip(keys, [float(v) for v in out]))
+
+
+def checkpoint_info(path):
+    """(n, n_species) of a checkpoint file (tersoff_checkpoint_info)."""
+    lib = load()
+    n, ns = _I(), _I()
+    st = lib.tersoff_checkpoint_info(os.fsencode(path), ctypes.byref(n), ctypes.byref(ns))
+    if st != OK:
+        raise TersoffError(st, f"{path!s}: not a readable checkpoint")
+    return n.value, ns.value
 
 
 def _ptr(t):
@@ -256,6 +269,22 @@ class Context:
         self._check(self.lib.tersoff_md_step(self.h, _ptr(x), _ptr(v), _ptr(f), int(x.shape[0]),
                                              m.ctypes.data_as(_P), float(dt), int(nsteps),
                                              int(rebuild_every), _ptr(thermo), _stream(stream)))
+
+    def checkpoint_save(self, path, x, v, f, step=0, stream=None):
+        """Writes the MD state (x, v, f device tensors, the context's species,
+        table, box, list radius, precision and rebuild phase) to `path`."""
+        self._check(self.lib.tersoff_checkpoint_save(self.h, os.fsencode(path), _ptr(x), _ptr(v),
+                                                     _ptr(f), int(x.shape[0]), int(step),
+                                                     _stream(stream)))
+
+    def checkpoint_load(self, path, x, v, f, types, stream=None):
+        """Restores a checkpoint into this context and the device tensors x, v,
+        f (N x 3 float64) and types (N int32); returns the saved step."""
+        step = ctypes.c_longlong()
+        self._check(self.lib.tersoff_checkpoint_load(self.h, os.fsencode(path), _ptr(x), _ptr(v),
+                                                     _ptr(f), _ptr(types), int(x.shape[0]),
+                                                     ctypes.byref(step), _stream(stream)))
+        return step.value
 
     def md_step_host(self, x, v, f, mass, dt, nsteps, rebuild_every, thermo=None, stream=None):
         """x, v, f, thermo: host (ideally pinned) float64 torch tensors."""

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtersoff_gb300.so")
 SOURCES = ["api.cu", "neighbor.cu", "integrate.cu", "fwd_f32.cu", "fwd_f64.cu", "noalloc.cu",
-           "tersoff_bwd.cu", "peaks.cu", "fwd_f32_cs.cu", "fwd_f32_quad.cu", "halo.cu"]
+           "tersoff_bwd.cu", "peaks.cu", "fwd_f32_cs.cu", "fwd_f32_quad.cu", "halo.cu", "checkpoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

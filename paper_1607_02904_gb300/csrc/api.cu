@@ -957,6 +957,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
                     G.thermo == thermo && G.dt == dt && G.nsteps == nsteps &&
                     G.rebuild_every == rebuild_every && G.ssb0 == ssb0 &&
                     G.precision == c->precision && G.timing == c->timing &&
+                    G.decisions == tgb::bucket_decisions(c) &&
                     std::memcmp(&G.coef, &c->coef, sizeof(tgb::Coef)) == 0;
   if (!same) {
     tgb::drop_graph(c);
@@ -997,6 +998,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     G.precision = c->precision;
     G.timing = c->timing;
     G.gen = c->gen;
+    G.decisions = tgb::bucket_decisions(c);
     G.kernels = c->launches - l0;
     c->launches = l0;
     c->last_rebuilds = 0;  // nothing ran yet

@@ -135,8 +135,8 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
     launch_t<T, NS, 8, BATCH>(c, bl, c->n_sm > 0 ? c->n_sm : 152, s);
     return;
   }
-  const bool split1 = c->opt_split < 0 ? (long long)c->nbucket[1] * 20 > (long long)c->n
-                                       : (c->opt_split > 0 && c->nbucket[1] > 0);
+  const int dec = bucket_decisions(c);
+  const bool split1 = (dec & 1) != 0;
   const bool fork = split1 && c->side != nullptr;
   cudaStream_t s2 = s;
   if (fork) {
@@ -154,7 +154,7 @@ void launch_buckets(Ctx* c, FwdArgs<T> a, cudaStream_t s) {
     launch_t<T, NS, 8, BATCH>(c, b1, force_grid(c, 8, ev_mode<T, BATCH>(a)), s2);
   }
   // bucket 0, then bucket 1 (unless split off), then bucket 2 (general path)
-  const bool wide = (long long)c->nbucket[2] * 200 > (long long)c->n;
+  const bool wide = (dec & 2) != 0;
   FwdArgs<T> b0 = a;
   b0.order = c->d_bucket;
   b0.n_items = c->d_flags + flag_bucket(0);

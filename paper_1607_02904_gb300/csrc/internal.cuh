@@ -240,12 +240,25 @@ struct Ctx {
     int nsteps = 0, rebuild_every = 0, ssb0 = 0, precision = 0;
     bool timing = false;
     long long gen = -1;
+    int decisions = -1;     // bucket_decisions() at capture
     long long kernels = 0;  // kernel launches inside the graph, conditional bodies excluded
     long long body_kernels = 0;  // kernel launches of one conditional rebuild
   } graph;
   double* d_snap = nullptr;  // x, v, f at the start of a graph launch (rollback)
   size_t snap_alloc = 0;
 };
+
+// The force launch's host decisions that depend on the last build's bucket
+// sizes, as bits: a capacity-8 launch for bucket 1 on the side stream (1),
+// the wide kernel for bucket 2 (2). They choose which kernel evaluates an
+// atom, and so the rounding of its terms; a captured MD graph holds them, and
+// is captured again when they change.
+inline int bucket_decisions(const Ctx* c) {
+  const bool split1 = c->opt_split < 0 ? (long long)c->nbucket[1] * 20 > (long long)c->n
+                                       : (c->opt_split > 0 && c->nbucket[1] > 0);
+  const bool wide = (long long)c->nbucket[2] * 200 > (long long)c->n;
+  return (split1 ? 1 : 0) | (wide ? 2 : 0);
+}
 
 // Records an event pair around a launch sequence when timing is enabled.
 struct TimedRegion {

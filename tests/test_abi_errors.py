@@ -23,7 +23,7 @@ def lib():
 def _null_args(argtypes):
     out = []
     for t in argtypes[1:]:
-        if t is ctypes.c_int:
+        if t in (ctypes.c_int, ctypes.c_longlong):
             out.append(0)
         elif t is ctypes.c_double:
             out.append(0.0)
