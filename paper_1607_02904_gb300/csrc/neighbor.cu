@@ -328,10 +328,13 @@ struct Radii {
 
 // Atoms of each cell in ascending index order, so that list order (stencil
 // order, then cell order) does not depend on the scatter's atomic order.
-// Sorts each cell's atoms by index (insertion sort: cells hold a few atoms)
-// and writes the positions in cell order for the candidate scan: slot s of the
-// cell arrays holds the float offsets of atom j = cell_atoms[s] and, in the
-// fourth word, the bits of 4 j + species (j < 2^26, at most 4 species).
+// Sorts each cell's atoms by index and writes the positions in cell order for
+// the candidate scan: slot s of the cell arrays holds the float offsets of
+// atom j = cell_atoms[s] and, in the fourth word, the bits of 4 j + species
+// (j < 2^26, at most 4 species). A cell of at most CS_REG atoms is sorted in
+// registers (odd-even transposition over CS_REG keys, empty keys last) with
+// its loads issued together; larger cells by insertion in place.
+constexpr int CS_REG = 8;
 __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
                             int* __restrict__ cell_atoms, const float4* __restrict__ pos32,
                             float4* __restrict__ posc) {
@@ -339,6 +342,32 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start,
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncell) return;
   const int s0 = cell_start[c], s1 = cell_start[c + 1];
+  const int m = s1 - s0;
+  if (m <= CS_REG) {
+    int k[CS_REG];
+#pragma unroll
+    for (int q = 0; q < CS_REG; ++q) k[q] = q < m ? cell_atoms[s0 + q] : 0x7fffffff;
+#pragma unroll
+    for (int r = 0; r < CS_REG; ++r)
+#pragma unroll
+      for (int q = r & 1; q + 1 < CS_REG; q += 2) {
+        const int lo = min(k[q], k[q + 1]), hi = max(k[q], k[q + 1]);
+        k[q] = lo;
+        k[q + 1] = hi;
+      }
+    float4 p[CS_REG];
+#pragma unroll
+    for (int q = 0; q < CS_REG; ++q)
+      if (q < m) p[q] = pos32[k[q]];
+#pragma unroll
+    for (int q = 0; q < CS_REG; ++q)
+      if (q < m) {
+        cell_atoms[s0 + q] = k[q];
+        posc[s0 + q] = make_float4(p[q].x, p[q].y, p[q].z,
+                                   __int_as_float(4 * k[q] + __float_as_int(p[q].w)));
+      }
+    return;
+  }
   for (int a = s0 + 1; a < s1; ++a) {
     const int key = cell_atoms[a];
     int b = a - 1;
