@@ -833,9 +833,11 @@ static int enqueue_conditional_build(Ctx* c, const double* x, cudaStream_t cs,
 
 // Enqueues nsteps velocity-Verlet steps. sync_builds: rebuild with a host
 // check (eager); otherwise without host synchronisation (graph capture).
+// snap (may be null): receives x, v, f as the first step reads them (the
+// start state of a rerun)
 static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
                       int nsteps, int rebuild_every, double* rows, double* thermo,
-                      bool sync_builds, cudaStream_t s) {
+                      bool sync_builds, cudaStream_t s, double* snap = nullptr) {
   int st = TERSOFF_OK;
   const bool on_skin = rebuild_every == TERSOFF_REBUILD_ON_SKIN;
   if (rows) TGB_CUDA(c, cudaMemsetAsync(rows, 0, sizeof(double) * tgb::ACC_LEN * (size_t)nsteps, s));
@@ -850,7 +852,7 @@ static int enqueue_md(Ctx* c, double* x, double* v, double* f, double dt,
     {
       tgb::TimedRegion tr(c, 2, s);
       if ((st = tgb::launch_md_step(c, x, v, f, dt, step == 0 ? 1 : 2, !rebuild, ke_row,
-                                    nullptr, s)))
+                                    nullptr, s, step == 0 ? snap : nullptr)))
         return st;
     }
     if (rebuild) {
@@ -942,18 +944,17 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     TGB_CUDA(c, cudaStreamSynchronize(s));
     return TERSOFF_OK;
   }
-  // graph path: snapshot the state, replay (capturing on a new shape), check
+  // graph path: replay (capturing on a new shape), check; the graph's first
+  // step writes the start state into the snapshot as it reads it
   const size_t m = 3 * (size_t)n;
   if (c->snap_alloc < 3 * m) {
     if ((st = tgb::dev_alloc(c, &c->d_snap, 3 * m))) return st;
     c->snap_alloc = 3 * m;
   }
-  TGB_CUDA(c, cudaMemcpyAsync(c->d_snap, x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-  TGB_CUDA(c, cudaMemcpyAsync(c->d_snap + m, v, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
-  TGB_CUDA(c, cudaMemcpyAsync(c->d_snap + 2 * m, f, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
   const int ssb0 = on_skin ? -1 : c->steps_since_build;
   auto& G = c->graph;
   const bool same = G.exec && G.gen == c->gen && G.x == x && G.v == v && G.f == f &&
+                    G.snap == c->d_snap &&
                     G.thermo == thermo && G.dt == dt && G.nsteps == nsteps &&
                     G.rebuild_every == rebuild_every && G.ssb0 == ssb0 &&
                     G.precision == c->precision && G.timing == c->timing &&
@@ -969,7 +970,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     const long long l0 = c->launches;
     c->capturing = true;
     c->timer_sink = &G.timers;
-    st = enqueue_md(c, x, v, f, dt, nsteps, rebuild_every, rows, thermo, false, cs);
+    st = enqueue_md(c, x, v, f, dt, nsteps, rebuild_every, rows, thermo, false, cs, c->d_snap);
     c->capturing = false;
     c->timer_sink = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
@@ -989,6 +990,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
     G.x = x;
     G.v = v;
     G.f = f;
+    G.snap = c->d_snap;
     G.thermo = thermo;
     G.dt = dt;
     G.coef = c->coef;

@@ -147,10 +147,13 @@ __device__ __forceinline__ void block_sum_add(double v, double* dst) {
 // slots with compensated sums), KE its kinetic-energy row; with MG false the
 // kernel decides both at run time. The specialised instances carry fewer
 // registers.
+// snap (first step of a call, MG false; may be null): receives x, v and f as
+// read (three n x 3 blocks), the state a rerun of the call starts from.
 template <bool MG, bool KE>
 __global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restrict__ x,
                        double* __restrict__ v, const double* __restrict__ f, const __grid_constant__ Coef cf,
-                       double dt, int kick, int do_pack, double* ke_row_, double* acc_zero) {
+                       double dt, int kick, int do_pack, double* ke_row_, double* acc_zero,
+                       double* __restrict__ snap) {
   pdl_wait();  // the previous kernel's writes (a launch with launch_pdl)
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int gather = MG ? 1 : gather_;
@@ -173,6 +176,18 @@ __global__ void k_step(PackArgs pk, GatherArgs ga, int gather_, double* __restri
       F0 = f[b];
       F1 = f[b + 1];
       F2 = f[b + 2];
+    }
+    if (!MG && snap) {
+      const size_t m = 3 * (size_t)pk.n;
+      snap[b] = x0;
+      snap[b + 1] = x1;
+      snap[b + 2] = x2;
+      snap[m + b] = v0;
+      snap[m + b + 1] = v1;
+      snap[m + b + 2] = v2;
+      snap[2 * m + b] = F0;
+      snap[2 * m + b + 1] = F1;
+      snap[2 * m + b + 2] = F2;
     }
     const double cu = cf.c[t];
     const double kcu = kick == 2 ? cf.c2[t] : cu;
@@ -399,21 +414,23 @@ int launch_pack_positions(Ctx* c, const double* x, bool build, cudaStream_t s) {
 }
 
 int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick, bool pack,
-                   double* ke_row, double* acc_zero, cudaStream_t s) {
+                   double* ke_row, double* acc_zero, cudaStream_t s, double* snap) {
   const int B = c->opt_block;
   const GatherArgs ga = make_gather(c);
   const int grid = (c->n + B - 1) / B;
   if (kick == 2 && !ga.fp64 && !ga.atomic_mode) {
     if (ke_row)
       TGB_CUDA(c, launch_pdl(k_step<true, true>, grid, B, 0, s, make_pack(c, true), ga, 1, x, v,
-                             f, c->coef, dt, kick, pack ? 1 : 0, ke_row, acc_zero));
+                             f, c->coef, dt, kick, pack ? 1 : 0, ke_row, acc_zero,
+                             (double*)nullptr));
     else
       TGB_CUDA(c, launch_pdl(k_step<true, false>, grid, B, 0, s, make_pack(c, true), ga, 1, x, v,
-                             f, c->coef, dt, kick, pack ? 1 : 0, (double*)nullptr, acc_zero));
+                             f, c->coef, dt, kick, pack ? 1 : 0, (double*)nullptr, acc_zero,
+                             (double*)nullptr));
   } else {
     TGB_CUDA(c, launch_pdl(k_step<false, false>, grid, B, 0, s, make_pack(c, true), ga,
                            kick == 2 ? 1 : 0, x, v, f, c->coef, dt, kick, pack ? 1 : 0, ke_row,
-                           acc_zero));
+                           acc_zero, snap));
   }
   c->launches++;
   TGB_CUDA(c, cudaGetLastError());

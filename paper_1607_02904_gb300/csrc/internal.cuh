@@ -235,6 +235,7 @@ struct Ctx {
     cudaGraphExec_t exec = nullptr;
     std::vector<Pending> timers;
     const double *x = nullptr, *v = nullptr, *f = nullptr, *thermo = nullptr;
+    const double* snap = nullptr;  // the start-state copy the first step writes
     double dt = 0.0;
     Coef coef{};
     int nsteps = 0, rebuild_every = 0, ssb0 = 0, precision = 0;
@@ -392,9 +393,10 @@ int launch_gather(Ctx* c, double* f, cudaStream_t s);
 //   evaluation: the closing half kick of the previous step and the opening
 //   half kick of this one); x += dt v; pack; ke_row (optional) receives
 //   sum m (v_prev + c F)^2 / 2 of the previous step; acc_zero (optional) is
-//   cleared for the coming force evaluation.
+//   cleared for the coming force evaluation; snap (optional, kick 1 only)
+//   receives x, v and f as read (3 x n x 3 doubles).
 int launch_md_step(Ctx* c, double* x, double* v, double* f, double dt, int kick, bool pack,
-                   double* ke_row, double* acc_zero, cudaStream_t s);
+                   double* ke_row, double* acc_zero, cudaStream_t s, double* snap = nullptr);
 // closing half kick of the last step with gathered forces, which are also
 // written to f; ke_row (optional) as above
 int launch_final_kick(Ctx* c, double* v, double* f, double* ke_row, cudaStream_t s);
