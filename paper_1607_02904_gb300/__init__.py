@@ -27,5 +27,5 @@ from ._lib import (  # noqa: F401
     pipe_peaks,
     checkpoint_info,
 )
-from .params import mix_tersoff89, FIELDS  # noqa: F401
+from .params import mix_tersoff89, read_table, write_table, FIELDS  # noqa: F401
 from .autograd import TersoffSystem, TersoffBatch, TersoffFunction, energy_forces  # noqa: F401

@@ -48,3 +48,59 @@ def mix_tersoff89(elem, chi):
     t[..., 12] = 0.5 * (lam[i] + lam[j])
     t[..., 13] = np.sqrt(A[i] * A[j])
     return t.ravel()
+
+
+def read_table(path, species):
+    """Per-triplet table from a text file of element-triplet entries.
+
+    Each entry is three element names (e_i e_j e_k) followed by the 14 values
+    of its record in ``FIELDS`` order (m, gamma, lambda3, c, d, h, n, beta,
+    lambda2, B, R, D, lambda1, A); an entry may run over several lines, and
+    text after '#' is a comment. ``species`` lists the element names in
+    species-index order; entries naming other elements are skipped. Every
+    triplet of the listed elements must appear exactly once. Returns the flat
+    table (n_species^3 x 14) for tersoff_params.
+    """
+    names = list(species)
+    index = {e: q for q, e in enumerate(names)}
+    if len(index) != len(names):
+        raise ValueError("duplicate element names")
+    tokens = []
+    with open(path) as fh:
+        for line in fh:
+            tokens.extend(line.split("#", 1)[0].split())
+    per = 3 + len(FIELDS)
+    if len(tokens) % per:
+        raise ValueError(f"{path}: {len(tokens)} fields do not form entries of {per}")
+    ns = len(names)
+    t = np.full((ns, ns, ns, len(FIELDS)), np.nan)
+    seen = set()
+    for q in range(0, len(tokens), per):
+        e = tokens[q:q + 3]
+        if not all(x in index for x in e):
+            continue
+        key = tuple(index[x] for x in e)
+        if key in seen:
+            raise ValueError(f"{path}: entry {' '.join(e)} appears twice")
+        seen.add(key)
+        t[key] = [float(v) for v in tokens[q + 3:q + per]]
+    if len(seen) != ns ** 3:
+        missing = [" ".join(names[a] for a in (i, j, k)) for i in range(ns) for j in range(ns)
+                   for k in range(ns) if (i, j, k) not in seen]
+        raise ValueError(f"{path}: no entry for {', '.join(missing)}")
+    return t.ravel()
+
+
+def write_table(path, table, species):
+    """Writes a flat per-triplet table in the format ``read_table`` reads, one
+    entry per line, values with 17 significant digits (exact round trip)."""
+    names = list(species)
+    ns = len(names)
+    t = np.asarray(table, dtype=np.float64).reshape(ns, ns, ns, len(FIELDS))
+    with open(path, "w") as fh:
+        fh.write("# e_i e_j e_k " + " ".join(FIELDS) + "\n")
+        for i in range(ns):
+            for j in range(ns):
+                for k in range(ns):
+                    vals = " ".join(f"{v:.17g}" for v in t[i, j, k])
+                    fh.write(f"{names[i]} {names[j]} {names[k]} {vals}\n")

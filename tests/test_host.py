@@ -62,3 +62,52 @@ def test_create_without_gpu_reports_error():
     assert st == 6  # TERSOFF_E_CUDA
     assert lib.tersoff_create(None, 1) == 1
     assert lib.tersoff_destroy(None) == 0
+
+
+@pytest.mark.parametrize("names", [["Si"], ["Si", "C"]])
+def test_table_file_round_trip(tmp_path, names):
+    import paper_1607_02904_gb300 as T
+    table = T.mix_tersoff89(*W.element_records(names))
+    p = tmp_path / "t.txt"
+    T.write_table(str(p), table, names)
+    assert np.array_equal(T.read_table(str(p), names), table)
+    # species order is the caller's: the same file read with the names swapped
+    # gives the table with species indices permuted
+    if len(names) == 2:
+        sw = T.read_table(str(p), names[::-1]).reshape(2, 2, 2, 14)
+        ref = np.asarray(table).reshape(2, 2, 2, 14)
+        for i in range(2):
+            for j in range(2):
+                for k in range(2):
+                    assert np.array_equal(sw[1 - i, 1 - j, 1 - k], ref[i, j, k])
+
+
+def test_table_file_format(tmp_path):
+    """A hand-written file: comments, an entry over two lines, an entry of
+    another element that is skipped, and the record each entry lands in."""
+    import paper_1607_02904_gb300 as T
+    vals = {("A", "A", "A"): 1.0, ("A", "A", "B"): 2.0, ("A", "B", "A"): 3.0, ("A", "B", "B"): 4.0,
+            ("B", "A", "A"): 5.0, ("B", "A", "B"): 6.0, ("B", "B", "A"): 7.0, ("B", "B", "B"): 8.0}
+    lines = ["# test table", "X A A " + " ".join(["9"] * 14) + "  # another element"]
+    for (i, j, k), v in vals.items():
+        rec = " ".join(f"{v + q / 100:g}" for q in range(14))
+        if (i, j, k) == ("A", "B", "A"):
+            toks = rec.split()
+            lines += [f"{i} {j} {k} " + " ".join(toks[:5]), " ".join(toks[5:])]
+        else:
+            lines.append(f"{i} {j} {k} {rec}")
+    p = tmp_path / "t.txt"
+    p.write_text("\n".join(lines) + "\n")
+    t = T.read_table(str(p), ["A", "B"]).reshape(2, 2, 2, 14)
+    for (i, j, k), v in vals.items():
+        idx = tuple("AB".index(x) for x in (i, j, k))
+        assert np.allclose(t[idx], [v + q / 100 for q in range(14)], rtol=0, atol=1e-12)
+    # a missing triplet, a duplicate, a broken entry are refused
+    with pytest.raises(ValueError, match="no entry"):
+        T.read_table(str(p), ["A", "B", "X"])
+    p.write_text("\n".join(lines + [lines[2]]) + "\n")
+    with pytest.raises(ValueError, match="twice"):
+        T.read_table(str(p), ["A", "B"])
+    p.write_text("\n".join(lines + ["A A"]) + "\n")
+    with pytest.raises(ValueError, match="entries of 17"):
+        T.read_table(str(p), ["A", "B"])
