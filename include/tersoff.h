@@ -20,6 +20,10 @@
  *    tersoff_last_error() gives a one-line description of the last failure on
  *    that context. A failed call leaves caller-owned outputs undefined.
  *  - A context is not thread-safe: one host thread at a time per context.
+ *  - The entry points that enqueue work (builds, evaluations, backward, MD,
+ *    autotuning, halo packing, checkpoints; not tersoff_compute_noalloc) mark
+ *    their host call with an NVTX range named after the entry point, which
+ *    profilers that record NVTX show around the call's kernels.
  */
 #ifndef TERSOFF_GB300_H
 #define TERSOFF_GB300_H

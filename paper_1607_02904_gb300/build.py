@@ -73,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".{os.getpid()}.tmp"
     libdir = _cuda_lib_dir(nvcc)
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-        "-L" + libdir, "-Xlinker", "-rpath=" + libdir]
+        "-L" + libdir, "-Xlinker", "-rpath=" + libdir, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -478,6 +478,7 @@ int tersoff_params(tersoff_ctx* p, int ns, const double* table) {
 
 int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, int n,
                            const double* box, double r_list, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_neighbor_build");
   Ctx* c = C(p);
   int st = tgb::check_ctx(c);
   if (st) return st;
@@ -516,6 +517,7 @@ int tersoff_neighbor_build(tersoff_ctx* p, const double* x, const int* types, in
 int tersoff_neighbor_build_batched(tersoff_ctx* p, const double* x, const int* types, int n,
                                    const int* sys_offsets, const double* boxes, int n_sys,
                                    double r_list, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_neighbor_build_batched");
   Ctx* c = C(p);
   int st = tgb::check_ctx(c);
   if (st) return st;
@@ -689,6 +691,7 @@ static int compute_impl(Ctx* c, const double* x, int n, double* energy, double* 
 
 int tersoff_compute_batched(tersoff_ctx* p, const double* x, int n, double* energies,
                             double* forces, double* virials, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_compute_batched");
   Ctx* c = C(p);
   int st = tgb::check_ctx(c);
   if (st) return st;
@@ -701,11 +704,13 @@ int tersoff_compute_batched(tersoff_ctx* p, const double* x, int n, double* ener
 
 int tersoff_compute(tersoff_ctx* p, const double* x, int n, double* energy, double* forces,
                     double* virial, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_compute");
   return compute_impl(C(p), x, n, energy, forces, virial, nullptr, (cudaStream_t)stream);
 }
 
 int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eatom,
                             void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_compute_peratom");
   Ctx* c = C(p);
   if (!c) return TERSOFF_E_INVALID_ARG;
   if (!eatom && n > 0) return tgb::fail(c, TERSOFF_E_INVALID_ARG, "eatom is null");
@@ -714,6 +719,7 @@ int tersoff_compute_peratom(tersoff_ctx* p, const double* x, int n, double* eato
 
 int tersoff_backward(tersoff_ctx* p, const double* x, int n, const double* gE, const double* gF,
                      double* grad_x, double* grad_table, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_backward");
   Ctx* c = C(p);
   int st = tgb::check_ctx(c);
   if (st) return st;
@@ -1057,6 +1063,7 @@ static int md_impl(Ctx* c, double* x, double* v, double* f, int n, const double*
 
 int tersoff_md_step(tersoff_ctx* p, double* x, double* v, double* f, int n, const double* mass,
                     double dt, int nsteps, int rebuild_every, double* thermo, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_md_step");
   return md_impl(C(p), x, v, f, n, mass, dt, nsteps, rebuild_every, thermo,
                  (cudaStream_t)stream);
 }
@@ -1064,6 +1071,7 @@ int tersoff_md_step(tersoff_ctx* p, double* x, double* v, double* f, int n, cons
 int tersoff_md_step_host(tersoff_ctx* p, double* x, double* v, double* f, int n,
                          const double* mass, double dt, int nsteps, int rebuild_every,
                          double* thermo, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_md_step_host");
   Ctx* c = C(p);
   int st = tgb::check_ctx(c);
   if (st) return st;
@@ -1123,6 +1131,7 @@ std::string opt_text(const TuneOpt& o) {
 
 int tersoff_autotune(tersoff_ctx* p, const double* x, const double* v, int n, const double* mass,
                      double dt, int steps, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_autotune");
   Ctx* c = C(p);
   if (c) c->fine_valid = false;  // trial steps rebuild the lists
   int st = tgb::check_ctx(c);
@@ -1264,6 +1273,7 @@ int tersoff_halo_pack(tersoff_ctx* p, const double* x, const int* types, const l
                       int n, int axis, const double* geo, int cap, double* x_local,
                       double* send_x, int* send_t, long long* send_id, int* counts,
                       void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_halo_pack");
   Ctx* c = C(p);
   if (!c) return TERSOFF_E_INVALID_ARG;
   if (n < 0 || cap < 0 || axis < 0 || axis > 2 || !geo || !counts)

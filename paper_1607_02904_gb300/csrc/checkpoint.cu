@@ -126,6 +126,7 @@ extern "C" {
 
 int tersoff_checkpoint_save(tersoff_ctx* p, const char* path, const double* x, const double* v,
                             const double* f, int n, long long step, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_checkpoint_save");
   Ctx* c = p ? &p->impl : nullptr;
   if (!c) return TERSOFF_E_INVALID_ARG;
   TGB_CUDA(c, cudaSetDevice(c->device));
@@ -188,6 +189,7 @@ int tersoff_checkpoint_info(const char* path, int* n, int* n_species) {
 
 int tersoff_checkpoint_load(tersoff_ctx* p, const char* path, double* x, double* v, double* f,
                             int* types, int n, long long* step, void* stream) {
+  tgb::NvtxRange nvtx_range("tersoff_checkpoint_load");
   Ctx* c = p ? &p->impl : nullptr;
   if (!c) return TERSOFF_E_INVALID_ARG;
   TGB_CUDA(c, cudaSetDevice(c->device));

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -260,6 +261,16 @@ inline int bucket_decisions(const Ctx* c) {
   const bool wide = (long long)c->nbucket[2] * 200 > (long long)c->n;
   return (split1 ? 1 : 0) | (wide ? 2 : 0);
 }
+
+// An NVTX range over an entry point's host call, named after it: profilers that
+// record NVTX (Nsight Systems; Nsight Compute's --nvtx filters) show each
+// call's kernels under it. Without such a tool attached it costs a check.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Records an event pair around a launch sequence when timing is enabled.
 struct TimedRegion {
