@@ -137,49 +137,72 @@ __global__ void k_bin_pack(int n, const double* __restrict__ x, const __grid_con
   if (i >= n) return;
   const int t = bp.types[i];
   int c3[3], q3[3];
-  double xr[3], o3[3];
+  double xr[3], o3[3], qo3[3];
+  long long xb3[3], lo3[3], hi3[3];
+  bool inb[3];
   bool finite = true;
   const long long mb = __double_as_longlong(6755399441055744.0);
+  // per axis: the bits of x, the inside-the-box test and a float estimate of
+  // the cell (truncated from the bits); then, for the three axes together, the
+  // estimated cell's thresholds and origins (one round of independent loads)
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double x_in = x[3 * (size_t)i + a];
     xr[a] = x_in;
-    double xa = x_in;
-    long long xb = __double_as_longlong(xa);
+    long long xb = __double_as_longlong(x_in);
     if ((xb & 0x7ff0000000000000ll) == 0x7ff0000000000000ll) {
       finite = false;
-      xa = 0.0;
-      xb = 0;
+      xb = 0;  // binned as x = 0
     }
+    xb3[a] = xb;
     const long long* tb = bp.tab + a * BT_AXIS;
-    int c;
-    double o, qo;
-    if (xb >= 0 && xb < __ldg(&tb[0])) {
-      // float estimate of the cell from the bits of x (truncated), then the
-      // exact cell from the thresholds
-      const int e = (int)(xb >> 52) - 1023 + 127;
-      const float xf = __uint_as_float(
-          e <= 0 ? 0u : (((uint32_t)e << 23) | (uint32_t)((xb >> 29) & 0x7fffff)));
-      c = (int)(xf * bp.invhf[a]);
-      c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-      while (c < g.nc[a] - 1 && xb >= __ldg(&tb[c + 1])) ++c;
-      while (c > 0 && xb < __ldg(&tb[c])) --c;
-      o = __longlong_as_double(__ldg(&tb[BT_O + c]));
-      qo = __longlong_as_double(__ldg(&tb[BT_Q + c]));
+    inb[a] = xb >= 0 && xb < __ldg(&tb[0]);
+    const int e = (int)(xb >> 52) - 1023 + 127;
+    const float xf = __uint_as_float(
+        e <= 0 ? 0u : (((uint32_t)e << 23) | (uint32_t)((xb >> 29) & 0x7fffff)));
+    int c = (int)(xf * bp.invhf[a]);
+    c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
+    c3[a] = c;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long* tb = bp.tab + a * BT_AXIS;
+    const int c = c3[a];
+    lo3[a] = __ldg(&tb[c]);      // threshold of cell c (c > 0)
+    hi3[a] = __ldg(&tb[c + 1]);  // of cell c + 1 (c + 1 < nc; otherwise an origin word, unused)
+    o3[a] = __longlong_as_double(__ldg(&tb[BT_O + c]));
+    qo3[a] = __longlong_as_double(__ldg(&tb[BT_Q + c]));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const long long* tb = bp.tab + a * BT_AXIS;
+    const long long xb = xb3[a];
+    const int nc = g.nc[a];
+    int c = c3[a];
+    if (inb[a]) {
+      // the exact cell from the thresholds (the estimate is off by at most a
+      // step, rarely)
+      if (!((c == 0 || xb >= lo3[a]) && (c == nc - 1 || xb < hi3[a]))) {
+        while (c < nc - 1 && xb >= __ldg(&tb[c + 1])) ++c;
+        while (c > 0 && xb < __ldg(&tb[c])) --c;
+        o3[a] = __longlong_as_double(__ldg(&tb[BT_O + c]));
+        qo3[a] = __longlong_as_double(__ldg(&tb[BT_Q + c]));
+      }
     } else {
       // k_bin's general path: periodic image and wrapped coordinate
+      const double xa = __longlong_as_double(xb);
       const double k = floor(xa * g.invL[a]);
       const double w = xa - g.L[a] * k;
       c = (int)(w * g.invh[a]);
-      c = c < 0 ? 0 : (c >= g.nc[a] ? g.nc[a] - 1 : c);
-      o = fma(k, g.L[a], c * g.h[a]);
-      qo = 6755399441055744.0 - o * bp.scale;
+      c = c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+      o3[a] = fma(k, g.L[a], c * g.h[a]);
+      qo3[a] = 6755399441055744.0 - o3[a] * bp.scale;
     }
-    origin[3 * (size_t)i + a] = o;
-    qorg[3 * (size_t)i + a] = qo;
     c3[a] = c;
-    o3[a] = o;
+    origin[3 * (size_t)i + a] = o3[a];
+    qorg[3 * (size_t)i + a] = qo3[a];
     // the pack of k_pack at a build: q = round((x - o) 2^S) with one rounding
-    q3[a] = (int)(__double_as_longlong(fma(x_in, bp.scale, qo)) - mb);
+    q3[a] = (int)(__double_as_longlong(fma(xr[a], bp.scale, qo3[a])) - mb);
   }
   if (!finite) atomicOr(&flags[FLAG_NONFINITE], 1);
   const int cell = (c3[2] * g.nc[1] + c3[1]) * g.nc[0] + c3[0];
