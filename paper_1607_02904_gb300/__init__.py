@@ -28,4 +28,5 @@ from ._lib import (  # noqa: F401
     checkpoint_info,
 )
 from .params import mix_tersoff89, read_table, write_table, FIELDS  # noqa: F401
+from . import thermo  # noqa: F401
 from .autograd import TersoffSystem, TersoffBatch, TersoffFunction, energy_forces  # noqa: F401

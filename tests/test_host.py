@@ -111,3 +111,28 @@ def test_table_file_format(tmp_path):
     p.write_text("\n".join(lines + ["A A"]) + "\n")
     with pytest.raises(ValueError, match="entries of 17"):
         T.read_table(str(p), ["A", "B"])
+
+
+def test_thermo_records_and_jsonl(tmp_path):
+    """Temperature from the kinetic energy (3/2 N kB T), the ideal-gas pressure
+    with a zero virial, the virial's share, step numbering and the file."""
+    import json
+    from paper_1607_02904_gb300 import thermo
+    n, T0 = 1000, 1000.0
+    ke = 1.5 * n * thermo.KB_EV_PER_K * T0
+    rows = np.array([[-4630.0, ke, -4630.0 + ke], [-4629.0, 2 * ke, -4629.0 + 2 * ke]])
+    vol = 20000.0
+    w = np.zeros((2, 6))
+    w[1, :3] = 30.0  # trace 90 eV: adds 30 eV / V
+    recs = thermo.records(rows, n, step0=10, virials=w, volume=vol)
+    assert [r["step"] for r in recs] == [11, 12]
+    assert abs(recs[0]["temperature_K"] - T0) < 1e-9 and abs(recs[1]["temperature_K"] - 2 * T0) < 1e-9
+    ideal = n * thermo.KB_EV_PER_K * T0 / vol * thermo.EV_PER_A3_IN_BAR
+    assert abs(recs[0]["pressure_bar"] - ideal) < 1e-9 * ideal
+    assert abs(recs[1]["pressure_bar"] - (2 * ideal + 30.0 / vol * thermo.EV_PER_A3_IN_BAR)) < 1e-6
+    p = tmp_path / "thermo.jsonl"
+    assert thermo.write_jsonl(str(p), rows, n, append=False) == 2
+    assert thermo.write_jsonl(str(p), rows, n, step0=2) == 2
+    lines = [json.loads(s) for s in p.read_text().splitlines()]
+    assert [r["step"] for r in lines] == [1, 2, 3, 4]
+    assert lines[0]["etot_eV"] == rows[0, 2] and "pressure_bar" not in lines[0]
