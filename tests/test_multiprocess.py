@@ -1,4 +1,4 @@
-"""The benchmark's multi-process logic on CPU ranks (gloo, world size 2): the
+"""The benchmark's multi-process logic on CPU ranks (gloo, world size 2 or 3): the
 reported time is the maximum over ranks and the work is the sum, and rank
 identity comes from the launcher's environment. Each GPU runs an independent
 replica of the workload (no collective on the data path), so these are the
@@ -137,10 +137,10 @@ def _fit_worker(rank, world, port, out):
         dist.destroy_process_group()
 
 
-def test_sharded_fit_step_equals_whole_batch():
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_fit_step_equals_whole_batch(world):
     import numpy as np
     import workloads as W
-    world = 2
     port = _free_port()
     mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
